@@ -1,0 +1,340 @@
+"""Throughput of one optimizer iteration of per-pixel stochastic gradient estimation.
+
+Workload (the batched-estimator configuration): UV sphere of 8,192 triangles
+(64 x 64 segments, 4,034 welded vertices), 512^2 RGB float32 texture, 512^2
+render, 8 seeded views on a sphere of radius 3, 64 antithetic pairs per view
+per iteration, all in one persistent launch; the whole iteration (estimate +
+Adam step, lr = eps as in the paper's Section 5) is captured in a CUDA graph.
+Synthetic data: seeded meshes/textures, targets rendered from a seeded target
+scene.  A "step" is one such iteration: 8 x 64 x 512^2 = 134,217,728
+antithetic pixel pairs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (test infrastructure, single thread) on a
+bounded sample of the same workload.  With N > 1 (torchrun) every rank runs an
+independent replica (the estimator does not need a collective), and rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "antithetic render-pair pixels/s and param-gradients/s vs plain path; HBM GB/s fraction"
+UNIT = "pixel-pairs/s"
+WORKLOAD = "sphere8k_tex512_r512_8views_x_64pairs"
+N_VIEWS, PAIRS, RENDER = 8, 64, 512
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# lane-instructions one pixel pair costs in the estimator kernel; see the design doc (roofline)
+ALU_OPS_PER_PIXEL_PAIR = None
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_scene():
+    import synth
+    return synth.config_batched(n_views=N_VIEWS, pairs=PAIRS, render=RENDER)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The oracle, single-threaded, on a bounded sample: view 0, pairs 0.. until the budget is spent."""
+    import oracle
+    import synth
+    sc = make_scene()
+    tg = oracle.render_targets(sc, synth.target_scene(sc))
+    osc = oracle.OracleScene(sc, tg)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        n += 1
+        t1 = time.perf_counter()
+        oracle.estimate(osc, 1, 0, [0], n)
+        dt = time.perf_counter() - t1
+        if dt >= budget_s or n >= 64:
+            break
+        n = max(n, int(n * budget_s / max(dt, 1e-3) * 0.5))
+    px = n * RENDER * RENDER
+    return {"value": px / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"view 0, {n} antithetic pairs at {RENDER}x{RENDER} ({px} pixel pairs), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    sc = make_scene()
+    tg = oracle.render_targets(sc, synth.target_scene(sc))
+    osc = oracle.OracleScene(sc, tg)
+    for w in range(args.warmup):
+        oracle.estimate(osc, 1, w, [w % N_VIEWS], 1)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.estimate(osc, 1, 100 + k, [k % N_VIEWS], 1)
+        times.append(time.perf_counter() - t0)
+    per_step = RENDER * RENDER  # one pair of one view per step (a bounded sample of the iteration)
+    value = per_step * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "1 pair of 1 view per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps x 1 antithetic pair at {RENDER}^2"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2404_09758_gb300 import STEP_ADAM, Scene
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev) if "device_id" in dist.init_process_group.__code__.co_varnames \
+            else dist.init_process_group("nccl")
+
+    sc = make_scene()
+    tgt_scene = Scene.from_arrays(synth.target_scene(sc))
+    targets = tgt_scene.render_targets()
+    torch.cuda.synchronize()
+    del tgt_scene
+    g = Scene.from_arrays(sc, targets=targets)
+    grad, counts = g.new_grad_buffers()
+    m = torch.zeros(g.n_params, device=dev)
+    v = torch.zeros(g.n_params, device=dev)
+    loss = torch.zeros(N_VIEWS, device=dev)
+    views = list(range(N_VIEWS))
+    lr_tex = [t[1] for t in g.textures]
+    n_total = N_VIEWS * PAIRS
+    st = torch.cuda.Stream(device=dev)
+    step_no = [1]
+
+    def iteration(it, t):
+        loss.zero_()
+        g.estimate_grad(1, it, views, PAIRS, grad, counts, loss=loss, stream=st)
+        g.step(STEP_ADAM, grad, counts, n_total, g.textures and sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+
+    # contributions of one iteration (parameter gradients credited), counted exactly
+    with torch.cuda.stream(st):
+        g.estimate_grad(1, 0, views, PAIRS, grad, counts, stream=st)
+    st.synchronize()
+    contributions = int(counts.to(torch.int64).sum().item())
+    touched = int((counts != 0).sum().item())
+    grad.zero_()
+    counts.zero_()
+    assert g.status(st) == 0
+
+    # warm up eagerly, then capture one iteration in a CUDA graph (iteration counter and
+    # Adam step live in host-side arguments, so the graph replays one fixed iteration index)
+    for w in range(max(args.warmup, 1)):
+        iteration(w, w + 1)
+    st.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        iteration(1000, 1)
+    st.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB of L2
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(st):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(st)
+                graph.replay()
+                ev[k][1].record(st)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(ms) / 1000.0
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    px_per_step = N_VIEWS * PAIRS * RENDER * RENDER
+    value = world * px_per_step * args.steps / t_total
+    assert g.status(st) == 0
+
+    # dominant kernel: the estimate call alone (binning prologue + persistent estimator), eager
+    ek = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(st):
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            ek[k][0].record(st)
+            g.estimate_grad(1, 2000 + k, views, PAIRS, grad, counts, stream=st)
+            ek[k][1].record(st)
+    torch.cuda.synchronize()
+    est_ms = statistics.mean(a.elapsed_time(b) for a, b in ek)
+    grad.zero_()
+    counts.zero_()
+
+    # plain path: one estimate after another, separate R and G launches (baseline of the batched path)
+    plain_steps = 1
+    with torch.cuda.stream(st):
+        g.estimate_grad_plain(1, 3000, views, PAIRS, grad, counts, stream=st)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for k in range(plain_steps):
+            g.estimate_grad_plain(1, 3001 + k, views, PAIRS, grad, counts, stream=st)
+        e1.record(st)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / plain_steps
+    grad.zero_()
+    counts.zero_()
+
+    # end to end through the public API from pinned host memory: parameters and targets in,
+    # updated parameters and the loss out, every step
+    host_params = [p.detach().cpu().pin_memory() for p in g.param_groups()]
+    host_targets = targets.cpu().pin_memory()
+    host_loss = torch.empty(N_VIEWS, pin_memory=True)
+    h2d = sum(p.numel() * 4 for p in host_params) + host_targets.numel() * 4
+    d2h = sum(p.numel() * 4 for p in host_params) + host_loss.numel() * 4
+    e2e_steps = max(1, min(args.steps, 5))
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
+    with torch.cuda.stream(st):
+        for k in range(e2e_steps):
+            flush.fill_(k & 0xFF)
+            ee[k][0].record(st)
+            for hp, dp in zip(host_params, g.param_groups()):
+                dp.copy_(hp, non_blocking=True)
+            g.targets.copy_(host_targets, non_blocking=True)
+            graph.replay()
+            for hp, dp in zip(host_params, g.param_groups()):
+                hp.copy_(dp, non_blocking=True)
+            host_loss.copy_(loss, non_blocking=True)
+            ee[k][1].record(st)
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in ee) / 1000.0
+    e2e_value = world * px_per_step * e2e_steps / e2e_s
+
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    clocks = clk.summary()
+    sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    roofline = None
+    if ALU_OPS_PER_PIXEL_PAIR:
+        peak = n_sm * 128 * sm_clock_mhz * 1e6 / 1e12  # lane-ops/s in T
+        achieved = ALU_OPS_PER_PIXEL_PAIR * px_per_step / (est_ms / 1000.0) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": "k_estimate (sge_estimate_grad)"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "views": N_VIEWS, "pairs_per_view": PAIRS,
+                       "render": f"{RENDER}x{RENDER}", "triangles": int(sc.pos_idx.shape[0]),
+                       "params": int(g.n_params), "l2": "flushed between timed steps (256 MB write)",
+                       "graph": "estimate + Adam step captured in one CUDA graph",
+                       "parallelism": f"replicas x{world}"},
+            "param_gradients_per_s": world * contributions * args.steps / t_total,
+            "touched_params_per_s": world * touched * args.steps / t_total,
+            "contributions_per_step": contributions,
+            "estimate_ms": est_ms,
+            "plain_path": {"value": px_per_step / (plain_ms / 1000.0), "unit": UNIT, "ms_per_step": plain_ms,
+                           "param_gradients_per_s": contributions / (plain_ms / 1000.0)},
+            "batched_over_plain": plain_ms / (1000.0 * t_total / args.steps),
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": 6 * args.steps,
+            "clocks": clocks}
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

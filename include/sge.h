@@ -1,0 +1,196 @@
+/*
+ * sge.h -- C ABI of a GB300 (sm_103a) implementation of per-pixel stochastic
+ * gradient estimation through a plain rasterizer (Deliot, Heitz, Belcour,
+ * "Transforming a Non-Differentiable Rasterizer into a Differentiable One with
+ * Stochastic Gradient Estimation", 2024).
+ *
+ * One optimisation iteration of the paper (Section 5) is
+ *     repeat N times:  P (perturb, Algorithm 1) -> R (rasterize theta + s eps and
+ *                      theta - s eps, Section 4.3) -> G (per-pixel loss difference,
+ *                      scattered to the contributing parameters, Algorithm 2, Eq. 8)
+ *     then D (descent step on the averaged estimate, Eq. 9, Section 5).
+ * Here sge_estimate_grad runs all N estimates of one iteration (several views,
+ * several antithetic pairs per view) in one persistent launch and
+ * sge_step runs D; sge_render_idb exposes one render of R with its ID and UV
+ * buffers (Section 4.4).
+ *
+ * Conventions shared by every call
+ *  - Every pointer named "device" is CUDA device memory owned by the caller; the
+ *    library borrows it for the lifetime of the scene and never frees it.
+ *  - The library never allocates device memory: scratch lives in a caller-owned
+ *    workspace of sge_workspace_size() bytes.
+ *  - Calls are asynchronous and ordered on the stream given (a cudaStream_t,
+ *    NULL = legacy default stream).  They never synchronise; errors detected by
+ *    kernels (bin overflow, bad indices) land in a device status word that
+ *    sge_status() reads.
+ *  - Return value: SGE_OK or an sge_result code; sge_last_error() gives a
+ *    thread-local message for the last failing call of the calling thread.
+ *  - Parameter vector theta (Table 1): all vertex coordinates first (vertex-major
+ *    x,y,z), then each texture in order, row-major (y, x, channel).
+ *  - A scene is not thread-safe: calls on one scene must be serialised by the caller.
+ */
+#ifndef SGE_H
+#define SGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SGE_MAX_TEXTURES 8
+#define SGE_MAX_VIEWS_PER_CALL 64
+
+typedef enum {
+    SGE_OK = 0,
+    SGE_ERR_INVALID_ARG = 1,   /* a bad argument or descriptor (message says which) */
+    SGE_ERR_CUDA = 2,          /* a CUDA runtime call failed                         */
+    SGE_ERR_BIN_OVERFLOW = 3,  /* (device status) tile bins exceeded bin_capacity    */
+    SGE_ERR_BAD_INDEX = 4,     /* (device status) an index buffer entry out of range */
+    SGE_ERR_UNSUPPORTED = 5,   /* a valid request this build does not implement      */
+    SGE_ERR_WORKSPACE = 6      /* workspace missing, too small or misaligned         */
+} sge_result;
+
+/* Texture roles: what the shading model reads a texture as. */
+enum { SGE_ROLE_ALBEDO = 0, SGE_ROLE_NORMAL = 1, SGE_ROLE_ROUGHNESS = 2, SGE_ROLE_METALLIC = 3 };
+/* Shading models: unlit albedo; Lambert + normal map; GGX (Cook-Torrance) + 4 maps. */
+enum { SGE_SHADE_UNLIT = 0, SGE_SHADE_LAMBERT = 1, SGE_SHADE_GGX = 2 };
+/* Descent steps (Section 5).  MEAN divides each sum by its count instead of 2 eps N. */
+enum { SGE_STEP_SGD = 0, SGE_STEP_ADAM = 1, SGE_STEP_SGD_MEAN = 2 };
+
+typedef struct CUstream_st *sge_stream_t; /* identical to cudaStream_t */
+
+/* One texture parameter group (texels are parameters theta_i, Table 1). */
+typedef struct {
+    float *texels;          /* device, [height][width][channels] float32, row-major      */
+    int32_t width, height;  /* >= 1, width*height < 2^28                                  */
+    int32_t channels;       /* 1..4                                                       */
+    float eps;              /* perturbation magnitude eps_i of every texel channel        */
+    int32_t role;           /* SGE_ROLE_*; only the first texture of each role is read    */
+} sge_texture;
+
+/* Scene: an opaque triangle mesh with textures seen from n_views cameras. */
+typedef struct {
+    float *positions;       /* device, [n_vertices][3] float32 (parameters)               */
+    int32_t n_vertices;     /* >= 3, < 2^28                                                */
+    float eps_pos;          /* perturbation magnitude of every vertex coordinate          */
+    const int32_t *pos_idx; /* device, [n_triangles][3] into positions (welded vertices)  */
+    int32_t n_triangles;    /* >= 1                                                        */
+    const float *uvs;       /* device, [n_uvs][2] float32                                 */
+    int32_t n_uvs;
+    const int32_t *uv_idx;  /* device, [n_triangles][3] into uvs                          */
+    int32_t n_textures;     /* 0..SGE_MAX_TEXTURES                                        */
+    sge_texture textures[SGE_MAX_TEXTURES];
+    const float *mvp;       /* device, [n_views][4][4] row-major; clip = M (x,y,z,1)      */
+    const float *cam_pos;   /* device, [n_views][3] eye positions (GGX view vector)       */
+    int32_t n_views;
+    int32_t width, height;  /* render size, 1..16384                                      */
+    float near_w;           /* a vertex needs clip w > near_w, else its triangle drops    */
+    const float *targets;   /* device, [n_views][height][width][3] target images I        */
+    float background[3];    /* colour of uncovered pixels                                 */
+    int32_t shading;        /* SGE_SHADE_*                                                */
+    float light_dir[3];     /* unit vector towards the light, world space                 */
+    float light_rgb[3];
+    float ambient;
+} sge_scene_desc;
+
+/* Tuning knobs; zero-initialise for defaults. */
+typedef struct {
+    int32_t max_views_per_call; /* views per estimate call the workspace is sized for (default n_views, <= 64) */
+    int64_t bin_capacity;       /* triangle-tile bin entries over those views (default 16 * n_triangles * views) */
+    int32_t pairs_per_item;     /* antithetic pairs one CTA runs per (view, tile) item (default 16) */
+    int32_t blocks_per_sm;      /* persistent CTAs per SM (default: as many as fit) */
+} sge_config;
+
+typedef struct {
+    int32_t kind;                       /* SGE_STEP_*                                   */
+    float lr_pos;                       /* learning rate of vertex coordinates          */
+    float lr_tex[SGE_MAX_TEXTURES];     /* learning rate of each texture                */
+    float beta1, beta2, adam_eps;       /* Adam (Kingma & Ba 2015); paper: 0.9, 0.999   */
+    int32_t t;                          /* Adam step number, >= 1 (bias correction)     */
+} sge_opt;
+
+typedef struct sge_scene sge_scene;
+
+/* Bytes of device workspace a scene needs (scratch for bins, tile lists and the
+ * staged buffers of sge_render_idb).  Table 1 / Section 4.4 for what is stored. */
+int sge_workspace_size(const sge_scene_desc *desc, const sge_config *cfg, size_t *bytes);
+
+/* Validate desc (host-side checks only: sizes, pointers, enums) and create a scene
+ * that borrows every device pointer in desc and uses `workspace` (device, 256-byte
+ * aligned, >= sge_workspace_size bytes) as scratch.  *out receives a host object to
+ * release with sge_destroy_scene.  Index buffers are checked on the device by
+ * sge_validate (status SGE_ERR_BAD_INDEX). */
+int sge_create_scene(const sge_scene_desc *desc, const sge_config *cfg, void *workspace,
+                     size_t workspace_bytes, sge_scene **out);
+
+/* Number of parameters d of the scene (Table 1). */
+int sge_num_params(const sge_scene *scene, int64_t *d);
+
+/* Point the scene at new target images (device, same layout as desc->targets). */
+int sge_set_targets(sge_scene *scene, const float *targets);
+
+/* Enqueue a range check of pos_idx / uv_idx; failures set SGE_ERR_BAD_INDEX. */
+int sge_validate(sge_scene *scene, sge_stream_t stream);
+
+/* Rasterize one perturbed scene (Section 4.3, R; ID and UV buffers, Section 4.4):
+ * theta + side * s eps with s the sign vector of estimate (seed, iter, view, pair)
+ * and side in {-1, 0, +1} (0 = unperturbed).  Outputs (device, any may be NULL):
+ *   depth_id [height][width] uint64: (ordered depth bits << 32) | triangle id of the
+ *            visible triangle (smallest depth, then lowest id), ~0 on background;
+ *   uv       [height][width][2] float32 perspective-correct UV, 0 on background;
+ *   rgb      [height][width][3] float32 shaded colour, background colour where uncovered. */
+int sge_render_idb(sge_scene *scene, int32_t view, uint64_t seed, uint32_t iter, uint32_t pair,
+                   int32_t side, uint64_t *depth_id, float *uv, float *rgb, sge_stream_t stream);
+
+/* All estimates of one iteration (Eq. 9): for each of the n_views views in view_ids
+ * (host array, distinct indices < desc->n_views, n_views <= max_views_per_call) and
+ * each pair n < pairs_per_view, render theta +- s eps with s drawn from
+ * (seed, iter, view, n) and, per pixel p, add (f+_p - f-_p) s_i to grad_sums[i]
+ * and 1 to counts[i] for every parameter i contributing to p on either side
+ * (Algorithm 2, Eq. 8; the three welded vertices of the visible triangle and the
+ * bilinear 2x2 texel footprint of every texture the shading reads).
+ * grad_sums [d] float32 and counts [d] uint32 (device) ACCUMULATE: zero them
+ * before the first call (sge_step zeroes them).  The estimate of Eq. 9 is
+ * grad_sums[i] / (2 eps_i N) with N = n_views * pairs_per_view.
+ * loss_out (device [n_views] float32 or NULL) ACCUMULATES, per view, the sum
+ * over pixels of the mean over pairs of (f+ + f-)/2.
+ * delta_f_out (device [n_views][pairs_per_view][height][width] float32 or NULL)
+ * receives f+ - f- per pixel (a debugging output; it costs bandwidth). */
+int sge_estimate_grad(sge_scene *scene, uint64_t seed, uint32_t iter, const int32_t *view_ids,
+                      int32_t n_views, int32_t pairs_per_view, float *grad_sums, uint32_t *counts,
+                      float *loss_out, float *delta_f_out, sge_stream_t stream);
+
+/* Same results as sge_estimate_grad, computed the plain way: for every (view, pair)
+ * separate launches render both sides into ID/UV buffers, form f+ - f- per pixel
+ * and scatter with global atomics, one estimate after another (the paper's
+ * P -> R -> G loop of Section 5).  Kept as the baseline the batched path is
+ * measured against. */
+int sge_estimate_grad_plain(sge_scene *scene, uint64_t seed, uint32_t iter, const int32_t *view_ids,
+                            int32_t n_views, int32_t pairs_per_view, float *grad_sums,
+                            uint32_t *counts, float *loss_out, sge_stream_t stream);
+
+/* Descent step D (Section 5) on every parameter group, then zero grad_sums and
+ * counts.  g_i = grad_sums[i] / (2 eps_i n_pairs_total) (Eq. 9; for
+ * SGE_STEP_SGD_MEAN, / (2 eps_i max(counts[i], 1))).  SGD: theta -= lr g.  Adam:
+ * m, v (device [d] float32, caller-zeroed before step 1) updated in place,
+ * theta -= lr mhat / (sqrt(vhat) + adam_eps).  The paper uses Adam with
+ * lr = eps (Section 5). */
+int sge_step(sge_scene *scene, const sge_opt *opt, float *grad_sums, uint32_t *counts,
+             int64_t n_pairs_total, float *adam_m, float *adam_v, sge_stream_t stream);
+
+/* Synchronise `stream`, return the device status word (SGE_OK or the first
+ * device-side error) in *device_status and clear it. */
+int sge_status(sge_scene *scene, sge_stream_t stream, int32_t *device_status);
+
+/* Release the host object (never the borrowed device memory). */
+void sge_destroy_scene(sge_scene *scene);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *sge_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGE_H */

@@ -1,0 +1,235 @@
+"""Per-pixel stochastic gradient estimation through a plain rasterizer, on GB300.
+
+Python binding of the C ABI in include/sge.h (libsge.so, built from csrc/):
+tensors provide device memory and streams, every step of the method runs in
+the library's CUDA kernels.  There is no CPU path: the calls raise if the
+library or a CUDA device is missing.
+
+    scene = Scene.from_arrays(arrays, targets)      # borrows torch CUDA tensors
+    scene.estimate_grad(seed, it, views, pairs, grad, counts)   # Eq. 9 sums
+    scene.step(opt, grad, counts, n_total, m, v)                # Adam / SGD, Section 5
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence
+
+from . import _abi
+from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_TEXTURES, MAX_VIEWS_PER_CALL, OK, STEP_ADAM,
+                   STEP_SGD, STEP_SGD_MEAN, SGEError)
+from ._build import build
+
+__all__ = ["Scene", "SGEError", "build", "load", "STEP_SGD", "STEP_ADAM", "STEP_SGD_MEAN", "OK",
+           "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
+
+
+def load(build_if_missing: bool = False):
+    return _abi.load(build_if_missing)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+class Scene:
+    """A scene on the GPU: borrows the tensors it is built from (keep them alive).
+
+    positions [V,3] and every texture [H,W,C] (float32, CUDA, contiguous) are the
+    parameters theta that sge_step updates in place.
+    """
+
+    def __init__(self, positions, pos_idx, uvs, uv_idx, textures, eps_pos: float, mvp, cam_pos,
+                 width: int, height: int, targets=None, near: float = 0.1, shading: int = 0,
+                 light_dir=(0.0, 0.0, 1.0), light_rgb=(1.0, 1.0, 1.0), ambient: float = 0.0,
+                 background=(0.0, 0.0, 0.0), max_views_per_call: int = 0, bin_capacity: int = 0,
+                 pairs_per_item: int = 0, blocks_per_sm: int = 0, device=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("sge needs a CUDA device; there is no CPU path")
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        L = _abi.load()
+
+        def dev(x, dtype):
+            t = torch.as_tensor(x).to(device=self.device, dtype=dtype)
+            return t.contiguous()
+
+        self.positions = dev(positions, torch.float32)
+        self.pos_idx = dev(pos_idx, torch.int32)
+        self.uvs = dev(uvs, torch.float32)
+        self.uv_idx = dev(uv_idx, torch.int32)
+        self.textures = []  # list of (tensor [H,W,C], eps, role)
+        for t in textures:
+            data = dev(t[0], torch.float32)
+            if data.dim() == 2:
+                data = data.unsqueeze(-1).contiguous()
+            self.textures.append((data, float(t[1]), int(t[2])))
+        self.mvp = dev(mvp, torch.float32).reshape(-1, 4, 4).contiguous()
+        self.cam_pos = dev(cam_pos, torch.float32).reshape(-1, 3).contiguous()
+        self.n_views = int(self.mvp.shape[0])
+        self.width, self.height = int(width), int(height)
+        if targets is None:
+            targets = torch.zeros(self.n_views, self.height, self.width, 3)
+        self.targets = dev(targets, torch.float32)
+        if len(self.textures) > MAX_TEXTURES:
+            raise ValueError(f"at most {MAX_TEXTURES} textures")
+
+        d = _abi.SceneDesc()
+        d.positions = _ptr(self.positions)
+        d.n_vertices = int(self.positions.shape[0])
+        d.eps_pos = float(eps_pos)
+        d.pos_idx = _ptr(self.pos_idx)
+        d.n_triangles = int(self.pos_idx.shape[0])
+        d.uvs = _ptr(self.uvs)
+        d.n_uvs = int(self.uvs.shape[0])
+        d.uv_idx = _ptr(self.uv_idx)
+        d.n_textures = len(self.textures)
+        for k, (data, eps, role) in enumerate(self.textures):
+            d.textures[k].texels = _ptr(data)
+            d.textures[k].height, d.textures[k].width, d.textures[k].channels = (int(x) for x in data.shape)
+            d.textures[k].eps = eps
+            d.textures[k].role = role
+        d.mvp = _ptr(self.mvp)
+        d.cam_pos = _ptr(self.cam_pos)
+        d.n_views = self.n_views
+        d.width, d.height = self.width, self.height
+        d.near_w = float(near)
+        d.targets = _ptr(self.targets)
+        for c in range(3):
+            d.background[c] = float(background[c])
+            d.light_dir[c] = float(light_dir[c])
+            d.light_rgb[c] = float(light_rgb[c])
+        d.shading = int(shading)
+        d.ambient = float(ambient)
+        self._desc = d
+        cfg = _abi.Config(int(max_views_per_call), int(bin_capacity), int(pairs_per_item), int(blocks_per_sm))
+        self._cfg = cfg
+        nbytes = C.c_size_t()
+        _abi.check(L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        base = _ptr(self.workspace)
+        off = (-base) % 256
+        handle = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _abi.check(L.sge_create_scene(C.byref(d), C.byref(cfg), base + off, int(nbytes.value),
+                                          C.byref(handle)))
+        self._h = handle
+        n = C.c_int64()
+        _abi.check(L.sge_num_params(self._h, C.byref(n)))
+        self.n_params = int(n.value)
+
+    # ------------------------------------------------------------------ construction helpers
+    @classmethod
+    def from_arrays(cls, s, targets=None, **kw) -> "Scene":
+        """From any object with synth.Scene's attributes (numpy arrays)."""
+        return cls(s.positions, s.pos_idx, s.uvs, s.uv_idx, [(t.data, t.eps, t.role) for t in s.textures],
+                   s.eps_pos, s.mvp, s.cam_pos, s.width, s.height, targets=targets, near=s.near,
+                   shading=s.shading, light_dir=s.light_dir, light_rgb=s.light_rgb, ambient=s.ambient,
+                   background=s.background, **kw)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _abi.load().sge_destroy_scene(h)
+            except Exception:
+                pass
+            self._h = None
+
+    # ------------------------------------------------------------------ parameters
+    def param_groups(self) -> List:
+        return [self.positions] + [t[0] for t in self.textures]
+
+    def group_offsets(self) -> List[int]:
+        offs, o = [], 0
+        for g in self.param_groups():
+            offs.append(o)
+            o += g.numel()
+        return offs
+
+    def new_grad_buffers(self):
+        torch = _torch()
+        return (torch.zeros(self.n_params, dtype=torch.float32, device=self.device),
+                torch.zeros(self.n_params, dtype=torch.int32, device=self.device))
+
+    def set_targets(self, targets) -> None:
+        torch = _torch()
+        t = torch.as_tensor(targets).to(device=self.device, dtype=torch.float32).contiguous()
+        if tuple(t.shape) != (self.n_views, self.height, self.width, 3):
+            raise ValueError(f"targets must be [{self.n_views},{self.height},{self.width},3]")
+        self.targets = t
+        _abi.check(_abi.load().sge_set_targets(self._h, _ptr(t)))
+
+    # ------------------------------------------------------------------ calls
+    def validate(self, stream=None) -> int:
+        L = _abi.load()
+        _abi.check(L.sge_validate(self._h, _stream_ptr(stream)))
+        return self.status(stream)
+
+    def status(self, stream=None) -> int:
+        v = C.c_int32()
+        _abi.check(_abi.load().sge_status(self._h, _stream_ptr(stream), C.byref(v)))
+        return int(v.value)
+
+    def render_idb(self, view: int, seed: int = 0, it: int = 0, pair: int = 0, side: int = 0,
+                   keys=None, uv=None, rgb=None, stream=None):
+        """One render (Section 4.3 R): depth|ID [H,W] int64 (bit pattern of uint64), UV, RGB."""
+        torch = _torch()
+        H, W = self.height, self.width
+        keys = torch.empty(H, W, dtype=torch.int64, device=self.device) if keys is None else keys
+        uv = torch.empty(H, W, 2, dtype=torch.float32, device=self.device) if uv is None else uv
+        rgb = torch.empty(H, W, 3, dtype=torch.float32, device=self.device) if rgb is None else rgb
+        _abi.check(_abi.load().sge_render_idb(self._h, int(view), int(seed), int(it), int(pair), int(side),
+                                              _ptr(keys), _ptr(uv), _ptr(rgb), _stream_ptr(stream)))
+        return keys, uv, rgb
+
+    def render_targets(self, stream=None):
+        """Unperturbed renders of every view, [n_views,H,W,3] (e.g. of a target scene)."""
+        torch = _torch()
+        out = torch.empty(self.n_views, self.height, self.width, 3, dtype=torch.float32, device=self.device)
+        for v in range(self.n_views):
+            self.render_idb(v, side=0, rgb=out[v], stream=stream)
+        return out
+
+    @staticmethod
+    def _views(view_ids: Sequence[int]):
+        arr = (C.c_int32 * len(view_ids))(*[int(v) for v in view_ids])
+        return arr, len(view_ids)
+
+    def estimate_grad(self, seed: int, it: int, view_ids: Sequence[int], pairs_per_view: int, grad, counts,
+                      loss=None, delta_f=None, stream=None) -> None:
+        """Accumulate Eq. 9's numerators into grad [d] and counts [d] (batched, one launch)."""
+        arr, n = self._views(view_ids)
+        _abi.check(_abi.load().sge_estimate_grad(self._h, int(seed), int(it), arr, n, int(pairs_per_view),
+                                                 _ptr(grad), _ptr(counts), _ptr(loss), _ptr(delta_f),
+                                                 _stream_ptr(stream)))
+
+    def estimate_grad_plain(self, seed: int, it: int, view_ids: Sequence[int], pairs_per_view: int, grad,
+                            counts, loss=None, stream=None) -> None:
+        """Same sums, one estimate at a time with separate R and G launches (the baseline path)."""
+        arr, n = self._views(view_ids)
+        _abi.check(_abi.load().sge_estimate_grad_plain(self._h, int(seed), int(it), arr, n, int(pairs_per_view),
+                                                       _ptr(grad), _ptr(counts), _ptr(loss), _stream_ptr(stream)))
+
+    def step(self, kind: int, grad, counts, n_pairs_total: int, lr_pos: float, lr_tex: Sequence[float],
+             m=None, v=None, t: int = 1, beta1: float = 0.9, beta2: float = 0.999, adam_eps: float = 1e-8,
+             stream=None) -> None:
+        """Descent step D on every group (Section 5); zeroes grad and counts."""
+        o = _abi.Opt()
+        o.kind = int(kind)
+        o.lr_pos = float(lr_pos)
+        for k, lr in enumerate(lr_tex):
+            o.lr_tex[k] = float(lr)
+        o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), int(t)
+        _abi.check(_abi.load().sge_step(self._h, C.byref(o), _ptr(grad), _ptr(counts), int(n_pairs_total),
+                                        _ptr(m), _ptr(v), _stream_ptr(stream)))

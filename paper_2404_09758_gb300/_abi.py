@@ -1,0 +1,100 @@
+"""ctypes mirror of include/sge.h: structures, prototypes and the library loader.
+
+Argument marshalling only; every step of the method runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import _build
+
+MAX_TEXTURES = 8
+MAX_VIEWS_PER_CALL = 64
+
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_BIN_OVERFLOW, ERR_BAD_INDEX, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
+STEP_SGD, STEP_ADAM, STEP_SGD_MEAN = 0, 1, 2
+
+EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_targets", "sge_validate",
+           "sge_render_idb", "sge_estimate_grad", "sge_estimate_grad_plain", "sge_step", "sge_status",
+           "sge_destroy_scene", "sge_last_error")
+
+
+class Texture(C.Structure):
+    _fields_ = [("texels", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32),
+                ("channels", C.c_int32), ("eps", C.c_float), ("role", C.c_int32)]
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("positions", C.c_void_p), ("n_vertices", C.c_int32), ("eps_pos", C.c_float),
+                ("pos_idx", C.c_void_p), ("n_triangles", C.c_int32),
+                ("uvs", C.c_void_p), ("n_uvs", C.c_int32), ("uv_idx", C.c_void_p),
+                ("n_textures", C.c_int32), ("textures", Texture * MAX_TEXTURES),
+                ("mvp", C.c_void_p), ("cam_pos", C.c_void_p), ("n_views", C.c_int32),
+                ("width", C.c_int32), ("height", C.c_int32), ("near_w", C.c_float),
+                ("targets", C.c_void_p), ("background", C.c_float * 3), ("shading", C.c_int32),
+                ("light_dir", C.c_float * 3), ("light_rgb", C.c_float * 3), ("ambient", C.c_float)]
+
+
+class Config(C.Structure):
+    _fields_ = [("max_views_per_call", C.c_int32), ("bin_capacity", C.c_int64),
+                ("pairs_per_item", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+class Opt(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("lr_pos", C.c_float), ("lr_tex", C.c_float * MAX_TEXTURES),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("adam_eps", C.c_float), ("t", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SGEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sge error {code}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.OUT
+
+
+def load(build_if_missing: bool = False):
+    """Load libsge.so (never falls back to anything else: raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: build it with paper_2404_09758_gb300.build.build()")
+            _build.build()
+        L = C.CDLL(path)
+        P, I32, U32, U64, I64, SZ = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64, C.c_int64, C.c_size_t
+        L.sge_workspace_size.argtypes = [P, P, C.POINTER(SZ)]
+        L.sge_create_scene.argtypes = [P, P, P, SZ, C.POINTER(P)]
+        L.sge_num_params.argtypes = [P, C.POINTER(I64)]
+        L.sge_set_targets.argtypes = [P, P]
+        L.sge_validate.argtypes = [P, P]
+        L.sge_render_idb.argtypes = [P, I32, U64, U32, U32, I32, P, P, P, P]
+        L.sge_estimate_grad.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P, P]
+        L.sge_estimate_grad_plain.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P]
+        L.sge_step.argtypes = [P, P, P, P, I64, P, P, P]
+        L.sge_status.argtypes = [P, P, C.POINTER(I32)]
+        L.sge_destroy_scene.argtypes = [P]
+        L.sge_destroy_scene.restype = None
+        L.sge_last_error.argtypes = []
+        L.sge_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("sge_destroy_scene", "sge_last_error"):
+                getattr(L, name).restype = I32
+        _lib = L
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != OK:
+        raise SGEError(rc, load().sge_last_error().decode())

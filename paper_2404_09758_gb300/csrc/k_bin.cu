@@ -1,0 +1,167 @@
+// Tile binning shared by every pair and both sides of an estimate.
+//
+// The paper's rasterizer R (Section 4.3) renders theta + s eps and theta - s eps
+// for every estimate.  All those scenes differ from theta by at most eps_pos per
+// vertex coordinate, so one binning per view and call serves every render of
+// that view: each triangle is binned into the tiles its screen bounding box can
+// reach under any such perturbation (interval bounds of the projection plus a
+// one-pixel margin).  A render then tests, per tile, only the triangles in the
+// tile's bin, with the exact perturbed vertices.
+#include <cuda_runtime.h>
+
+#include "sge_device.cuh"
+
+namespace sge {
+
+namespace {
+
+// Interval of one clip coordinate row of M over the box p +- eps (per coordinate).
+__device__ __forceinline__ void clip_interval(const float* m, float x, float y, float z, float eps, float& lo,
+                                              float& hi) {
+  float c = m[0] * x + m[1] * y + m[2] * z + m[3];
+  float r = eps * (fabsf(m[0]) + fabsf(m[1]) + fabsf(m[2]));
+  r = r * 1.0001f + 1e-6f * (fabsf(c) + fabsf(m[3]) + 1.0f);
+  lo = c - r;
+  hi = c + r;
+}
+
+__global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
+  __shared__ float m[16];
+  int slot = blockIdx.y;
+  int view = vl.id[slot];
+  if (threadIdx.x < 16) m[threadIdx.x] = S.mvp[16 * view + threadIdx.x];
+  __syncthreads();
+  int tri = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tri >= S.nt) return;
+  int vi[3] = {__ldg(S.pidx + 3 * tri), __ldg(S.pidx + 3 * tri + 1), __ldg(S.pidx + 3 * tri + 2)};
+  int4 rect = make_int4(1, 1, 0, 0);  // empty
+  bool skip = vi[0] == vi[1] || vi[1] == vi[2] || vi[0] == vi[2];  // welded duplicates: zero area always
+  // a triangle with an index out of range is never binned, so no render reads through it
+  for (int k = 0; k < 3; ++k) {
+    const int ti = __ldg(S.uvidx + 3 * tri + k);
+    if (ti < 0 || ti >= S.nuv) skip = true;
+  }
+  float sx0 = 3.4e38f, sx1 = -3.4e38f, sy0 = 3.4e38f, sy1 = -3.4e38f;
+  bool full = false;
+  for (int k = 0; k < 3 && !skip; ++k) {
+    if (vi[k] < 0 || vi[k] >= S.nv) { skip = true; break; }
+    const float* p = S.pos + 3ll * vi[k];
+    float x = p[0], y = p[1], z = p[2];
+    float xl, xh, yl, yh, wl, wh;
+    clip_interval(m + 0, x, y, z, S.eps_pos, xl, xh);
+    clip_interval(m + 4, x, y, z, S.eps_pos, yl, yh);
+    clip_interval(m + 12, x, y, z, S.eps_pos, wl, wh);
+    if (wh <= S.near_w) { skip = true; break; }  // always behind the near limit: triangle never drawn
+    if (wl <= S.near_w) { full = true; continue; }  // may or may not be drawn: bin everywhere
+    float nx0 = fminf(fminf(xl / wl, xl / wh), fminf(xh / wl, xh / wh));
+    float nx1 = fmaxf(fmaxf(xl / wl, xl / wh), fmaxf(xh / wl, xh / wh));
+    float ny0 = fminf(fminf(yl / wl, yl / wh), fminf(yh / wl, yh / wh));
+    float ny1 = fmaxf(fmaxf(yl / wl, yl / wh), fmaxf(yh / wl, yh / wh));
+    sx0 = fminf(sx0, (nx0 * 0.5f + 0.5f) * S.W);
+    sx1 = fmaxf(sx1, (nx1 * 0.5f + 0.5f) * S.W);
+    sy0 = fminf(sy0, (0.5f - ny1 * 0.5f) * S.H);
+    sy1 = fmaxf(sy1, (0.5f - ny0 * 0.5f) * S.H);
+  }
+  if (!skip) {
+    int px0, px1, py0, py1;
+    if (full) {
+      px0 = 0; py0 = 0; px1 = S.W - 1; py1 = S.H - 1;
+    } else {
+      // pixel centres px + 0.5 inside [sx0, sx1], one pixel of margin each way
+      px0 = (int)fmaxf(floorf(sx0) - 1.0f, 0.0f);
+      py0 = (int)fmaxf(floorf(sy0) - 1.0f, 0.0f);
+      px1 = (int)fminf(floorf(sx1) + 1.0f, (float)(S.W - 1));
+      py1 = (int)fminf(floorf(sy1) + 1.0f, (float)(S.H - 1));
+    }
+    if (px0 <= px1 && py0 <= py1) rect = make_int4(px0 / TILE, py0 / TILE, px1 / TILE, py1 / TILE);
+  }
+  ws.tri_rect[(long long)slot * S.nt + tri] = rect;
+  int nt = n_tiles(S);
+  for (int ty = rect.y; ty <= rect.w; ++ty)
+    for (int tx = rect.x; tx <= rect.z; ++tx)
+      atomicAdd(ws.tile_count + (long long)slot * nt + ty * S.tiles_x + tx, 1u);
+}
+
+// One CTA: exclusive scan of the per-(slot, tile) counts, list of non-empty tiles,
+// fill cursors, and the estimate kernel's work counter.
+__global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt) {
+  __shared__ uint32_t wsum[32], wne[32];
+  int tid = threadIdx.x;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  int beg = min(n, tid * per), end = min(n, beg + per);
+  uint32_t sum = 0, ne = 0;
+  for (int i = beg; i < end; ++i) {
+    uint32_t c = ws.tile_count[i];
+    sum += c;
+    ne += c > 0;
+  }
+  // block exclusive scan of (sum, ne)
+  uint32_t xs = sum, xn = ne;
+  int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t a = __shfl_up_sync(0xffffffffu, xs, o), b = __shfl_up_sync(0xffffffffu, xn, o);
+    if (lane >= o) { xs += a; xn += b; }
+  }
+  if (lane == 31) { wsum[wid] = xs; wne[wid] = xn; }
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t a = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u, b = lane < (int)(blockDim.x >> 5) ? wne[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t pa = __shfl_up_sync(0xffffffffu, a, o), pb = __shfl_up_sync(0xffffffffu, b, o);
+      if (lane >= o) { a += pa; b += pb; }
+    }
+    wsum[lane] = a;
+    wne[lane] = b;
+  }
+  __syncthreads();
+  uint32_t off = (wid ? wsum[wid - 1] : 0u) + xs - sum;
+  uint32_t noff = (wid ? wne[wid - 1] : 0u) + xn - ne;
+  for (int i = beg; i < end; ++i) {
+    uint32_t c = ws.tile_count[i];
+    ws.tile_off[i] = off;
+    ws.tile_cur[i] = off;
+    if (c > 0) {
+      int slot = i / nt, tile = i - slot * nt;
+      ws.items[noff++] = ((uint32_t)slot << 24) | (uint32_t)tile;
+    }
+    off += c;
+  }
+  if (tid == blockDim.x - 1) {
+    ws.tile_off[n] = off;
+    bool overflow = (long long)off > ws.bin_capacity;
+    ws.counters[0] = overflow ? 0u : noff;
+    ws.counters[1] = 0u;
+    ws.counters[2] = off;
+    if (overflow) atomicCAS(ws.counters + 3, 0u, (uint32_t)SGE_ERR_BIN_OVERFLOW);
+  }
+}
+
+__global__ void k_bin_fill(SceneDev S, Workspace ws) {
+  int slot = blockIdx.y;
+  int tri = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tri >= S.nt) return;
+  int4 rect = ws.tri_rect[(long long)slot * S.nt + tri];
+  int nt = n_tiles(S);
+  for (int ty = rect.y; ty <= rect.w; ++ty)
+    for (int tx = rect.x; tx <= rect.z; ++tx) {
+      uint32_t pos = atomicAdd(ws.tile_cur + (long long)slot * nt + ty * S.tiles_x + tx, 1u);
+      if ((long long)pos < ws.bin_capacity) ws.bins[pos] = (uint32_t)tri;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st) {
+  int nt = n_tiles(S);
+  cudaError_t e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * (size_t)vl.n * nt, st);
+  if (e != cudaSuccess) return e;
+  dim3 grid((S.nt + 255) / 256, vl.n);
+  k_bin_rect_count<<<grid, 256, 0, st>>>(S, ws, vl);
+  k_bin_scan<<<1, 1024, 0, st>>>(ws, vl.n * nt, nt);
+  k_bin_fill<<<grid, 256, 0, st>>>(S, ws);
+  return cudaGetLastError();
+}
+
+}  // namespace sge

@@ -1,0 +1,354 @@
+// Fused, batched estimator: every estimate of one iteration (views x antithetic
+// pairs) in one persistent launch (Eq. 9, Algorithms 1-2, Section 4.3).
+//
+// Work item = (view, 16x16 tile, run of pairs).  A CTA owns one item at a time,
+// one thread per pixel, and for every pair of its run:
+//   P+R  perturbs and sets up, in shared memory, both sides' versions of the
+//        triangles binned to the tile (signs recomputed from the hash; nothing
+//        perturbed is ever stored in global memory), then each thread finds its
+//        pixel's visible triangle on both sides (64-bit depth|id minimum);
+//   G    shades both sides (UV buffer value, bilinear texels), forms
+//        f+ - f- = sum_c (I+_c - I-_c)(I+_c + I-_c - 2 I_c) and credits it to the
+//        union of both sides' contributing parameters.
+// Credits go to a shared-memory hash table keyed by vertex / texel.  Within a
+// pair all channels of a key share f+ - f- (only the sign s_i differs), so the
+// table accumulates A_key = sum_p (f+ - f-) and n_key per pair, and once per pair
+// folds s_i * A_key into per-channel sums.  At the end of the item each key
+// issues one global atomic per channel for the sum and the count.  A table that
+// fills up falls back to direct global atomics for the keys that do not fit.
+#include <cuda_runtime.h>
+
+#include "sge_device.cuh"
+
+namespace sge {
+
+namespace {
+
+constexpr int BIN_CHUNK = 256;     // triangles staged per pass (one per thread)
+constexpr int TABLE = 2048;        // hash-table slots (power of two)
+constexpr int MAX_PROBE = 32;
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+
+struct SideSmem {
+  long long e0[3][BIN_CHUNK];
+  int a[3][BIN_CHUNK], b[3][BIN_CHUNK];
+  int bias[BIN_CHUNK];  // bit k set: edge k is not top/left
+  float inv_area[BIN_CHUNK];
+  float z[3][BIN_CHUNK], iw[3][BIN_CHUNK];
+  int tri[BIN_CHUNK];  // -1 when not drawn on this side
+};
+
+struct TableSmem {
+  uint32_t key[TABLE];
+  float A[TABLE];
+  uint32_t n[TABLE];
+  float S[4][TABLE];
+  uint32_t cnt[TABLE];
+};
+
+struct Smem {
+  SideSmem side[2];
+  TableSmem tab;
+  float m[16];
+  float red[TILE_PX / 32];
+  uint32_t item;
+};
+
+__device__ __forceinline__ void store_tri(SideSmem& s, int j, const Tri& t, int tri) {
+  if (!t.ok) {
+    s.tri[j] = -1;
+    return;
+  }
+  int bias = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s.e0[k][j] = t.e0[k];
+    s.a[k][j] = t.a[k];
+    s.b[k][j] = t.b[k];
+    s.z[k][j] = t.z[k];
+    s.iw[k][j] = t.iw[k];
+    bias |= (t.bias[k] ? 1 : 0) << k;
+  }
+  s.bias[j] = bias;
+  s.inv_area[j] = t.inv_area;
+  s.tri[j] = tri;
+}
+
+__device__ __forceinline__ void load_tri(const SideSmem& s, int j, Tri& t) {
+  int bias = s.bias[j];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    t.e0[k] = s.e0[k][j];
+    t.a[k] = s.a[k][j];
+    t.b[k] = s.b[k][j];
+    t.z[k] = s.z[k][j];
+    t.iw[k] = s.iw[k][j];
+    t.bias[k] = (bias >> k) & 1 ? -1 : 0;
+  }
+  t.inv_area = s.inv_area[j];
+  t.ok = 1;
+}
+
+// Coverage + depth of staged triangle j at pixel offset (dx, dy); returns the key or ~0.
+__device__ __forceinline__ unsigned long long test_key(const SideSmem& s, int j, int dx, int dy) {
+  int tri = s.tri[j];
+  if (tri < 0) return ~0ull;
+  int bias = s.bias[j];
+  long long e[3];
+  bool in = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    e[k] = s.e0[k][j] + (long long)s.a[k][j] * (dx * 256) + (long long)s.b[k][j] * (dy * 256);
+    in = in && (e[k] - ((bias >> k) & 1) >= 0);
+  }
+  if (!in) return ~0ull;
+  float l[3], z[3] = {s.z[0][j], s.z[1][j], s.z[2][j]};
+  lambdas(e, s.inv_area[j], l);
+  float d = interp_depth(l, z);
+  return ((unsigned long long)ordered_bits(d) << 32) | (uint32_t)tri;
+}
+
+__device__ __forceinline__ uint32_t slot_hash(uint32_t k) {
+  k ^= k >> 16;
+  k *= 0x7feb352du;
+  k ^= k >> 15;
+  return k & (TABLE - 1);
+}
+
+// Credit df to key: shared-memory table, or global atomics when the table is full.
+__device__ __forceinline__ void credit(const SceneDev& S, TableSmem& tb, uint32_t key, float df, uint64_t pkey,
+                                       float* grad, uint32_t* counts) {
+  uint32_t slot = slot_hash(key);
+#pragma unroll 1
+  for (int p = 0; p < MAX_PROBE; ++p) {
+    uint32_t k = *(volatile uint32_t*)&tb.key[slot];
+    if (k == EMPTY) k = atomicCAS(&tb.key[slot], EMPTY, key), k = (k == EMPTY) ? key : k;
+    if (k == key) {
+      atomicAdd(&tb.A[slot], df);
+      atomicAdd(&tb.n[slot], 1u);
+      return;
+    }
+    slot = (slot + 1) & (TABLE - 1);
+  }
+  long long base;
+  int nch;
+  key_params(S, key, base, nch);
+  for (int c = 0; c < nch; ++c) {
+    bool neg = sign_neg(pkey, (uint64_t)(base + c));
+    atomicAdd(grad + base + c, neg ? -df : df);
+    atomicAdd(counts + base + c, 1u);
+  }
+}
+
+// Fold the pair's per-key sums into the per-channel accumulators (signs of this pair).
+__device__ __forceinline__ void fold(const SceneDev& S, TableSmem& tb, uint64_t pkey) {
+  for (int slot = threadIdx.x; slot < TABLE; slot += blockDim.x) {
+    uint32_t key = tb.key[slot];
+    if (key == EMPTY) continue;
+    uint32_t nn = tb.n[slot];
+    if (nn == 0) continue;
+    float A = tb.A[slot];
+    long long base;
+    int nch;
+    key_params(S, key, base, nch);
+    for (int c = 0; c < nch; ++c) tb.S[c][slot] += sign_neg(pkey, (uint64_t)(base + c)) ? -A : A;
+    tb.cnt[slot] += nn;
+    tb.A[slot] = 0.0f;
+    tb.n[slot] = 0u;
+  }
+}
+
+__device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem& tb, float* grad, uint32_t* counts) {
+  for (int slot = threadIdx.x; slot < TABLE; slot += blockDim.x) {
+    uint32_t key = tb.key[slot];
+    if (key != EMPTY) {
+      long long base;
+      int nch;
+      key_params(S, key, base, nch);
+      uint32_t cn = tb.cnt[slot];
+      for (int c = 0; c < nch; ++c) {
+        atomicAdd(grad + base + c, tb.S[c][slot]);
+        if (cn) atomicAdd(counts + base + c, cn);
+      }
+    }
+    tb.key[slot] = EMPTY;
+    tb.A[slot] = 0.0f;
+    tb.n[slot] = 0u;
+    tb.cnt[slot] = 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tb.S[c][slot] = 0.0f;
+  }
+}
+
+__global__ void __launch_bounds__(TILE_PX) k_estimate(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int dx = tid % TILE, dy = tid / TILE;
+  const int ntl = n_tiles(S);
+  const int n_chunks = (a.pairs + a.pairs_per_item - 1) / a.pairs_per_item;
+  const long long n_work = (long long)ws.counters[0] * n_chunks;
+
+  for (int s = tid; s < TABLE; s += blockDim.x) {
+    sm.tab.key[s] = EMPTY;
+    sm.tab.A[s] = 0.0f;
+    sm.tab.n[s] = 0u;
+    sm.tab.cnt[s] = 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm.tab.S[c][s] = 0.0f;
+  }
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) sm.item = atomicAdd(ws.counters + 1, 1u);
+    __syncthreads();
+    const long long w = sm.item;
+    if (w >= n_work) break;
+    const uint32_t it = ws.items[w / n_chunks];
+    const int chunk = (int)(w % n_chunks);
+    const int slot = it >> 24, tile = it & 0xFFFFFF;
+    const int view = vl.id[slot];
+    const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+    const int px = tx * TILE + dx, py = ty * TILE + dy;
+    const bool valid = px < S.W && py < S.H;
+    const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
+    const uint32_t bin_beg = ws.tile_off[slot * ntl + tile];
+    const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - bin_beg);
+    const int p0 = chunk * a.pairs_per_item, p1 = min(a.pairs, p0 + a.pairs_per_item);
+    if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
+    float3 tgt = f3(0.f, 0.f, 0.f);
+    if (valid) {
+      const float* tp = S.targets + (((long long)view * S.H + py) * S.W + px) * 3;
+      tgt = f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
+    }
+    float loss_acc = 0.0f;
+
+    for (int pair = p0; pair < p1; ++pair) {
+      const uint64_t pkey = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)pair);
+      unsigned long long best[2] = {~0ull, ~0ull};
+      int bestj[2] = {-1, -1}, bestc[2] = {-1, -1};
+      int last_c = 0;
+      for (int c0 = 0; c0 < nb; c0 += BIN_CHUNK) {
+        const int cnt = min(BIN_CHUNK, nb - c0);
+        __syncthreads();
+        if (tid < cnt) {
+          const int tri = (int)ws.bins[bin_beg + c0 + tid];
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            Tri t;
+            setup_from_scene(S, sm.m, tri, pkey, sd == 0 ? 1 : -1, rx, ry, t);
+            store_tri(sm.side[sd], tid, t, tri);
+          }
+        }
+        __syncthreads();
+        for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            unsigned long long k = test_key(sm.side[sd], j, dx, dy);
+            if (k < best[sd]) {
+              best[sd] = k;
+              bestj[sd] = j;
+              bestc[sd] = c0;
+            }
+          }
+        }
+        last_c = c0;
+      }
+
+      // ---- G: shade both sides, loss difference, credits
+      Surf sf[2];
+      int tris[2] = {-1, -1};
+      float3 col[2];
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        col[sd] = f3(S.bg[0], S.bg[1], S.bg[2]);
+        if (!valid || best[sd] == ~0ull) continue;
+        const int tri = (int)(best[sd] & 0xFFFFFFFFu);
+        const int side = sd == 0 ? 1 : -1;
+        Tri t;
+        if (bestc[sd] == last_c) load_tri(sm.side[sd], bestj[sd], t);
+        else setup_from_scene(S, sm.m, tri, pkey, side, rx, ry, t);
+        long long e[3];
+        cover(t, dx, dy, e);
+        surface(S, view, tri, t, e, pkey, side, sf[sd]);
+        col[sd] = sf[sd].rgb;
+        tris[sd] = tri;
+      }
+      float df = 0.0f;
+      if (valid) {
+        float fp, fm;
+        df = loss_diff(col[0], col[1], tgt, fp, fm);
+        loss_acc += 0.5f * (fp + fm);
+        if (a.delta_f) a.delta_f[(((long long)slot * a.pairs + pair) * S.H + py) * S.W + px] = df;
+        Foot foot[2][MAX_READ];
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd)
+#pragma unroll
+          for (int r = 0; r < MAX_READ; ++r) foot[sd][r] = sf[sd].foot[r];
+        for_each_contrib(S, tris, foot, [&](uint32_t key) { credit(S, sm.tab, key, df, pkey, a.grad, a.counts); });
+      }
+      __syncthreads();
+      fold(S, sm.tab, pkey);
+    }
+    __syncthreads();
+    flush_and_clear(S, sm.tab, a.grad, a.counts);
+    if (a.loss) {
+      float v = loss_acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) sm.red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        float sum = 0.0f;
+        for (int i = 0; i < TILE_PX / 32; ++i) sum += sm.red[i];
+        atomicAdd(a.loss + slot, sum / (float)a.pairs);
+      }
+    }
+  }
+}
+
+// Loss of pixels in tiles no triangle can reach: the background on both sides.
+__global__ void k_background_loss(SceneDev S, Workspace ws, ViewList vl, float* loss) {
+  const int slot = blockIdx.y, tile = blockIdx.x;
+  const int ntl = n_tiles(S);
+  if (ws.tile_count[slot * ntl + tile] != 0) return;
+  const int view = vl.id[slot];
+  const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+  const int px = tx * TILE + threadIdx.x % TILE, py = ty * TILE + threadIdx.x / TILE;
+  float v = 0.0f;
+  if (px < S.W && py < S.H) {
+    const float* tp = S.targets + (((long long)view * S.H + py) * S.W + px) * 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float d = S.bg[c] - tp[c];
+      v += d * d;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(loss + slot, v);
+}
+
+}  // namespace
+
+int estimate_blocks_per_sm() {
+  static int cached = -1;
+  if (cached < 0) {
+    int n = 0;
+    cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate, TILE_PX, sizeof(Smem));
+    cached = n > 0 ? n : 1;
+  }
+  return cached;
+}
+
+cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
+                            int grid, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  k_estimate<<<grid, TILE_PX, sizeof(Smem), st>>>(S, ws, vl, a);
+  if (a.loss) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);
+  return cudaGetLastError();
+}
+
+}  // namespace sge

@@ -1,0 +1,81 @@
+// Descent step D (Section 5): gradient estimate of Eq. 9 from the accumulated
+// sums, SGD or Adam (Kingma & Ba 2015) per parameter, then the sums and counts
+// are zeroed for the next iteration.  One thread per parameter; memory bound.
+#include <cuda_runtime.h>
+
+#include "sge_internal.h"
+
+namespace sge {
+
+namespace {
+
+struct StepGroups {
+  int n;
+  long long begin[SGE_MAX_TEXTURES + 2];  // flat parameter index where each group starts (+ end)
+  float* theta[SGE_MAX_TEXTURES + 1];
+  float eps[SGE_MAX_TEXTURES + 1];
+  float lr[SGE_MAX_TEXTURES + 1];
+};
+
+__global__ void k_step(StepGroups G, int kind, float* grad, uint32_t* counts, float inv_n, float b1, float b2,
+                       float c1, float c2, float aeps, float* m, float* v) {
+  const long long d = G.begin[G.n];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (long long)gridDim.x * blockDim.x) {
+    int g = 0;
+#pragma unroll 1
+    while (g + 1 < G.n && i >= G.begin[g + 1]) ++g;
+    const long long li = i - G.begin[g];
+    const float s = grad[i];
+    const uint32_t cn = counts[i];
+    const float scale = kind == SGE_STEP_SGD_MEAN ? 1.0f / (float)(cn > 0 ? cn : 1u) : inv_n;
+    const float gr = s * scale / (2.0f * G.eps[g]);
+    float th = G.theta[g][li];
+    if (kind == SGE_STEP_ADAM) {
+      const float mm = b1 * m[i] + (1.0f - b1) * gr;
+      const float vv = b2 * v[i] + (1.0f - b2) * gr * gr;
+      m[i] = mm;
+      v[i] = vv;
+      th -= G.lr[g] * (mm / c1) / (sqrtf(vv / c2) + aeps);
+    } else {
+      th -= G.lr[g] * gr;
+    }
+    G.theta[g][li] = th;
+    grad[i] = 0.0f;
+    counts[i] = 0u;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32_t* counts, long long n_total,
+                        float* m, float* v, cudaStream_t st) {
+  StepGroups G;
+  G.n = 1 + S.ntex;
+  G.begin[0] = 0;
+  G.theta[0] = const_cast<float*>(S.pos);
+  G.eps[0] = S.eps_pos;
+  G.lr[0] = o.lr_pos;
+  for (int k = 0; k < S.ntex; ++k) {
+    G.begin[k + 1] = S.tex[k].offset;
+    G.theta[k + 1] = const_cast<float*>(S.tex[k].ptr);
+    G.eps[k + 1] = S.tex[k].eps;
+    G.lr[k + 1] = o.lr_tex[k];
+  }
+  G.begin[G.n] = S.n_params;
+  double c1 = 1.0, c2 = 1.0;
+  if (o.kind == SGE_STEP_ADAM) {
+    c1 = 1.0 - pow((double)o.beta1, (double)o.t);
+    c2 = 1.0 - pow((double)o.beta2, (double)o.t);
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (S.n_params + 255) / 256;
+  if (blocks > 8ll * sms) blocks = 8ll * sms;
+  if (blocks < 1) blocks = 1;
+  k_step<<<(unsigned)blocks, 256, 0, st>>>(G, o.kind, grad, counts, (float)(1.0 / (double)n_total), o.beta1,
+                                           o.beta2, (float)c1, (float)c2, o.adam_eps, m, v);
+  return cudaGetLastError();
+}
+
+}  // namespace sge

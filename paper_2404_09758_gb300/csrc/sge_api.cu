@@ -1,0 +1,336 @@
+// The C ABI of include/sge.h: argument checks, workspace layout and launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "sge_device.cuh"
+
+using namespace sge;
+
+struct sge_scene {
+  sge_scene_desc desc;
+  sge_config cfg;
+  SceneDev dev;
+  Workspace ws;
+  int grid;  // persistent CTAs of the estimate kernel
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SGE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t tri_rect, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf, total;
+  int max_views;
+  long long bin_capacity;
+};
+
+int tiles_of(int n) { return (n + TILE - 1) / TILE; }
+
+int check_desc(const sge_scene_desc* d) {
+  if (!d) return fail(SGE_ERR_INVALID_ARG, "desc is NULL");
+  if (!d->positions || !d->pos_idx || !d->uvs || !d->uv_idx || !d->mvp || !d->targets)
+    return fail(SGE_ERR_INVALID_ARG, "positions, pos_idx, uvs, uv_idx, mvp and targets must be non-NULL");
+  if (d->n_vertices < 3 || d->n_vertices >= (1 << 28)) return fail(SGE_ERR_INVALID_ARG, "n_vertices %d out of [3, 2^28)", d->n_vertices);
+  if (d->n_triangles < 1) return fail(SGE_ERR_INVALID_ARG, "n_triangles must be >= 1");
+  if (d->n_uvs < 1) return fail(SGE_ERR_INVALID_ARG, "n_uvs must be >= 1");
+  if (d->n_views < 1) return fail(SGE_ERR_INVALID_ARG, "n_views must be >= 1");
+  if (d->width < 1 || d->height < 1 || d->width > 16384 || d->height > 16384)
+    return fail(SGE_ERR_INVALID_ARG, "render size %dx%d out of [1, 16384]", d->width, d->height);
+  if (!(d->eps_pos >= 0.0f) || !std::isfinite(d->eps_pos)) return fail(SGE_ERR_INVALID_ARG, "eps_pos must be finite and >= 0");
+  if (!(d->near_w > 0.0f)) return fail(SGE_ERR_INVALID_ARG, "near_w must be > 0");
+  if (d->shading < SGE_SHADE_UNLIT || d->shading > SGE_SHADE_GGX) return fail(SGE_ERR_INVALID_ARG, "bad shading %d", d->shading);
+  if (d->shading == SGE_SHADE_GGX && !d->cam_pos) return fail(SGE_ERR_INVALID_ARG, "GGX shading needs cam_pos");
+  if (d->n_textures < 0 || d->n_textures > SGE_MAX_TEXTURES) return fail(SGE_ERR_INVALID_ARG, "n_textures %d out of [0, %d]", d->n_textures, SGE_MAX_TEXTURES);
+  for (int k = 0; k < d->n_textures; ++k) {
+    const sge_texture& t = d->textures[k];
+    if (!t.texels) return fail(SGE_ERR_INVALID_ARG, "texture %d has NULL texels", k);
+    if (t.width < 1 || t.height < 1 || (long long)t.width * t.height >= (1ll << 28))
+      return fail(SGE_ERR_INVALID_ARG, "texture %d size %dx%d out of range", k, t.width, t.height);
+    if (t.channels < 1 || t.channels > 4) return fail(SGE_ERR_INVALID_ARG, "texture %d channels %d not in 1..4", k, t.channels);
+    if (t.role < SGE_ROLE_ALBEDO || t.role > SGE_ROLE_METALLIC) return fail(SGE_ERR_INVALID_ARG, "texture %d bad role", k);
+    if (!(t.eps >= 0.0f) || !std::isfinite(t.eps)) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be finite and >= 0", k);
+  }
+  return SGE_OK;
+}
+
+int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
+  L.max_views = (c && c->max_views_per_call > 0) ? c->max_views_per_call : d->n_views;
+  if (L.max_views > SGE_MAX_VIEWS_PER_CALL) L.max_views = SGE_MAX_VIEWS_PER_CALL;
+  const long long ntl = (long long)tiles_of(d->width) * tiles_of(d->height);
+  L.bin_capacity = (c && c->bin_capacity > 0) ? c->bin_capacity
+                                               : (6ll * d->n_triangles + ntl) * (long long)L.max_views;
+  if (L.bin_capacity >= (1ll << 32)) return fail(SGE_ERR_INVALID_ARG, "bin_capacity must be < 2^32");
+  const long long npx = (long long)d->width * d->height;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+  L.tri_rect = take(sizeof(int4) * (size_t)L.max_views * d->n_triangles);
+  L.tile_count = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
+  L.tile_off = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl + 1));
+  L.tile_cur = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
+  L.bins = take(sizeof(uint32_t) * (size_t)L.bin_capacity);
+  L.items = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
+  L.counters = take(64);
+  L.keys = take(sizeof(unsigned long long) * 2 * (size_t)npx);
+  L.uvbuf = take(sizeof(float2) * 2 * (size_t)npx);
+  L.dfbuf = take(sizeof(float) * (size_t)npx);
+  L.total = o;
+  return SGE_OK;
+}
+
+void make_dev(const sge_scene_desc* d, SceneDev& S) {
+  memset(&S, 0, sizeof(S));
+  S.pos = d->positions;
+  S.nv = d->n_vertices;
+  S.eps_pos = d->eps_pos;
+  S.pidx = d->pos_idx;
+  S.nt = d->n_triangles;
+  S.uvs = d->uvs;
+  S.uvidx = d->uv_idx;
+  S.nuv = d->n_uvs;
+  S.ntex = d->n_textures;
+  long long off = 3ll * d->n_vertices;
+  int first_of_role[4] = {-1, -1, -1, -1};
+  for (int k = 0; k < d->n_textures; ++k) {
+    const sge_texture& t = d->textures[k];
+    TexDev& T = S.tex[k];
+    T.ptr = t.texels;
+    T.w = t.width;
+    T.h = t.height;
+    T.c = t.channels;
+    T.eps = t.eps;
+    T.role = t.role;
+    T.offset = off;
+    off += (long long)t.width * t.height * t.channels;
+    if (first_of_role[t.role] < 0) first_of_role[t.role] = k;
+  }
+  S.n_params = off;
+  for (int k = 0; k < d->n_textures; ++k) {
+    const int role = d->textures[k].role;
+    bool read = first_of_role[role] == k &&
+                (d->shading == SGE_SHADE_GGX || role == SGE_ROLE_ALBEDO ||
+                 (d->shading == SGE_SHADE_LAMBERT && role == SGE_ROLE_NORMAL));
+    S.tex[k].read = read;
+    if (read) S.read_k[S.nread++] = k;
+  }
+  S.mvp = d->mvp;
+  S.cam_pos = d->cam_pos;
+  S.nviews = d->n_views;
+  S.W = d->width;
+  S.H = d->height;
+  S.near_w = d->near_w;
+  S.targets = d->targets;
+  for (int c = 0; c < 3; ++c) {
+    S.bg[c] = d->background[c];
+    S.light_dir[c] = d->light_dir[c];
+    S.light_rgb[c] = d->light_rgb[c];
+  }
+  S.shading = d->shading;
+  S.ambient = d->ambient;
+  S.tiles_x = tiles_of(d->width);
+  S.tiles_y = tiles_of(d->height);
+}
+
+int views_of(const sge_scene* s, const int32_t* view_ids, int32_t n, ViewList& vl) {
+  if (!view_ids) return fail(SGE_ERR_INVALID_ARG, "view_ids is NULL");
+  if (n < 1 || n > s->ws.max_views)
+    return fail(SGE_ERR_INVALID_ARG, "n_views %d out of [1, %d] (max_views_per_call)", n, s->ws.max_views);
+  vl.n = n;
+  for (int i = 0; i < n; ++i) {
+    if (view_ids[i] < 0 || view_ids[i] >= s->desc.n_views)
+      return fail(SGE_ERR_INVALID_ARG, "view_ids[%d] = %d out of [0, %d)", i, view_ids[i], s->desc.n_views);
+    for (int j = 0; j < i; ++j)
+      if (view_ids[j] == view_ids[i]) return fail(SGE_ERR_INVALID_ARG, "view %d listed twice", view_ids[i]);
+    vl.id[i] = view_ids[i];
+  }
+  return SGE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sge_last_error(void) { return g_err; }
+
+int sge_workspace_size(const sge_scene_desc* desc, const sge_config* cfg, size_t* bytes) {
+  if (!bytes) return fail(SGE_ERR_INVALID_ARG, "bytes is NULL");
+  int rc = check_desc(desc);
+  if (rc) return rc;
+  Layout L;
+  rc = make_layout(desc, cfg, L);
+  if (rc) return rc;
+  *bytes = L.total;
+  return SGE_OK;
+}
+
+int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* workspace, size_t workspace_bytes,
+                     sge_scene** out) {
+  if (!out) return fail(SGE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int rc = check_desc(desc);
+  if (rc) return rc;
+  Layout L;
+  rc = make_layout(desc, cfg, L);
+  if (rc) return rc;
+  if (!workspace) return fail(SGE_ERR_WORKSPACE, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(SGE_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  if (workspace_bytes < L.total)
+    return fail(SGE_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", workspace_bytes, L.total);
+  sge_scene* s = new (std::nothrow) sge_scene;
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "out of host memory");
+  s->desc = *desc;
+  s->cfg = cfg ? *cfg : sge_config{};
+  make_dev(desc, s->dev);
+  char* base = static_cast<char*>(workspace);
+  Workspace& w = s->ws;
+  w.tri_rect = reinterpret_cast<int4*>(base + L.tri_rect);
+  w.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
+  w.tile_off = reinterpret_cast<uint32_t*>(base + L.tile_off);
+  w.tile_cur = reinterpret_cast<uint32_t*>(base + L.tile_cur);
+  w.bins = reinterpret_cast<uint32_t*>(base + L.bins);
+  w.items = reinterpret_cast<uint32_t*>(base + L.items);
+  w.counters = reinterpret_cast<uint32_t*>(base + L.counters);
+  w.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
+  w.uvbuf = reinterpret_cast<float2*>(base + L.uvbuf);
+  w.dfbuf = reinterpret_cast<float*>(base + L.dfbuf);
+  w.bin_capacity = L.bin_capacity;
+  w.max_views = L.max_views;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMemset(w.counters, 0, 64);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "sge_create_scene");
+  }
+  int bps = (s->cfg.blocks_per_sm > 0) ? s->cfg.blocks_per_sm : estimate_blocks_per_sm();
+  s->grid = sms * bps;
+  if (s->cfg.pairs_per_item <= 0) s->cfg.pairs_per_item = 16;
+  *out = s;
+  return SGE_OK;
+}
+
+int sge_num_params(const sge_scene* s, int64_t* d) {
+  if (!s || !d) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  *d = s->dev.n_params;
+  return SGE_OK;
+}
+
+int sge_set_targets(sge_scene* s, const float* targets) {
+  if (!s || !targets) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  s->desc.targets = targets;
+  s->dev.targets = targets;
+  return SGE_OK;
+}
+
+int sge_validate(sge_scene* s, sge_stream_t stream) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  cudaError_t e = launch_validate(s->dev, s->ws.counters + 3, (cudaStream_t)stream);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_validate");
+}
+
+int sge_render_idb(sge_scene* s, int32_t view, uint64_t seed, uint32_t iter, uint32_t pair, int32_t side,
+                   uint64_t* depth_id, float* uv, float* rgb, sge_stream_t stream) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  if (side < -1 || side > 1) return fail(SGE_ERR_INVALID_ARG, "side %d not in {-1, 0, 1}", side);
+  ViewList vl;
+  int rc = views_of(s, &view, 1, vl);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_binning(s->dev, s->ws, vl, st);
+  if (e == cudaSuccess)
+    e = launch_render(s->dev, s->ws, 0, view, pair_key(seed, iter, (uint32_t)view, pair), side,
+                      reinterpret_cast<unsigned long long*>(depth_id), reinterpret_cast<float2*>(uv), rgb, st);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_render_idb");
+}
+
+int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids, int32_t n_views,
+                      int32_t pairs_per_view, float* grad_sums, uint32_t* counts, float* loss_out, float* delta_f_out,
+                      sge_stream_t stream) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  if (!grad_sums || !counts) return fail(SGE_ERR_INVALID_ARG, "grad_sums and counts must be non-NULL");
+  if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
+  ViewList vl;
+  int rc = views_of(s, view_ids, n_views, vl);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  EstimateArgs a{seed, iter, pairs_per_view, s->cfg.pairs_per_item, grad_sums, counts, loss_out, delta_f_out};
+  cudaError_t e = cudaSuccess;
+  if (delta_f_out)
+    e = cudaMemsetAsync(delta_f_out, 0, sizeof(float) * (size_t)n_views * pairs_per_view * s->dev.W * s->dev.H, st);
+  if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
+  if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, a, s->grid, st);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
+}
+
+int sge_estimate_grad_plain(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids, int32_t n_views,
+                            int32_t pairs_per_view, float* grad_sums, uint32_t* counts, float* loss_out,
+                            sge_stream_t stream) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  if (!grad_sums || !counts) return fail(SGE_ERR_INVALID_ARG, "grad_sums and counts must be non-NULL");
+  if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
+  ViewList vl;
+  int rc = views_of(s, view_ids, n_views, vl);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  EstimateArgs a{seed, iter, pairs_per_view, 1, grad_sums, counts, loss_out, nullptr};
+  cudaError_t e = launch_binning(s->dev, s->ws, vl, st);
+  for (int j = 0; j < n_views && e == cudaSuccess; ++j)
+    for (int n = 0; n < pairs_per_view && e == cudaSuccess; ++n)
+      e = launch_plain_pair(s->dev, s->ws, j, vl.id[j], pair_key(seed, iter, (uint32_t)vl.id[j], (uint32_t)n), a,
+                            1.0f / (float)pairs_per_view, st);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad_plain");
+}
+
+int sge_step(sge_scene* s, const sge_opt* o, float* grad_sums, uint32_t* counts, int64_t n_pairs_total, float* adam_m,
+             float* adam_v, sge_stream_t stream) {
+  if (!s || !o) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  if (!grad_sums || !counts) return fail(SGE_ERR_INVALID_ARG, "grad_sums and counts must be non-NULL");
+  if (o->kind < SGE_STEP_SGD || o->kind > SGE_STEP_SGD_MEAN) return fail(SGE_ERR_INVALID_ARG, "bad step kind %d", o->kind);
+  if (o->kind != SGE_STEP_SGD_MEAN && n_pairs_total < 1) return fail(SGE_ERR_INVALID_ARG, "n_pairs_total must be >= 1");
+  if (o->kind == SGE_STEP_ADAM) {
+    if (!adam_m || !adam_v) return fail(SGE_ERR_INVALID_ARG, "Adam needs m and v");
+    if (o->t < 1) return fail(SGE_ERR_INVALID_ARG, "Adam step t must be >= 1");
+  }
+  if (s->desc.eps_pos <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "eps_pos must be > 0 to form Eq. 9's estimate");
+  for (int k = 0; k < s->dev.ntex; ++k)
+    if (s->dev.tex[k].eps <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be > 0 to step", k);
+  cudaError_t e = launch_step(s->dev, *o, grad_sums, counts, n_pairs_total > 0 ? n_pairs_total : 1, adam_m, adam_v,
+                              (cudaStream_t)stream);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_step");
+}
+
+int sge_status(sge_scene* s, sge_stream_t stream, int32_t* device_status) {
+  if (!s || !device_status) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  uint32_t v = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(&v, s->ws.counters + 3, sizeof(v), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->ws.counters + 3, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sge_status");
+  *device_status = (int32_t)v;
+  return SGE_OK;
+}
+
+void sge_destroy_scene(sge_scene* s) { delete s; }
+
+}  // extern "C"

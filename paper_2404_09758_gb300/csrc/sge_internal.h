@@ -1,0 +1,109 @@
+// Internal types shared by the host API and the kernels (not part of the C ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sge.h"
+
+namespace sge {
+
+constexpr int SGE_MAX_TEX_DEV = SGE_MAX_TEXTURES;
+constexpr int MAX_READ = 4;              // albedo, normal, roughness, metallic
+constexpr int TILE = 16;                 // tile edge in pixels; one CTA thread per pixel
+constexpr int TILE_PX = TILE * TILE;     // 256 threads
+constexpr int ROLE_ALBEDO = SGE_ROLE_ALBEDO, ROLE_NORMAL = SGE_ROLE_NORMAL;
+constexpr int ROLE_ROUGHNESS = SGE_ROLE_ROUGHNESS, ROLE_METALLIC = SGE_ROLE_METALLIC;
+constexpr int SHADE_UNLIT = SGE_SHADE_UNLIT, SHADE_LAMBERT = SGE_SHADE_LAMBERT, SHADE_GGX = SGE_SHADE_GGX;
+
+struct TexDev {
+  const float* ptr;
+  int w, h, c;
+  float eps;
+  int role;
+  int read;          // does the shading model read this texture (so its texels contribute)?
+  long long offset;  // first parameter index of this texture in theta
+};
+
+// Device view of a scene, passed to kernels by value.
+struct SceneDev {
+  const float* pos;
+  int nv;
+  float eps_pos;
+  const int* pidx;
+  int nt;
+  const float* uvs;
+  const int* uvidx;
+  int nuv;
+  int ntex;
+  TexDev tex[SGE_MAX_TEX_DEV];
+  int nread;                 // textures the shading model reads (at most one per role)
+  int read_k[MAX_READ];      // their indices in tex[]
+  const float* mvp;
+  const float* cam_pos;
+  int nviews;
+  int W, H;
+  float near_w;
+  const float* targets;
+  float bg[3];
+  int shading;
+  float light_dir[3], light_rgb[3], ambient;
+  long long n_params;
+  int tiles_x, tiles_y;
+};
+
+// Views of one estimate call, by value (graph capture bakes them in).
+struct ViewList {
+  int n;
+  int id[SGE_MAX_VIEWS_PER_CALL];
+};
+
+// Scratch carved out of the caller's workspace.
+struct Workspace {
+  int4* tri_rect;        // [max_views][nt] tile rectangle (x0,y0,x1,y1) of each triangle's bin span
+  uint32_t* tile_count;  // [max_views][n_tiles]
+  uint32_t* tile_off;    // [max_views][n_tiles + 1] exclusive scan of counts
+  uint32_t* tile_cur;    // [max_views][n_tiles] fill cursors
+  uint32_t* bins;        // [bin_capacity] triangle ids grouped by (view slot, tile)
+  uint32_t* items;       // [max_views * n_tiles] non-empty (view slot << 24 | tile)
+  uint32_t* counters;    // [0] n_items, [1] work counter, [2] total bin entries, [3] status
+  unsigned long long* keys;  // [2][H*W] staged depth|ID buffers (both sides)
+  float2* uvbuf;             // [2][H*W] staged UV buffers
+  float* dfbuf;              // [H*W] staged loss differences
+  long long bin_capacity;
+  int max_views;
+};
+
+// ---- kernels launchers (all asynchronous on `st`)
+// Tile binning of every triangle for each view of `vl`, conservative for any
+// perturbation of at most eps_pos per coordinate.  Fills ws bins / items.
+cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st);
+
+struct EstimateArgs {
+  uint64_t seed;
+  uint32_t iter;
+  int pairs;
+  int pairs_per_item;
+  float* grad;
+  uint32_t* counts;
+  float* loss;
+  float* delta_f;
+};
+cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl,
+                            const EstimateArgs& a, int grid, cudaStream_t st);
+int estimate_blocks_per_sm();
+
+// Staged path: render one side of one estimate into keys/uv/rgb.
+cudaError_t launch_render(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key,
+                          int side, unsigned long long* keys, float2* uv, float* rgb, cudaStream_t st);
+// Staged path: loss differences and scatter of one estimate from both sides' buffers.
+cudaError_t launch_plain_pair(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key,
+                              const EstimateArgs& a, float loss_scale, cudaStream_t st);
+
+cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32_t* counts,
+                        long long n_total, float* m, float* v, cudaStream_t st);
+cudaError_t launch_validate(const SceneDev& S, uint32_t* status, cudaStream_t st);
+
+__host__ __device__ inline int n_tiles(const SceneDev& S) { return S.tiles_x * S.tiles_y; }
+
+}  // namespace sge
