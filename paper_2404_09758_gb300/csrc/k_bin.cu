@@ -42,6 +42,7 @@ __global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
     if (ti < 0 || ti >= S.nuv) skip = true;
   }
   float sx0 = 3.4e38f, sx1 = -3.4e38f, sy0 = 3.4e38f, sy1 = -3.4e38f;
+  float disp = 0.0f;  // widest screen interval of a vertex under the perturbation, pixels
   bool full = false;
   for (int k = 0; k < 3 && !skip; ++k) {
     if (vi[k] < 0 || vi[k] >= S.nv) { skip = true; break; }
@@ -57,11 +58,20 @@ __global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
     float nx1 = fmaxf(fmaxf(xl / wl, xl / wh), fmaxf(xh / wl, xh / wh));
     float ny0 = fminf(fminf(yl / wl, yl / wh), fminf(yh / wl, yh / wh));
     float ny1 = fmaxf(fmaxf(yl / wl, yl / wh), fmaxf(yh / wl, yh / wh));
-    sx0 = fminf(sx0, (nx0 * 0.5f + 0.5f) * S.W);
-    sx1 = fmaxf(sx1, (nx1 * 0.5f + 0.5f) * S.W);
-    sy0 = fminf(sy0, (0.5f - ny1 * 0.5f) * S.H);
-    sy1 = fmaxf(sy1, (0.5f - ny0 * 0.5f) * S.H);
+    const float vx0 = (nx0 * 0.5f + 0.5f) * S.W, vx1 = (nx1 * 0.5f + 0.5f) * S.W;
+    const float vy0 = (0.5f - ny1 * 0.5f) * S.H, vy1 = (0.5f - ny0 * 0.5f) * S.H;
+    sx0 = fminf(sx0, vx0);
+    sx1 = fmaxf(sx1, vx1);
+    sy0 = fminf(sy0, vy0);
+    sy1 = fmaxf(sy1, vy1);
+    disp = fmaxf(disp, fmaxf(vx1 - vx0, vy1 - vy0));
   }
+  // Margin (fixed-point units) that bounds how far any snapped perturbed vertex can
+  // be from the snapped unperturbed one: the interval width, one unit of snapping on
+  // each side and slack for float rounding of the interval; "full" = unbounded.
+  int margin = 0x7FFFFFFF;
+  if (!full && !skip && disp < 1.0e4f) margin = (int)ceilf(disp * 256.0f * 1.001f) + 4;
+  ws.tri_margin[(long long)slot * S.nt + tri] = margin;
   if (!skip) {
     int px0, px1, py0, py1;
     if (full) {
@@ -85,46 +95,55 @@ __global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
 // One CTA: exclusive scan of the per-(slot, tile) counts, list of non-empty tiles,
 // fill cursors, and the estimate kernel's work counter.
 __global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt) {
-  __shared__ uint32_t wsum[32], wne[32];
+  __shared__ uint32_t wsum[32], wne[32], wnh[32];
   int tid = threadIdx.x;
   const int per = (n + blockDim.x - 1) / blockDim.x;
   int beg = min(n, tid * per), end = min(n, beg + per);
-  uint32_t sum = 0, ne = 0;
+  uint32_t sum = 0, ne = 0, nh = 0;
   for (int i = beg; i < end; ++i) {
     uint32_t c = ws.tile_count[i];
     sum += c;
-    ne += c > 0;
+    ne += c > 0 && c <= (uint32_t)kLightBin;
+    nh += c > (uint32_t)kLightBin;
   }
-  // block exclusive scan of (sum, ne)
-  uint32_t xs = sum, xn = ne;
+  // block exclusive scan of (sum, ne, nh)
+  uint32_t xs = sum, xn = ne, xh = nh;
   int lane = tid & 31, wid = tid >> 5;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     uint32_t a = __shfl_up_sync(0xffffffffu, xs, o), b = __shfl_up_sync(0xffffffffu, xn, o);
-    if (lane >= o) { xs += a; xn += b; }
+    uint32_t c = __shfl_up_sync(0xffffffffu, xh, o);
+    if (lane >= o) { xs += a; xn += b; xh += c; }
   }
-  if (lane == 31) { wsum[wid] = xs; wne[wid] = xn; }
+  if (lane == 31) { wsum[wid] = xs; wne[wid] = xn; wnh[wid] = xh; }
   __syncthreads();
   if (wid == 0) {
-    uint32_t a = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u, b = lane < (int)(blockDim.x >> 5) ? wne[lane] : 0u;
+    const bool in = lane < (int)(blockDim.x >> 5);
+    uint32_t a = in ? wsum[lane] : 0u, b = in ? wne[lane] : 0u, c = in ? wnh[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t pa = __shfl_up_sync(0xffffffffu, a, o), pb = __shfl_up_sync(0xffffffffu, b, o);
-      if (lane >= o) { a += pa; b += pb; }
+      uint32_t pc = __shfl_up_sync(0xffffffffu, c, o);
+      if (lane >= o) { a += pa; b += pb; c += pc; }
     }
     wsum[lane] = a;
     wne[lane] = b;
+    wnh[lane] = c;
   }
   __syncthreads();
   uint32_t off = (wid ? wsum[wid - 1] : 0u) + xs - sum;
   uint32_t noff = (wid ? wne[wid - 1] : 0u) + xn - ne;
+  uint32_t hoff = (wid ? wnh[wid - 1] : 0u) + xh - nh;
   for (int i = beg; i < end; ++i) {
     uint32_t c = ws.tile_count[i];
     ws.tile_off[i] = off;
     ws.tile_cur[i] = off;
     if (c > 0) {
       int slot = i / nt, tile = i - slot * nt;
-      ws.items[noff++] = ((uint32_t)slot << 24) | (uint32_t)tile;
+      const uint32_t it = ((uint32_t)slot << 24) | (uint32_t)tile;
+      // light items from the front of the list, heavy ones from the back
+      if (c <= (uint32_t)kLightBin) ws.items[noff++] = it;
+      else ws.items[n - 1 - hoff++] = it;
     }
     off += c;
   }
@@ -134,6 +153,8 @@ __global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt) 
     ws.counters[0] = overflow ? 0u : noff;
     ws.counters[1] = 0u;
     ws.counters[2] = off;
+    ws.counters[4] = overflow ? 0u : hoff;
+    ws.counters[5] = 0u;
     if (overflow) atomicCAS(ws.counters + 3, 0u, (uint32_t)SGE_ERR_BIN_OVERFLOW);
   }
 }

@@ -180,14 +180,15 @@ __device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem& tb
   }
 }
 
-__global__ void __launch_bounds__(TILE_PX) k_estimate(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
+__global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
   const int n_chunks = (a.pairs + a.pairs_per_item - 1) / a.pairs_per_item;
-  const long long n_work = (long long)ws.counters[0] * n_chunks;
+  const long long n_work = (long long)ws.counters[4] * n_chunks;
+  const int n_all = vl.n * ntl;
 
   for (int s = tid; s < TABLE; s += blockDim.x) {
     sm.tab.key[s] = EMPTY;
@@ -200,11 +201,11 @@ __global__ void __launch_bounds__(TILE_PX) k_estimate(SceneDev S, Workspace ws, 
 
   for (;;) {
     __syncthreads();
-    if (tid == 0) sm.item = atomicAdd(ws.counters + 1, 1u);
+    if (tid == 0) sm.item = atomicAdd(ws.counters + 5, 1u);
     __syncthreads();
     const long long w = sm.item;
     if (w >= n_work) break;
-    const uint32_t it = ws.items[w / n_chunks];
+    const uint32_t it = ws.items[n_all - 1 - (int)(w / n_chunks)];
     const int chunk = (int)(w % n_chunks);
     const int slot = it >> 24, tile = it & 0xFFFFFF;
     const int view = vl.id[slot];
@@ -335,18 +336,20 @@ int estimate_blocks_per_sm() {
   static int cached = -1;
   if (cached < 0) {
     int n = 0;
-    cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate, TILE_PX, sizeof(Smem));
+    cudaFuncSetAttribute(k_estimate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy, TILE_PX, sizeof(Smem));
     cached = n > 0 ? n : 1;
   }
   return cached;
 }
 
 cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
-                            int grid, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_estimate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+                            int grid_fast, int grid_heavy, cudaStream_t st) {
+  cudaError_t e = launch_fast(S, ws, vl, a, grid_fast, st);
   if (e != cudaSuccess) return e;
-  k_estimate<<<grid, TILE_PX, sizeof(Smem), st>>>(S, ws, vl, a);
+  e = cudaFuncSetAttribute(k_estimate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+  if (e != cudaSuccess) return e;
+  k_estimate_heavy<<<grid_heavy, TILE_PX, sizeof(Smem), st>>>(S, ws, vl, a);
   if (a.loss) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);
   return cudaGetLastError();
 }

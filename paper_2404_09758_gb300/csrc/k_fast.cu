@@ -1,0 +1,618 @@
+// Batched estimator, fast path: tiles whose bin holds at most kLightBin triangles.
+//
+// Work item = (view, 16x16 tile, run of antithetic pairs); one CTA thread per pixel.
+// Per item, once:
+//   the bin's triangles are set up unperturbed; every pixel keeps the (at most
+//   CMAX) triangles that can cover it under ANY perturbation of the call (each
+//   edge function pushed out by the triangle's margin: the support of the box
+//   every snapped perturbed vertex stays in), so a pair tests a handful of
+//   triangles instead of the whole bin.
+// Per pair (Eq. 8 for one sign vector s, Algorithms 1-2):
+//   S   each bin triangle draws its 9 vertex-coordinate signs once, perturbs and
+//       sets up both sides (theta + s eps, theta - s eps) in shared memory;
+//   R   each pixel finds its visible triangle on both sides among its candidates
+//       (smallest packed depth|id key);
+//   U   each pixel computes both sides' UV and inserts the texels of their bilinear
+//       footprints into a shared-memory table;
+//   G1  the table folds the previous pair's per-texel sums with that pair's signs
+//       and draws this pair's signs once per touched texel and channel; the
+//       triangles fold their previous pair's vertex credits likewise;
+//   G2  each pixel samples its perturbed texels (signs from the table), shades both
+//       sides, forms f+ - f- and credits it: the visible triangle (all three
+//       vertices at once, or single corners where the sides disagree) and the union
+//       of the texel footprints.
+// At the end of the item every credited vertex corner and texel issues one global
+// atomic per channel for its sum and its count.
+#include <cuda_runtime.h>
+
+#include "sge_device.cuh"
+
+namespace sge {
+
+namespace {
+
+constexpr int NB = kLightBin;
+constexpr int CMAX = 8;  // candidate triangles kept per pixel
+constexpr int MAX_PROBE = 16;
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr uint32_t NOSLOT = 0xFFFFu;
+
+template <int SH>
+struct Model {
+  static constexpr int NREAD = SH == SHADE_UNLIT ? 1 : (SH == SHADE_LAMBERT ? 2 : 4);
+  static constexpr int TABLE = SH == SHADE_UNLIT ? 512 : 1024;
+};
+
+struct __align__(16) TriS {
+  long long e0[3];  // oriented edge functions at the tile's first pixel centre
+  int bias;         // bit k set: edge k is not a top/left edge
+  int tri;          // triangle id, -1 when not drawn on this side
+  int a[3], b[3];   // oriented edge steps per fixed-point unit in x and y
+  float inv_area;
+  int margin;       // (unperturbed setup only) perturbation margin, fixed-point units
+  float z[3], iw[3];
+  int pad[2];
+};
+
+template <int TABLE>
+struct FastSmem {
+  TriS side[2][NB];
+  float uv[NB][6];
+  int vid[NB][3];
+  int btri[NB];          // triangle id of each bin entry
+  uint32_t sgn9[2][NB];  // bit 3k+c: coordinate c of corner k has s = -1 (by pair parity)
+  float A_tri[NB];
+  uint32_t n_tri[NB];
+  float A_cor[NB][3];
+  uint32_t n_cor[NB][3];
+  float S_cor[NB][3][3];
+  uint32_t c_cor[NB][3];
+  uint32_t tkey[TABLE];
+  float tA[TABLE];
+  uint32_t tn[TABLE];
+  uint32_t tstamp[TABLE];
+  uint32_t tsb[TABLE];
+  float tS[4][TABLE];
+  uint32_t tcnt[TABLE];
+  float m[16];
+  float red[TILE_PX / 32];
+  uint32_t item;
+};
+
+__device__ __forceinline__ void store_side(TriS& d, const Tri& t, int tri) {
+  if (!t.ok) {
+    d.tri = -1;
+    return;
+  }
+  int bias = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    d.e0[k] = t.e0[k];
+    d.a[k] = t.a[k];
+    d.b[k] = t.b[k];
+    d.z[k] = t.z[k];
+    d.iw[k] = t.iw[k];
+    bias |= (t.bias[k] ? 1 : 0) << k;
+  }
+  d.bias = bias;
+  d.inv_area = t.inv_area;
+  d.tri = tri;
+}
+
+// Exact coverage at pixel offset (dx, dy): oriented edge functions into e, or false.
+__device__ __forceinline__ bool cover_s(const TriS& t, int dx, int dy, long long e[3]) {
+  bool in = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    e[k] = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
+    in = in && (e[k] - ((t.bias >> k) & 1) >= 0);
+  }
+  return in;
+}
+
+__device__ __forceinline__ unsigned long long key_s(const TriS& t, const long long e[3]) {
+  float l[3];
+  lambdas(e, t.inv_area, l);
+  return ((unsigned long long)ordered_bits(interp_depth(l, t.z)) << 32) | (uint32_t)t.tri;
+}
+
+__device__ __forceinline__ uint32_t hslot(uint32_t k, int table) {
+  k ^= k >> 16;
+  k *= 0x7feb352du;
+  k ^= k >> 15;
+  return k & (uint32_t)(table - 1);
+}
+
+template <int TABLE>
+__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE>& sm, uint32_t key, uint32_t stamp) {
+  uint32_t slot = hslot(key, TABLE);
+#pragma unroll 1
+  for (int p = 0; p < MAX_PROBE; ++p) {
+    uint32_t k = *(volatile uint32_t*)&sm.tkey[slot];
+    if (k == EMPTY) {
+      k = atomicCAS(&sm.tkey[slot], EMPTY, key);
+      if (k == EMPTY) k = key;
+    }
+    if (k == key) {
+      sm.tstamp[slot] = stamp;
+      return slot;
+    }
+    slot = (slot + 1) & (TABLE - 1);
+  }
+  return NOSLOT;
+}
+
+// Texel id (y * W + x) of footprint corner q (0: x0y0, 1: x1y0, 2: x0y1, 3: x1y1).
+__device__ __forceinline__ int foot_texel(const Foot& f, int q, int w) {
+  return ((q & 2) ? f.y1 : f.y0) * w + ((q & 1) ? f.x1 : f.x0);
+}
+
+template <int TABLE>
+__device__ __forceinline__ void clear_item_table(FastSmem<TABLE>& sm) {
+  for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
+    sm.tkey[s] = EMPTY;
+    sm.tA[s] = 0.0f;
+    sm.tn[s] = 0u;
+    sm.tstamp[s] = 0u;
+    sm.tcnt[s] = 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm.tS[c][s] = 0.0f;
+  }
+}
+
+// Fold the previous pair's credits (table entries and triangle corners) with that pair's signs;
+// draw this pair's texel signs for the entries stamped `stamp` (0: none).
+template <int TABLE>
+__device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE>& sm, int nb, int prev_parity, uint32_t stamp,
+                                     uint64_t pkey) {
+  for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
+    const uint32_t key = sm.tkey[s];
+    if (key == EMPTY) continue;
+    const uint32_t kind = key >> 28;
+    const TexDev& T = S.tex[kind - 1];
+    const uint32_t nn = sm.tn[s];
+    if (nn) {
+      const float A = sm.tA[s];
+      const uint32_t sb = sm.tsb[s];
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < T.c) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
+      sm.tcnt[s] += nn;
+      sm.tA[s] = 0.0f;
+      sm.tn[s] = 0u;
+    }
+    if (stamp && sm.tstamp[s] == stamp) {
+      const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
+      uint32_t sb = 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (c < T.c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << c;
+      sm.tsb[s] = sb;
+    }
+  }
+  const int j = threadIdx.x;
+  if (j < nb && prev_parity >= 0) {
+    const uint32_t sg = sm.sgn9[prev_parity][j];
+    const float at = sm.A_tri[j];
+    const uint32_t nt = sm.n_tri[j];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float a = at + sm.A_cor[j][k];
+      const uint32_t n = nt + sm.n_cor[j][k];
+      if (n) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sm.S_cor[j][k][c] += ((sg >> (3 * k + c)) & 1) ? -a : a;
+        sm.c_cor[j][k] += n;
+      }
+      sm.A_cor[j][k] = 0.0f;
+      sm.n_cor[j][k] = 0u;
+    }
+    sm.A_tri[j] = 0.0f;
+    sm.n_tri[j] = 0u;
+  }
+}
+
+template <int SH>
+__global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
+    k_estimate_fast(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
+  constexpr int NREAD = Model<SH>::NREAD;
+  constexpr int TABLE = Model<SH>::TABLE;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FastSmem<TABLE>& sm = *reinterpret_cast<FastSmem<TABLE>*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int dx = tid % TILE, dy = tid / TILE;
+  const int ntl = n_tiles(S);
+  const int n_chunks = (a.pairs + a.pairs_per_item - 1) / a.pairs_per_item;
+  const long long n_work = (long long)ws.counters[0] * n_chunks;
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) sm.item = atomicAdd(ws.counters + 1, 1u);
+    __syncthreads();
+    const long long w = sm.item;
+    if (w >= n_work) break;
+    const uint32_t it = ws.items[w / n_chunks];
+    const int chunk = (int)(w % n_chunks);
+    const int slot = it >> 24, tile = it & 0xFFFFFF;
+    const int view = vl.id[slot];
+    const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+    const int px = tx * TILE + dx, py = ty * TILE + dy;
+    const bool valid = px < S.W && py < S.H;
+    const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
+    const uint32_t bin_beg = ws.tile_off[slot * ntl + tile];
+    const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - bin_beg);
+    const int p0 = chunk * a.pairs_per_item, p1 = min(a.pairs, p0 + a.pairs_per_item);
+    if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
+    clear_item_table(sm);
+    __syncthreads();
+
+    // ---- per item: stage the bin unperturbed, build per-pixel candidate lists
+    if (tid < nb) {
+      const int tri = (int)ws.bins[bin_beg + tid];
+      sm.btri[tid] = tri;
+      Tri t;
+      setup_from_scene(S, sm.m, tri, 0, 0, rx, ry, t);
+      store_side(sm.side[0][tid], t, tri);
+      // not drawable unperturbed (zero area, or a vertex behind the near limit): a perturbed
+      // version may still be, so it stays a candidate for every pixel of the tile
+      if (!t.ok) sm.side[0][tid].tri = -2;
+      sm.side[0][tid].margin = ws.tri_margin[(long long)slot * S.nt + tri];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sm.vid[tid][k] = __ldg(S.pidx + 3 * tri + k);
+        const int ti = __ldg(S.uvidx + 3 * tri + k);
+        sm.uv[tid][2 * k] = __ldg(S.uvs + 2 * ti);
+        sm.uv[tid][2 * k + 1] = __ldg(S.uvs + 2 * ti + 1);
+        sm.A_cor[tid][k] = 0.0f;
+        sm.n_cor[tid][k] = 0u;
+        sm.c_cor[tid][k] = 0u;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sm.S_cor[tid][k][c] = 0.0f;
+      }
+      sm.A_tri[tid] = 0.0f;
+      sm.n_tri[tid] = 0u;
+    }
+    __syncthreads();
+    uint32_t cand[2] = {0u, 0u};
+    int ncand = 0;
+    for (int j = 0; j < nb; ++j) {
+      const TriS& t = sm.side[0][j];
+      bool maybe;
+      if (t.tri == -2 || t.margin == 0x7FFFFFFF) {
+        maybe = true;
+      } else {
+        maybe = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
+          const long long reach = (long long)t.margin * (long long)(abs(t.a[k]) + abs(t.b[k]));
+          maybe = maybe && (e + reach >= 0);
+        }
+      }
+      if (maybe) {
+        if (ncand < CMAX) cand[ncand >> 2] |= (uint32_t)j << (8 * (ncand & 3));
+        ++ncand;
+      }
+    }
+    const bool all_bin = ncand > CMAX;
+    float3 tgt = f3(0.f, 0.f, 0.f);
+    if (valid) {
+      const float* tp = S.targets + (((long long)view * S.H + py) * S.W + px) * 3;
+      tgt = f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
+    }
+    float loss_acc = 0.0f;
+
+    for (int pair = p0; pair < p1; ++pair) {
+      const uint64_t pkey = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)pair);
+      const int par = pair & 1;
+      __syncthreads();
+      // ---- S: perturb (signs drawn once for both sides) and set up the bin's triangles
+      if (tid < nb) {
+        uint32_t sg = 0;
+        float3 pp[3], pm[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int vi = sm.vid[tid][k];
+          const float* p = S.pos + 3ll * vi;
+          float q[3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const bool neg = sign_neg(pkey, 3ull * (uint64_t)vi + c);
+            sg |= (uint32_t)neg << (3 * k + c);
+            const float th = __ldg(p + c);
+            q[c] = neg ? -S.eps_pos : S.eps_pos;
+            (&pp[k].x)[c] = __fadd_rn(th, q[c]);
+            (&pm[k].x)[c] = __fadd_rn(th, -q[c]);
+          }
+        }
+        sm.sgn9[par][tid] = sg;
+        const int tid_tri = sm.btri[tid];
+        PVert vp[3], vm[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          vp[k] = project(sm.m, pp[k].x, pp[k].y, pp[k].z, S.W, S.H, S.near_w);
+          vm[k] = project(sm.m, pm[k].x, pm[k].y, pm[k].z, S.W, S.H, S.near_w);
+        }
+        Tri t;
+        setup_tri(vp[0], vp[1], vp[2], rx, ry, t);
+        store_side(sm.side[0][tid], t, tid_tri);
+        setup_tri(vm[0], vm[1], vm[2], rx, ry, t);
+        store_side(sm.side[1][tid], t, tid_tri);
+      }
+      __syncthreads();
+
+      // ---- R: visible triangle on both sides among the candidates
+      unsigned long long best[2] = {~0ull, ~0ull};
+      int bj[2] = {-1, -1};
+      if (valid) {
+        const int n_test = all_bin ? nb : ncand;
+        for (int q = 0; q < n_test; ++q) {
+          const int j = all_bin ? q : (int)((cand[q >> 2] >> (8 * (q & 3))) & 0xFFu);
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            const TriS& t = sm.side[sd][j];
+            if (t.tri < 0) continue;
+            long long e[3];
+            if (!cover_s(t, dx, dy, e)) continue;
+            const unsigned long long k = key_s(t, e);
+            if (k < best[sd]) {
+              best[sd] = k;
+              bj[sd] = j;
+            }
+          }
+        }
+      }
+
+      // ---- U: UV buffer values and texel keys of both sides
+      float2 uvs[2];
+      float bary[2][3];
+      uint32_t tslot[2][NREAD][2];  // four 16-bit slots per side and read texture
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        uvs[sd] = make_float2(0.f, 0.f);
+        if (bj[sd] < 0) continue;
+        const TriS& t = sm.side[sd][bj[sd]];
+        long long e[3];
+        cover_s(t, dx, dy, e);
+        float l[3];
+        lambdas(e, t.inv_area, l);
+        const PerspW pw = persp(l, t.iw);
+        const float* uvt = sm.uv[bj[sd]];
+        uvs[sd].x = persp_interp(pw, uvt[0], uvt[2], uvt[4]);
+        uvs[sd].y = persp_interp(pw, uvt[1], uvt[3], uvt[5]);
+        if (SH == SHADE_GGX) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) bary[sd][k] = pw.q[k] / pw.qs;
+        }
+#pragma unroll
+        for (int r = 0; r < NREAD; ++r) {
+          const int k = S.read_k[r];
+          const TexDev& T = S.tex[k];
+          const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
+          uint32_t sl[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) sl[q] = table_insert(sm, tkey(k, foot_texel(f, q, T.w)), (uint32_t)pair + 1);
+          tslot[sd][r][0] = sl[0] | (sl[1] << 16);
+          tslot[sd][r][1] = sl[2] | (sl[3] << 16);
+        }
+      }
+      __syncthreads();
+
+      // ---- G1: fold the previous pair, draw this pair's texel signs
+      fold(S, sm, nb, pair > p0 ? (par ^ 1) : -1, (uint32_t)pair + 1, pkey);
+      __syncthreads();
+
+      // ---- G2: shade both sides, f+ - f-, credits
+      float3 col[2];
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        col[sd] = f3(S.bg[0], S.bg[1], S.bg[2]);
+        if (bj[sd] < 0) continue;
+        float tex[4][4];
+#pragma unroll
+        for (int r = 0; r < NREAD; ++r) {
+          const int k = S.read_k[r];
+          const TexDev& T = S.tex[k];
+          const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
+          const float wq[4] = {(1.0f - f.fx) * (1.0f - f.fy), f.fx * (1.0f - f.fy), (1.0f - f.fx) * f.fy, f.fx * f.fy};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) tex[r][c] = 0.0f;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+            const long long texel = foot_texel(f, q, T.w);
+            const float* src = T.ptr + texel * T.c;
+            uint32_t sb;
+            if (sl != NOSLOT) {
+              sb = sm.tsb[sl];
+            } else {
+              sb = 0;
+              for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(T.offset + texel * T.c + c)) << c;
+            }
+            if (sd == 1) sb = ~sb;  // side -: theta - s eps
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              if (c < T.c) tex[r][c] += wq[q] * __fadd_rn(__ldg(src + c), ((sb >> c) & 1) ? -T.eps : T.eps);
+          }
+          if (T.c == 1) tex[r][1] = tex[r][2] = tex[r][0];
+        }
+        if (SH == SHADE_UNLIT) {
+          col[sd] = f3(tex[0][0], tex[0][1], tex[0][2]);
+        } else {
+          const int j = bj[sd];
+          const uint32_t sg = sm.sgn9[par][j] ^ (sd == 1 ? 0x1FFu : 0u);
+          float3 p[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float* src = S.pos + 3ll * sm.vid[j][k];
+            float q[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              q[c] = __fadd_rn(__ldg(src + c), ((sg >> (3 * k + c)) & 1) ? -S.eps_pos : S.eps_pos);
+            p[k] = f3(q[0], q[1], q[2]);
+          }
+          const float2 uvv[3] = {make_float2(sm.uv[j][0], sm.uv[j][1]), make_float2(sm.uv[j][2], sm.uv[j][3]),
+                                 make_float2(sm.uv[j][4], sm.uv[j][5])};
+          float alb[4] = {1.f, 1.f, 1.f, 1.f}, nm[4] = {0.5f, 0.5f, 1.f, 0.f}, rough[4] = {0.5f, 0.f, 0.f, 0.f},
+                metal[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int r = 0; r < NREAD; ++r) {
+            const int role = S.tex[S.read_k[r]].role;
+            float* dst = role == ROLE_ALBEDO ? alb : role == ROLE_NORMAL ? nm : role == ROLE_ROUGHNESS ? rough : metal;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dst[c] = tex[r][c];
+          }
+          const float bz[3] = {SH == SHADE_GGX ? bary[sd][0] : 0.f, SH == SHADE_GGX ? bary[sd][1] : 0.f,
+                               SH == SHADE_GGX ? bary[sd][2] : 0.f};
+          col[sd] = shade(S, view, alb, nm, rough, metal, p, uvv, bz);
+        }
+      }
+      if (valid) {
+        float fp, fm;
+        const float df = loss_diff(col[0], col[1], tgt, fp, fm);
+        loss_acc += 0.5f * (fp + fm);
+        if (a.delta_f) a.delta_f[(((long long)slot * a.pairs + pair) * S.H + py) * S.W + px] = df;
+        // vertices: the visible triangle of each side (union of corners)
+        if (bj[0] >= 0 && bj[0] == bj[1]) {
+          atomicAdd(&sm.A_tri[bj[0]], df);
+          atomicAdd(&sm.n_tri[bj[0]], 1u);
+        } else {
+          if (bj[0] >= 0) {
+            atomicAdd(&sm.A_tri[bj[0]], df);
+            atomicAdd(&sm.n_tri[bj[0]], 1u);
+          }
+          if (bj[1] >= 0) {
+            if (bj[0] < 0) {
+              atomicAdd(&sm.A_tri[bj[1]], df);
+              atomicAdd(&sm.n_tri[bj[1]], 1u);
+            } else {
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const int v = sm.vid[bj[1]][k];
+                if (v != sm.vid[bj[0]][0] && v != sm.vid[bj[0]][1] && v != sm.vid[bj[0]][2]) {
+                  atomicAdd(&sm.A_cor[bj[1]][k], df);
+                  atomicAdd(&sm.n_cor[bj[1]][k], 1u);
+                }
+              }
+            }
+          }
+        }
+        // texels: union of both sides' footprints of every read texture
+#pragma unroll
+        for (int r = 0; r < NREAD; ++r) {
+          const int k = S.read_k[r];
+          const TexDev& T = S.tex[k];
+          int ids[2][4];
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            if (bj[sd] < 0) continue;
+            const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ids[sd][q] = foot_texel(f, q, T.w);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              bool dup = false;
+#pragma unroll
+              for (int o = 0; o < q; ++o) dup = dup || ids[sd][o] == ids[sd][q];
+              if (sd == 1 && bj[0] >= 0) {
+#pragma unroll
+                for (int o = 0; o < 4; ++o) dup = dup || ids[0][o] == ids[1][q];
+              }
+              if (dup) continue;
+              const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+              if (sl != NOSLOT) {
+                atomicAdd(&sm.tA[sl], df);
+                atomicAdd(&sm.tn[sl], 1u);
+              } else {
+                const long long base = T.offset + (long long)ids[sd][q] * T.c;
+                for (int c = 0; c < T.c; ++c) {
+                  atomicAdd(a.grad + base + c, sign_neg(pkey, (uint64_t)(base + c)) ? -df : df);
+                  atomicAdd(a.counts + base + c, 1u);
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    fold(S, sm, nb, (p1 - 1) & 1, 0u, 0ull);
+    __syncthreads();
+    // ---- flush: one global atomic per credited vertex corner / texel and channel
+    for (int s = tid; s < TABLE; s += blockDim.x) {
+      const uint32_t key = sm.tkey[s];
+      if (key == EMPTY || sm.tcnt[s] == 0) continue;
+      const TexDev& T = S.tex[(key >> 28) - 1];
+      const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
+      for (int c = 0; c < T.c; ++c) {
+        atomicAdd(a.grad + base + c, sm.tS[c][s]);
+        atomicAdd(a.counts + base + c, sm.tcnt[s]);
+      }
+    }
+    if (tid < nb) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint32_t cn = sm.c_cor[tid][k];
+        if (!cn) continue;
+        const long long base = 3ll * sm.vid[tid][k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          atomicAdd(a.grad + base + c, sm.S_cor[tid][k][c]);
+          atomicAdd(a.counts + base + c, cn);
+        }
+      }
+    }
+    if (a.loss) {
+      float v = loss_acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) sm.red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        float sum = 0.0f;
+        for (int i = 0; i < TILE_PX / 32; ++i) sum += sm.red[i];
+        atomicAdd(a.loss + slot, sum / (float)a.pairs);
+      }
+    }
+  }
+}
+
+template <int SH>
+size_t fast_smem() {
+  return sizeof(FastSmem<Model<SH>::TABLE>);
+}
+
+template <int SH>
+cudaError_t launch_fast_t(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
+                          int grid, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_estimate_fast<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<SH>());
+  if (e != cudaSuccess) return e;
+  k_estimate_fast<SH><<<grid, TILE_PX, fast_smem<SH>(), st>>>(S, ws, vl, a);
+  return cudaGetLastError();
+}
+
+template <int SH>
+int fast_blocks_per_sm_t() {
+  int n = 0;
+  cudaFuncSetAttribute(k_estimate_fast<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_smem<SH>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_fast<SH>, TILE_PX, fast_smem<SH>());
+  return n > 0 ? n : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a, int grid,
+                        cudaStream_t st) {
+  if (S.shading == SHADE_UNLIT) return launch_fast_t<SHADE_UNLIT>(S, ws, vl, a, grid, st);
+  if (S.shading == SHADE_LAMBERT) return launch_fast_t<SHADE_LAMBERT>(S, ws, vl, a, grid, st);
+  return launch_fast_t<SHADE_GGX>(S, ws, vl, a, grid, st);
+}
+
+int fast_blocks_per_sm(int shading) {
+  if (shading == SHADE_UNLIT) return fast_blocks_per_sm_t<SHADE_UNLIT>();
+  if (shading == SHADE_LAMBERT) return fast_blocks_per_sm_t<SHADE_LAMBERT>();
+  return fast_blocks_per_sm_t<SHADE_GGX>();
+}
+
+}  // namespace sge

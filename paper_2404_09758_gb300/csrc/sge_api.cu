@@ -16,7 +16,7 @@ struct sge_scene {
   sge_config cfg;
   SceneDev dev;
   Workspace ws;
-  int grid;  // persistent CTAs of the estimate kernel
+  int grid_fast, grid_heavy;  // persistent CTAs of the two estimator kernels
 };
 
 namespace {
@@ -38,7 +38,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t tri_rect, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf, total;
+  size_t tri_rect, tri_margin, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf, total;
   int max_views;
   long long bin_capacity;
 };
@@ -83,6 +83,7 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
   L.tri_rect = take(sizeof(int4) * (size_t)L.max_views * d->n_triangles);
+  L.tri_margin = take(sizeof(int) * (size_t)L.max_views * d->n_triangles);
   L.tile_count = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
   L.tile_off = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl + 1));
   L.tile_cur = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
@@ -202,6 +203,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   char* base = static_cast<char*>(workspace);
   Workspace& w = s->ws;
   w.tri_rect = reinterpret_cast<int4*>(base + L.tri_rect);
+  w.tri_margin = reinterpret_cast<int*>(base + L.tri_margin);
   w.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
   w.tile_off = reinterpret_cast<uint32_t*>(base + L.tile_off);
   w.tile_cur = reinterpret_cast<uint32_t*>(base + L.tile_cur);
@@ -221,8 +223,9 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
     delete s;
     return cuda_fail(e, "sge_create_scene");
   }
-  int bps = (s->cfg.blocks_per_sm > 0) ? s->cfg.blocks_per_sm : estimate_blocks_per_sm();
-  s->grid = sms * bps;
+  int bps = (s->cfg.blocks_per_sm > 0) ? s->cfg.blocks_per_sm : fast_blocks_per_sm(desc->shading);
+  s->grid_fast = sms * bps;
+  s->grid_heavy = sms * estimate_blocks_per_sm();
   if (s->cfg.pairs_per_item <= 0) s->cfg.pairs_per_item = 16;
   *out = s;
   return SGE_OK;
@@ -277,7 +280,7 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
   if (delta_f_out)
     e = cudaMemsetAsync(delta_f_out, 0, sizeof(float) * (size_t)n_views * pairs_per_view * s->dev.W * s->dev.H, st);
   if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
-  if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, a, s->grid, st);
+  if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, a, s->grid_fast, s->grid_heavy, st);
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
 }
 

@@ -12,6 +12,7 @@ constexpr int SGE_MAX_TEX_DEV = SGE_MAX_TEXTURES;
 constexpr int MAX_READ = 4;              // albedo, normal, roughness, metallic
 constexpr int TILE = 16;                 // tile edge in pixels; one CTA thread per pixel
 constexpr int TILE_PX = TILE * TILE;     // 256 threads
+constexpr int kLightBin = 256;           // bins up to this size use the staged fast path
 constexpr int ROLE_ALBEDO = SGE_ROLE_ALBEDO, ROLE_NORMAL = SGE_ROLE_NORMAL;
 constexpr int ROLE_ROUGHNESS = SGE_ROLE_ROUGHNESS, ROLE_METALLIC = SGE_ROLE_METALLIC;
 constexpr int SHADE_UNLIT = SGE_SHADE_UNLIT, SHADE_LAMBERT = SGE_SHADE_LAMBERT, SHADE_GGX = SGE_SHADE_GGX;
@@ -61,12 +62,14 @@ struct ViewList {
 // Scratch carved out of the caller's workspace.
 struct Workspace {
   int4* tri_rect;        // [max_views][nt] tile rectangle (x0,y0,x1,y1) of each triangle's bin span
+  int* tri_margin;       // [max_views][nt] perturbation margin of each triangle, fixed-point units
   uint32_t* tile_count;  // [max_views][n_tiles]
   uint32_t* tile_off;    // [max_views][n_tiles + 1] exclusive scan of counts
   uint32_t* tile_cur;    // [max_views][n_tiles] fill cursors
   uint32_t* bins;        // [bin_capacity] triangle ids grouped by (view slot, tile)
-  uint32_t* items;       // [max_views * n_tiles] non-empty (view slot << 24 | tile)
-  uint32_t* counters;    // [0] n_items, [1] work counter, [2] total bin entries, [3] status
+  uint32_t* items;       // [max_views * n_tiles] (view slot << 24 | tile): light bins first, heavy from the end
+  uint32_t* counters;    // [0] light items, [1] their work counter, [2] total bin entries, [3] status,
+                         // [4] heavy items, [5] their work counter
   unsigned long long* keys;  // [2][H*W] staged depth|ID buffers (both sides)
   float2* uvbuf;             // [2][H*W] staged UV buffers
   float* dfbuf;              // [H*W] staged loss differences
@@ -89,9 +92,13 @@ struct EstimateArgs {
   float* loss;
   float* delta_f;
 };
+// Both estimator kernels: the fast path over light bins, the general one over heavy bins.
 cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl,
-                            const EstimateArgs& a, int grid, cudaStream_t st);
+                            const EstimateArgs& a, int grid_fast, int grid_heavy, cudaStream_t st);
+cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
+                        int grid, cudaStream_t st);
 int estimate_blocks_per_sm();
+int fast_blocks_per_sm(int shading);
 
 // Staged path: render one side of one estimate into keys/uv/rgb.
 cudaError_t launch_render(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key,
