@@ -27,7 +27,9 @@ __device__ __forceinline__ void raster_tile(const SceneDev& S, const Workspace& 
                                             int dy) {
   const int ntl = n_tiles(S);
   const uint32_t beg = ws.tile_off[slot * ntl + tile];
-  const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - beg);
+  int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - beg);
+  // after a bin overflow (reported in the status word) the tile's list was not stored
+  if ((long long)beg + nb > ws.bin_capacity) nb = 0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) best[s] = ~0ull;
   for (int c0 = 0; c0 < nb; c0 += RCHUNK) {

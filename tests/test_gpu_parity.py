@@ -162,6 +162,9 @@ def test_bin_overflow_is_reported_not_silent():
     assert g.status() == ERR_BIN_OVERFLOW
     assert g.status() == 0  # reading clears it
     assert counts.sum().item() == 0
+    keys, _, _ = g.render_idb(0)  # tiles whose list did not fit render as background
+    assert g.status() == ERR_BIN_OVERFLOW
+    assert (keys == -1).sum().item() > 0
 
 
 def test_bad_index_is_reported():
