@@ -184,6 +184,29 @@ int sge_step(sge_scene *scene, const sge_opt *opt, float *grad_sums, uint32_t *c
  * device-side error) in *device_status and clear it. */
 int sge_status(sge_scene *scene, sge_stream_t stream, int32_t *device_status);
 
+/* Allocation-free render, for callers that cannot allocate device memory: code
+ * embedded in a host application that owns the whole device-memory budget, or
+ * that must not let cudaMalloc / cudaFree synchronise the device mid-frame, and so
+ * cannot provide the workspace the other entry points need.  The paper has no
+ * counterpart; the result equals sge_render_idb's for the same arguments.
+ * Takes the scene description directly (no sge_scene, no workspace; targets may
+ * be NULL).  Its scratch is a fixed array in the library's device memory,
+ * SGE_STATIC_SCRATCH limits below, held on every GPU that loads the library until
+ * the process exits; requests beyond the limits return SGE_ERR_INVALID_ARG and
+ * launch nothing.  The first call on a device (that device current) looks up the
+ * array's address; make it before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU (other streams or threads) race; order
+ * them on one stream.  device_status (device int32, or NULL) receives SGE_OK or
+ * SGE_ERR_BIN_OVERFLOW (tiles whose lists did not fit render as background).
+ * Allocates nothing and calls no allocating library routine.  Errors are
+ * reported by return code only. */
+#define SGE_STATIC_MAX_TRIANGLES 131072
+#define SGE_STATIC_MAX_PIXELS (2048 * 2048)
+#define SGE_STATIC_BIN_ENTRIES (1 << 21)
+int sge_render_idb_static(const sge_scene_desc *desc, int32_t view, uint64_t seed, uint32_t iter,
+                          uint32_t pair, int32_t side, uint64_t *depth_id, float *uv, float *rgb,
+                          int32_t *device_status, sge_stream_t stream);
+
 /* Release the host object (never the borrowed device memory). */
 void sge_destroy_scene(sge_scene *scene);
 
