@@ -99,8 +99,9 @@ typedef struct {
 typedef struct {
     int32_t max_views_per_call; /* views per estimate call the workspace is sized for (default n_views, <= 64) */
     int64_t bin_capacity;       /* triangle-tile bin entries over those views (default 16 * n_triangles * views) */
-    int32_t pairs_per_item;     /* antithetic pairs one CTA runs per (view, tile) item (default 16) */
+    int32_t pairs_per_item;     /* antithetic pairs one CTA runs per (view, tile) item (default 16, <= 64) */
     int32_t blocks_per_sm;      /* persistent CTAs per SM (default: as many as fit) */
+    int32_t max_pairs_per_call; /* pairs per view projected at once (default 64); more run in blocks */
 } sge_config;
 
 typedef struct {
@@ -113,8 +114,10 @@ typedef struct {
 
 typedef struct sge_scene sge_scene;
 
-/* Bytes of device workspace a scene needs (scratch for bins, tile lists and the
- * staged buffers of sge_render_idb).  Table 1 / Section 4.4 for what is stored. */
+/* Bytes of device workspace a scene needs: scratch for bins and tile lists, the
+ * projected perturbed vertices of max_views_per_call x max_pairs_per_call
+ * estimates (32 B + 1 B per vertex each), and the staged buffers of
+ * sge_render_idb (Section 4.4). */
 int sge_workspace_size(const sge_scene_desc *desc, const sge_config *cfg, size_t *bytes);
 
 /* Validate desc (host-side checks only: sizes, pointers, enums) and create a scene

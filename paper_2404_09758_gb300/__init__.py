@@ -53,7 +53,7 @@ class Scene:
                  width: int, height: int, targets=None, near: float = 0.1, shading: int = 0,
                  light_dir=(0.0, 0.0, 1.0), light_rgb=(1.0, 1.0, 1.0), ambient: float = 0.0,
                  background=(0.0, 0.0, 0.0), max_views_per_call: int = 0, bin_capacity: int = 0,
-                 pairs_per_item: int = 0, blocks_per_sm: int = 0, device=None):
+                 pairs_per_item: int = 0, blocks_per_sm: int = 0, max_pairs_per_call: int = 0, device=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("sge needs a CUDA device; there is no CPU path")
@@ -112,7 +112,8 @@ class Scene:
         d.shading = int(shading)
         d.ambient = float(ambient)
         self._desc = d
-        cfg = _abi.Config(int(max_views_per_call), int(bin_capacity), int(pairs_per_item), int(blocks_per_sm))
+        cfg = _abi.Config(int(max_views_per_call), int(bin_capacity), int(pairs_per_item), int(blocks_per_sm),
+                          int(max_pairs_per_call))
         self._cfg = cfg
         nbytes = C.c_size_t()
         _abi.check(L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(nbytes)))

@@ -39,7 +39,8 @@ class SceneDesc(C.Structure):
 
 class Config(C.Structure):
     _fields_ = [("max_views_per_call", C.c_int32), ("bin_capacity", C.c_int64),
-                ("pairs_per_item", C.c_int32), ("blocks_per_sm", C.c_int32)]
+                ("pairs_per_item", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("max_pairs_per_call", C.c_int32)]
 
 
 class Opt(C.Structure):

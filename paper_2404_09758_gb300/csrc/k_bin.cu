@@ -16,13 +16,14 @@ namespace sge {
 namespace {
 
 // Interval of one clip coordinate row of M over the box p +- eps (per coordinate).
-__device__ __forceinline__ void clip_interval(const float* m, float x, float y, float z, float eps, float& lo,
-                                              float& hi) {
+__device__ __forceinline__ float clip_interval(const float* m, float x, float y, float z, float eps, float& lo,
+                                               float& hi) {
   float c = m[0] * x + m[1] * y + m[2] * z + m[3];
   float r = eps * (fabsf(m[0]) + fabsf(m[1]) + fabsf(m[2]));
   r = r * 1.0001f + 1e-6f * (fabsf(c) + fabsf(m[3]) + 1.0f);
   lo = c - r;
   hi = c + r;
+  return c;
 }
 
 __global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
@@ -43,35 +44,46 @@ __global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
   }
   float sx0 = 3.4e38f, sx1 = -3.4e38f, sy0 = 3.4e38f, sy1 = -3.4e38f;
   float disp = 0.0f;  // widest screen interval of a vertex under the perturbation, pixels
+  float zlo = 3.4e38f, zhi = -3.4e38f;  // depth interval of the triangle under the perturbation
   bool full = false;
   for (int k = 0; k < 3 && !skip; ++k) {
     if (vi[k] < 0 || vi[k] >= S.nv) { skip = true; break; }
     const float* p = S.pos + 3ll * vi[k];
     float x = p[0], y = p[1], z = p[2];
-    float xl, xh, yl, yh, wl, wh;
-    clip_interval(m + 0, x, y, z, S.eps_pos, xl, xh);
-    clip_interval(m + 4, x, y, z, S.eps_pos, yl, yh);
-    clip_interval(m + 12, x, y, z, S.eps_pos, wl, wh);
+    float xl, xh, yl, yh, zl, zh, wl, wh;
+    const float cx = clip_interval(m + 0, x, y, z, S.eps_pos, xl, xh);
+    const float cy = clip_interval(m + 4, x, y, z, S.eps_pos, yl, yh);
+    clip_interval(m + 8, x, y, z, S.eps_pos, zl, zh);
+    const float cw = clip_interval(m + 12, x, y, z, S.eps_pos, wl, wh);
     if (wh <= S.near_w) { skip = true; break; }  // always behind the near limit: triangle never drawn
     if (wl <= S.near_w) { full = true; continue; }  // may or may not be drawn: bin everywhere
     float nx0 = fminf(fminf(xl / wl, xl / wh), fminf(xh / wl, xh / wh));
     float nx1 = fmaxf(fmaxf(xl / wl, xl / wh), fmaxf(xh / wl, xh / wh));
     float ny0 = fminf(fminf(yl / wl, yl / wh), fminf(yh / wl, yh / wh));
     float ny1 = fmaxf(fmaxf(yl / wl, yl / wh), fmaxf(yh / wl, yh / wh));
+    zlo = fminf(zlo, fminf(fminf(zl / wl, zl / wh), fminf(zh / wl, zh / wh)));
+    zhi = fmaxf(zhi, fmaxf(fmaxf(zl / wl, zl / wh), fmaxf(zh / wl, zh / wh)));
     const float vx0 = (nx0 * 0.5f + 0.5f) * S.W, vx1 = (nx1 * 0.5f + 0.5f) * S.W;
     const float vy0 = (0.5f - ny1 * 0.5f) * S.H, vy1 = (0.5f - ny0 * 0.5f) * S.H;
     sx0 = fminf(sx0, vx0);
     sx1 = fmaxf(sx1, vx1);
     sy0 = fminf(sy0, vy0);
     sy1 = fmaxf(sy1, vy1);
-    disp = fmaxf(disp, fmaxf(vx1 - vx0, vy1 - vy0));
+    // farthest any perturbed screen position lies from the unperturbed one
+    const float ux = (cx / cw * 0.5f + 0.5f) * S.W, uy = (0.5f - cy / cw * 0.5f) * S.H;
+    disp = fmaxf(disp, fmaxf(fmaxf(vx1 - ux, ux - vx0), fmaxf(vy1 - uy, uy - vy0)));
+    // near the guard band the drop rule may flip under the perturbation
+    if (!(fmaxf(fabsf(vx0), fabsf(vx1)) < 30000.0f && fmaxf(fabsf(vy0), fabsf(vy1)) < 30000.0f)) full = true;
   }
-  // Margin (fixed-point units) that bounds how far any snapped perturbed vertex can
-  // be from the snapped unperturbed one: the interval width, one unit of snapping on
-  // each side and slack for float rounding of the interval; "full" = unbounded.
+  // Margin (fixed-point units) that bounds, per axis, how far any snapped perturbed
+  // vertex can be from the snapped unperturbed one: the farthest interval end, one
+  // unit for the two snaps and slack for float rounding; "full" = unbounded.
   int margin = 0x7FFFFFFF;
-  if (!full && !skip && disp < 1.0e4f) margin = (int)ceilf(disp * 256.0f * 1.001f) + 4;
+  if (!full && !skip && disp < 1.0e4f) margin = (int)ceilf(disp * 256.0f * 1.002f) + 4;
   ws.tri_margin[(long long)slot * S.nt + tri] = margin;
+  // interpolated depth of a covered pixel lies between the vertex depths; slack for float rounding
+  ws.tri_z[(long long)slot * S.nt + tri] =
+      make_float2(zlo - (1e-6f + 1e-5f * fabsf(zlo)), zhi + (1e-6f + 1e-5f * fabsf(zhi)));
   if (!skip) {
     int px0, px1, py0, py1;
     if (full) {

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspac
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
-  const int n_chunks = (a.pairs + a.pairs_per_item - 1) / a.pairs_per_item;
+  const int n_chunks = (a.pair_count + a.pairs_per_item - 1) / a.pairs_per_item;
   const long long n_work = (long long)ws.counters[4] * n_chunks;
   const int n_all = vl.n * ntl;
 
@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspac
     const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
     const uint32_t bin_beg = ws.tile_off[slot * ntl + tile];
     const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - bin_beg);
-    const int p0 = chunk * a.pairs_per_item, p1 = min(a.pairs, p0 + a.pairs_per_item);
+    const int p0 = a.pair_begin + chunk * a.pairs_per_item;
+    const int p1 = min(a.pair_begin + a.pair_count, p0 + a.pairs_per_item);
     if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
     float3 tgt = f3(0.f, 0.f, 0.f);
     if (valid) {
@@ -350,7 +351,7 @@ cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewLi
   e = cudaFuncSetAttribute(k_estimate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return e;
   k_estimate_heavy<<<grid_heavy, TILE_PX, sizeof(Smem), st>>>(S, ws, vl, a);
-  if (a.loss) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);
+  if (a.loss && a.pair_begin == 0) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);
   return cudaGetLastError();
 }
 

@@ -5,22 +5,24 @@
 //   the bin's triangles are set up unperturbed; every pixel keeps the (at most
 //   CMAX) triangles that can cover it under ANY perturbation of the call (each
 //   edge function pushed out by the triangle's margin: the support of the box
-//   every snapped perturbed vertex stays in), so a pair tests a handful of
-//   triangles instead of the whole bin.
+//   every snapped perturbed vertex stays in), minus those surely behind a
+//   triangle that surely covers it (farther than the largest vertex move from
+//   each of its edges, so every perturbed version still covers it, and depth
+//   intervals apart); a pair then tests a handful of triangles, not the bin.
 // Per pair (Eq. 8 for one sign vector s, Algorithms 1-2):
-//   S   each bin triangle draws its 9 vertex-coordinate signs once, perturbs and
-//       sets up both sides (theta + s eps, theta - s eps) in shared memory;
+//   F+S the previous pair's credits are folded into per-channel sums with that
+//       pair's signs; the bin's triangles are set up on both sides (theta + s eps,
+//       theta - s eps) in shared memory from the projected perturbed vertices of
+//       the vertex pass (k_vertex.cu), with their 9 coordinate signs;
 //   R   each pixel finds its visible triangle on both sides among its candidates
 //       (smallest packed depth|id key);
-//   U   each pixel computes both sides' UV and inserts the texels of their bilinear
-//       footprints into a shared-memory table;
-//   G1  the table folds the previous pair's per-texel sums with that pair's signs
-//       and draws this pair's signs once per touched texel and channel; the
-//       triangles fold their previous pair's vertex credits likewise;
-//   G2  each pixel samples its perturbed texels (signs from the table), shades both
-//       sides, forms f+ - f- and credits it: the visible triangle (all three
-//       vertices at once, or single corners where the sides disagree) and the union
-//       of the texel footprints.
+//   U   it computes both sides' UV and inserts the texels of their bilinear
+//       footprints into a shared-memory table; the first pixel to touch a texel in
+//       the pair draws the pair's signs of its channels;
+//   G   it samples its perturbed texels (signs from the table), shades both sides,
+//       forms f+ - f- and credits it: the visible triangle (all three vertices at
+//       once, or single corners where the sides disagree) and the union of the
+//       texel footprints.
 // At the end of the item every credited vertex corner and texel issues one global
 // atomic per channel for its sum and its count.
 #include <cuda_runtime.h>
@@ -32,7 +34,7 @@ namespace sge {
 namespace {
 
 constexpr int NB = kLightBin;
-constexpr int CMAX = 8;  // candidate triangles kept per pixel
+constexpr int CMAX = 16;  // candidate triangles kept per pixel
 constexpr int MAX_PROBE = 16;
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t NOSLOT = 0xFFFFu;
@@ -43,13 +45,14 @@ struct Model {
   static constexpr int TABLE = SH == SHADE_UNLIT ? 512 : 1024;
 };
 
+// One side of a staged triangle (the unperturbed set-up also keeps its margin).
 struct __align__(16) TriS {
   long long e0[3];  // oriented edge functions at the tile's first pixel centre
   int bias;         // bit k set: edge k is not a top/left edge
-  int tri;          // triangle id, -1 when not drawn on this side
+  int tri;          // triangle id; -1 not drawn; -2 (unperturbed) not drawable: always a candidate
   int a[3], b[3];   // oriented edge steps per fixed-point unit in x and y
   float inv_area;
-  int margin;       // (unperturbed setup only) perturbation margin, fixed-point units
+  int margin;       // perturbation margin, fixed-point units (unperturbed set-up only)
   float z[3], iw[3];
   int pad[2];
 };
@@ -60,6 +63,7 @@ struct FastSmem {
   float uv[NB][6];
   int vid[NB][3];
   int btri[NB];          // triangle id of each bin entry
+  float2 zr[NB];         // depth interval of each bin triangle under any perturbation
   uint32_t sgn9[2][NB];  // bit 3k+c: coordinate c of corner k has s = -1 (by pair parity)
   float A_tri[NB];
   uint32_t n_tri[NB];
@@ -71,9 +75,10 @@ struct FastSmem {
   float tA[TABLE];
   uint32_t tn[TABLE];
   uint32_t tstamp[TABLE];
-  uint32_t tsb[TABLE];
+  uint32_t tsb[2][TABLE];  // sign bits of the stamped pair, by pair parity
   float tS[4][TABLE];
   uint32_t tcnt[TABLE];
+  uint64_t pk[kMaxPairsPerItem];  // sign keys of the run's pairs
   float m[16];
   float red[TILE_PX / 32];
   uint32_t item;
@@ -123,8 +128,11 @@ __device__ __forceinline__ uint32_t hslot(uint32_t k, int table) {
   return k & (uint32_t)(table - 1);
 }
 
+// Find or insert a texel key; the first pixel to touch the entry in this pair draws
+// the pair's signs of the texel's channels (stamp = pair + 1) into tsb[par].
 template <int TABLE>
-__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE>& sm, uint32_t key, uint32_t stamp) {
+__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE>& sm, uint32_t key, uint32_t stamp,
+                                                 const TexDev& T, uint64_t pkey, int par) {
   uint32_t slot = hslot(key, TABLE);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
@@ -134,7 +142,12 @@ __device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE>& sm, uint32_t k
       if (k == EMPTY) k = key;
     }
     if (k == key) {
-      sm.tstamp[slot] = stamp;
+      if (*(volatile uint32_t*)&sm.tstamp[slot] != stamp && atomicExch(&sm.tstamp[slot], stamp) != stamp) {
+        const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
+        uint32_t sb = 0;
+        for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << c;
+        sm.tsb[par][slot] = sb;
+      }
       return slot;
     }
     slot = (slot + 1) & (TABLE - 1);
@@ -145,6 +158,14 @@ __device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE>& sm, uint32_t k
 // Texel id (y * W + x) of footprint corner q (0: x0y0, 1: x1y0, 2: x0y1, 3: x1y1).
 __device__ __forceinline__ int foot_texel(const Foot& f, int q, int w) {
   return ((q & 2) ? f.y1 : f.y0) * w + ((q & 1) ? f.x1 : f.x0);
+}
+
+// Texel id of footprint corner q from the packed (x0,y0) id and its edge flags.
+__device__ __forceinline__ long long texel_of(uint32_t pk, int q, int w) {
+  long long t = pk & 0x3FFFFFFFu;
+  if (q & 1) t += (pk & (1u << 30)) ? -(long long)(w - 1) : 1;
+  if ((q & 2) && !(pk & (1u << 31))) t += w;
+  return t;
 }
 
 template <int TABLE>
@@ -160,39 +181,27 @@ __device__ __forceinline__ void clear_item_table(FastSmem<TABLE>& sm) {
   }
 }
 
-// Fold the previous pair's credits (table entries and triangle corners) with that pair's signs;
-// draw this pair's texel signs for the entries stamped `stamp` (0: none).
+// Fold a pair's credits (table entries and triangle corners) into the per-channel sums with
+// that pair's signs (texel signs in tsb[parity], vertex signs in sgn9[parity]).
 template <int TABLE>
-__device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE>& sm, int nb, int prev_parity, uint32_t stamp,
-                                     uint64_t pkey) {
+__device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE>& sm, int nb, int parity) {
   for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
-    const uint32_t key = sm.tkey[s];
-    if (key == EMPTY) continue;
-    const uint32_t kind = key >> 28;
-    const TexDev& T = S.tex[kind - 1];
     const uint32_t nn = sm.tn[s];
-    if (nn) {
-      const float A = sm.tA[s];
-      const uint32_t sb = sm.tsb[s];
+    if (!nn) continue;
+    const uint32_t key = sm.tkey[s];
+    const int cn = S.tex[(key >> 28) - 1].c;
+    const float A = sm.tA[s];
+    const uint32_t sb = sm.tsb[parity][s];
 #pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (c < T.c) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
-      sm.tcnt[s] += nn;
-      sm.tA[s] = 0.0f;
-      sm.tn[s] = 0u;
-    }
-    if (stamp && sm.tstamp[s] == stamp) {
-      const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
-      uint32_t sb = 0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-        if (c < T.c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << c;
-      sm.tsb[s] = sb;
-    }
+    for (int c = 0; c < 4; ++c)
+      if (c < cn) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
+    sm.tcnt[s] += nn;
+    sm.tA[s] = 0.0f;
+    sm.tn[s] = 0u;
   }
   const int j = threadIdx.x;
-  if (j < nb && prev_parity >= 0) {
-    const uint32_t sg = sm.sgn9[prev_parity][j];
+  if (j < nb) {
+    const uint32_t sg = sm.sgn9[parity][j];
     const float at = sm.A_tri[j];
     const uint32_t nt = sm.n_tri[j];
 #pragma unroll
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
-  const int n_chunks = (a.pairs + a.pairs_per_item - 1) / a.pairs_per_item;
+  const int n_chunks = (a.pair_count + a.pairs_per_item - 1) / a.pairs_per_item;
   const long long n_work = (long long)ws.counters[0] * n_chunks;
 
   for (;;) {
@@ -241,8 +250,10 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
     const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
     const uint32_t bin_beg = ws.tile_off[slot * ntl + tile];
     const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - bin_beg);
-    const int p0 = chunk * a.pairs_per_item, p1 = min(a.pairs, p0 + a.pairs_per_item);
+    const int p0 = a.pair_begin + chunk * a.pairs_per_item;
+    const int p1 = min(a.pair_begin + a.pair_count, p0 + a.pairs_per_item);
     if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
+    if (tid < p1 - p0) sm.pk[tid] = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)(p0 + tid));
     clear_item_table(sm);
     __syncthreads();
 
@@ -257,6 +268,7 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
       // version may still be, so it stays a candidate for every pixel of the tile
       if (!t.ok) sm.side[0][tid].tri = -2;
       sm.side[0][tid].margin = ws.tri_margin[(long long)slot * S.nt + tri];
+      sm.zr[tid] = ws.tri_z[(long long)slot * S.nt + tri];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         sm.vid[tid][k] = __ldg(S.pidx + 3 * tri + k);
@@ -273,24 +285,43 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
       sm.n_tri[tid] = 0u;
     }
     __syncthreads();
-    uint32_t cand[2] = {0u, 0u};
+    // nearest far end of the triangles that cover this pixel whatever the perturbation
+    float zsure = 3.4e38f;
+    for (int j = 0; j < nb; ++j) {
+      const TriS& t = sm.side[0][j];
+      if (t.tri < 0 || t.margin == 0x7FFFFFFF) continue;
+      // every vertex moves at most margin per axis, so at most sqrt(2) margin: a pixel
+      // farther than that from each edge line stays inside every perturbed version
+      bool sure = true;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
+        const float fa = (float)t.a[k], fb = (float)t.b[k];
+        const float reach = 1.41422f * (float)t.margin * sqrtf(fa * fa + fb * fb) * 1.0001f + 2.0f;
+        sure = sure && ((float)e > reach);
+      }
+      if (sure) zsure = fminf(zsure, sm.zr[j].y);
+    }
+    uint32_t cand[CMAX / 4] = {};
     int ncand = 0;
     for (int j = 0; j < nb; ++j) {
       const TriS& t = sm.side[0][j];
-      bool maybe;
-      if (t.tri == -2 || t.margin == 0x7FFFFFFF) {
-        maybe = true;
-      } else {
-        maybe = true;
+      bool maybe = true;
+      if (t.tri != -2 && t.margin != 0x7FFFFFFF) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
           const long long reach = (long long)t.margin * (long long)(abs(t.a[k]) + abs(t.b[k]));
           maybe = maybe && (e + reach >= 0);
         }
+        // surely behind a surely covering triangle: can never be the visible one
+        maybe = maybe && sm.zr[j].x <= zsure;
       }
       if (maybe) {
-        if (ncand < CMAX) cand[ncand >> 2] |= (uint32_t)j << (8 * (ncand & 3));
+        const uint32_t bits = (uint32_t)j << (8 * (ncand & 3));
+#pragma unroll
+        for (int wd = 0; wd < CMAX / 4; ++wd)
+          if ((ncand >> 2) == wd) cand[wd] |= bits;
         ++ncand;
       }
     }
@@ -303,41 +334,35 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
     float loss_acc = 0.0f;
 
     for (int pair = p0; pair < p1; ++pair) {
-      const uint64_t pkey = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)pair);
+      const uint64_t pkey = sm.pk[pair - p0];
       const int par = pair & 1;
+      // the previous pair is complete (and the candidate build is done with side[0])
       __syncthreads();
-      // ---- S: perturb (signs drawn once for both sides) and set up the bin's triangles
-      if (tid < nb) {
-        uint32_t sg = 0;
-        float3 pp[3], pm[3];
+      // ---- F: fold the previous pair's credits with its signs (other parity buffers)
+      if (pair > p0) fold(S, sm, nb, par ^ 1);
+      // ---- S: set up the bin's triangles on both sides from the projected perturbed vertices
+      {
+        const long long vb = ((long long)slot * ws.max_pairs + (pair - a.pair_begin)) * S.nv;
+        for (int t2 = tid; t2 < 2 * nb; t2 += TILE_PX) {
+          const int sd = t2 < nb ? 0 : 1, j = t2 - sd * nb;
+          PVert v[3];
+          uint32_t sg = 0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int vi = sm.vid[tid][k];
-          const float* p = S.pos + 3ll * vi;
-          float q[3];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const bool neg = sign_neg(pkey, 3ull * (uint64_t)vi + c);
-            sg |= (uint32_t)neg << (3 * k + c);
-            const float th = __ldg(p + c);
-            q[c] = neg ? -S.eps_pos : S.eps_pos;
-            (&pp[k].x)[c] = __fadd_rn(th, q[c]);
-            (&pm[k].x)[c] = __fadd_rn(th, -q[c]);
+          for (int k = 0; k < 3; ++k) {
+            const long long o = vb + sm.vid[j][k];
+            const int4 q = __ldg(ws.pverts + 2 * o + sd);
+            v[k].X = q.x;
+            v[k].Y = q.y;
+            v[k].z = __int_as_float(q.z);
+            v[k].iw = __int_as_float(q.w);
+            v[k].ok = q.x != kNotDrawn;
+            if (sd == 0) sg |= ((uint32_t)__ldg(ws.vbits + o) & 7u) << (3 * k);
           }
+          if (sd == 0) sm.sgn9[par][j] = sg;
+          Tri t;
+          setup_tri(v[0], v[1], v[2], rx, ry, t);
+          store_side(sm.side[sd][j], t, sm.btri[j]);
         }
-        sm.sgn9[par][tid] = sg;
-        const int tid_tri = sm.btri[tid];
-        PVert vp[3], vm[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          vp[k] = project(sm.m, pp[k].x, pp[k].y, pp[k].z, S.W, S.H, S.near_w);
-          vm[k] = project(sm.m, pm[k].x, pm[k].y, pm[k].z, S.W, S.H, S.near_w);
-        }
-        Tri t;
-        setup_tri(vp[0], vp[1], vp[2], rx, ry, t);
-        store_side(sm.side[0][tid], t, tid_tri);
-        setup_tri(vm[0], vm[1], vm[2], rx, ry, t);
-        store_side(sm.side[1][tid], t, tid_tri);
       }
       __syncthreads();
 
@@ -345,9 +370,7 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
       unsigned long long best[2] = {~0ull, ~0ull};
       int bj[2] = {-1, -1};
       if (valid) {
-        const int n_test = all_bin ? nb : ncand;
-        for (int q = 0; q < n_test; ++q) {
-          const int j = all_bin ? q : (int)((cand[q >> 2] >> (8 * (q & 3))) & 0xFFu);
+        auto test = [&](int j) {
 #pragma unroll
           for (int sd = 0; sd < 2; ++sd) {
             const TriS& t = sm.side[sd][j];
@@ -360,13 +383,26 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
               bj[sd] = j;
             }
           }
+        };
+        if (all_bin) {
+          for (int j = 0; j < nb; ++j) test(j);
+        } else {
+#pragma unroll
+          for (int wd = 0; wd < CMAX / 4; ++wd) {
+            uint32_t word = cand[wd];
+            const int left = ncand - 4 * wd;
+            if (left <= 0) break;
+            for (int q = 0; q < 4 && q < left; ++q, word >>= 8) test((int)(word & 0xFFu));
+          }
         }
       }
 
-      // ---- U: UV buffer values and texel keys of both sides
+      // ---- U: UV buffer values and texel keys of both sides (footprints computed once)
       float2 uvs[2];
       float bary[2][3];
-      uint32_t tslot[2][NREAD][2];  // four 16-bit slots per side and read texture
+      float ffx[2][NREAD], ffy[2][NREAD];
+      uint32_t tpk[2][NREAD];       // texel (x0,y0) id | 1<<30 if x1 wrapped | 1<<31 if y1 == y0
+      uint32_t tslot[2][NREAD][2];  // four 16-bit table slots per side and read texture
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         uvs[sd] = make_float2(0.f, 0.f);
@@ -386,45 +422,49 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
         }
 #pragma unroll
         for (int r = 0; r < NREAD; ++r) {
-          const int k = S.read_k[r];
-          const TexDev& T = S.tex[k];
+          const TexDev& T = S.rtex[r];
           const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
+          ffx[sd][r] = f.fx;
+          ffy[sd][r] = f.fy;
+          tpk[sd][r] = (uint32_t)(f.y0 * T.w + f.x0) | (f.x1 != f.x0 + 1 ? 1u << 30 : 0u) |
+                       (f.y1 == f.y0 ? 1u << 31 : 0u);
+          if (sd == 1 && bj[0] >= 0 && tpk[1][r] == tpk[0][r]) {  // same footprint on both sides
+            tslot[1][r][0] = tslot[0][r][0];
+            tslot[1][r][1] = tslot[0][r][1];
+            continue;
+          }
           uint32_t sl[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) sl[q] = table_insert(sm, tkey(k, foot_texel(f, q, T.w)), (uint32_t)pair + 1);
+          for (int q = 0; q < 4; ++q)
+            sl[q] = table_insert(sm, tkey(T.index, foot_texel(f, q, T.w)), (uint32_t)pair + 1, T, pkey, par);
           tslot[sd][r][0] = sl[0] | (sl[1] << 16);
           tslot[sd][r][1] = sl[2] | (sl[3] << 16);
         }
       }
-      __syncthreads();
+      __syncthreads();  // the pair's texel signs are drawn
 
-      // ---- G1: fold the previous pair, draw this pair's texel signs
-      fold(S, sm, nb, pair > p0 ? (par ^ 1) : -1, (uint32_t)pair + 1, pkey);
-      __syncthreads();
-
-      // ---- G2: shade both sides, f+ - f-, credits
+      // ---- G: shade both sides, f+ - f-, credits
       float3 col[2];
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         col[sd] = f3(S.bg[0], S.bg[1], S.bg[2]);
         if (bj[sd] < 0) continue;
-        float tex[4][4];
+        float tex[NREAD][4];
 #pragma unroll
         for (int r = 0; r < NREAD; ++r) {
-          const int k = S.read_k[r];
-          const TexDev& T = S.tex[k];
-          const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
-          const float wq[4] = {(1.0f - f.fx) * (1.0f - f.fy), f.fx * (1.0f - f.fy), (1.0f - f.fx) * f.fy, f.fx * f.fy};
+          const TexDev& T = S.rtex[r];
+          const float fx = ffx[sd][r], fy = ffy[sd][r];
+          const float wq[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
 #pragma unroll
           for (int c = 0; c < 4; ++c) tex[r][c] = 0.0f;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-            const long long texel = foot_texel(f, q, T.w);
+            const long long texel = texel_of(tpk[sd][r], q, T.w);
             const float* src = T.ptr + texel * T.c;
             uint32_t sb;
             if (sl != NOSLOT) {
-              sb = sm.tsb[sl];
+              sb = sm.tsb[par][sl];
             } else {
               sb = 0;
               for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(T.offset + texel * T.c + c)) << c;
@@ -457,7 +497,7 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
                 metal[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
           for (int r = 0; r < NREAD; ++r) {
-            const int role = S.tex[S.read_k[r]].role;
+            const int role = S.rtex[r].role;
             float* dst = role == ROLE_ALBEDO ? alb : role == ROLE_NORMAL ? nm : role == ROLE_ROUGHNESS ? rough : metal;
 #pragma unroll
             for (int c = 0; c < 4; ++c) dst[c] = tex[r][c];
@@ -473,50 +513,42 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
         loss_acc += 0.5f * (fp + fm);
         if (a.delta_f) a.delta_f[(((long long)slot * a.pairs + pair) * S.H + py) * S.W + px] = df;
         // vertices: the visible triangle of each side (union of corners)
-        if (bj[0] >= 0 && bj[0] == bj[1]) {
+        if (bj[0] >= 0) {
           atomicAdd(&sm.A_tri[bj[0]], df);
           atomicAdd(&sm.n_tri[bj[0]], 1u);
-        } else {
-          if (bj[0] >= 0) {
-            atomicAdd(&sm.A_tri[bj[0]], df);
-            atomicAdd(&sm.n_tri[bj[0]], 1u);
-          }
-          if (bj[1] >= 0) {
-            if (bj[0] < 0) {
-              atomicAdd(&sm.A_tri[bj[1]], df);
-              atomicAdd(&sm.n_tri[bj[1]], 1u);
-            } else {
+          if (bj[1] >= 0 && bj[1] != bj[0]) {
 #pragma unroll
-              for (int k = 0; k < 3; ++k) {
-                const int v = sm.vid[bj[1]][k];
-                if (v != sm.vid[bj[0]][0] && v != sm.vid[bj[0]][1] && v != sm.vid[bj[0]][2]) {
-                  atomicAdd(&sm.A_cor[bj[1]][k], df);
-                  atomicAdd(&sm.n_cor[bj[1]][k], 1u);
-                }
+            for (int k = 0; k < 3; ++k) {
+              const int v = sm.vid[bj[1]][k];
+              if (v != sm.vid[bj[0]][0] && v != sm.vid[bj[0]][1] && v != sm.vid[bj[0]][2]) {
+                atomicAdd(&sm.A_cor[bj[1]][k], df);
+                atomicAdd(&sm.n_cor[bj[1]][k], 1u);
               }
             }
           }
+        } else if (bj[1] >= 0) {
+          atomicAdd(&sm.A_tri[bj[1]], df);
+          atomicAdd(&sm.n_tri[bj[1]], 1u);
         }
         // texels: union of both sides' footprints of every read texture
 #pragma unroll
         for (int r = 0; r < NREAD; ++r) {
-          const int k = S.read_k[r];
-          const TexDev& T = S.tex[k];
-          int ids[2][4];
+          const TexDev& T = S.rtex[r];
+          const bool same = bj[0] >= 0 && bj[1] >= 0 && tpk[0][r] == tpk[1][r];
 #pragma unroll
           for (int sd = 0; sd < 2; ++sd) {
-            if (bj[sd] < 0) continue;
-            const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
+            if (bj[sd] < 0 || (sd == 1 && same)) continue;
+            int ids[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ids[sd][q] = foot_texel(f, q, T.w);
+            for (int q = 0; q < 4; ++q) ids[q] = (int)texel_of(tpk[sd][r], q, T.w);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               bool dup = false;
 #pragma unroll
-              for (int o = 0; o < q; ++o) dup = dup || ids[sd][o] == ids[sd][q];
+              for (int o = 0; o < q; ++o) dup = dup || ids[o] == ids[q];
               if (sd == 1 && bj[0] >= 0) {
 #pragma unroll
-                for (int o = 0; o < 4; ++o) dup = dup || ids[0][o] == ids[1][q];
+                for (int o = 0; o < 4; ++o) dup = dup || (int)texel_of(tpk[0][r], o, T.w) == ids[q];
               }
               if (dup) continue;
               const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
@@ -524,7 +556,7 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
                 atomicAdd(&sm.tA[sl], df);
                 atomicAdd(&sm.tn[sl], 1u);
               } else {
-                const long long base = T.offset + (long long)ids[sd][q] * T.c;
+                const long long base = T.offset + (long long)ids[q] * T.c;
                 for (int c = 0; c < T.c; ++c) {
                   atomicAdd(a.grad + base + c, sign_neg(pkey, (uint64_t)(base + c)) ? -df : df);
                   atomicAdd(a.counts + base + c, 1u);
@@ -536,7 +568,7 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
       }
     }
     __syncthreads();
-    fold(S, sm, nb, (p1 - 1) & 1, 0u, 0ull);
+    fold(S, sm, nb, (p1 - 1) & 1);
     __syncthreads();
     // ---- flush: one global atomic per credited vertex corner / texel and channel
     for (int s = tid; s < TABLE; s += blockDim.x) {

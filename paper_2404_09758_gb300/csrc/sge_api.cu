@@ -38,8 +38,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t tri_rect, tri_margin, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf, total;
-  int max_views;
+  size_t tri_rect, tri_margin, tri_z, pverts, vbits, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf, total;
+  int max_views, max_pairs;
   long long bin_capacity;
 };
 
@@ -84,6 +84,10 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
   L.tri_rect = take(sizeof(int4) * (size_t)L.max_views * d->n_triangles);
   L.tri_margin = take(sizeof(int) * (size_t)L.max_views * d->n_triangles);
+  L.tri_z = take(sizeof(float2) * (size_t)L.max_views * d->n_triangles);
+  L.max_pairs = (c && c->max_pairs_per_call > 0) ? c->max_pairs_per_call : 64;
+  L.pverts = take(sizeof(int4) * 2 * (size_t)L.max_views * L.max_pairs * d->n_vertices);
+  L.vbits = take((size_t)L.max_views * L.max_pairs * d->n_vertices);
   L.tile_count = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
   L.tile_off = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl + 1));
   L.tile_cur = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
@@ -120,6 +124,7 @@ void make_dev(const sge_scene_desc* d, SceneDev& S) {
     T.eps = t.eps;
     T.role = t.role;
     T.offset = off;
+    T.index = k;
     off += (long long)t.width * t.height * t.channels;
     if (first_of_role[t.role] < 0) first_of_role[t.role] = k;
   }
@@ -132,6 +137,7 @@ void make_dev(const sge_scene_desc* d, SceneDev& S) {
     S.tex[k].read = read;
     if (read) S.read_k[S.nread++] = k;
   }
+  for (int r = 0; r < S.nread; ++r) S.rtex[r] = S.tex[S.read_k[r]];
   S.mvp = d->mvp;
   S.cam_pos = d->cam_pos;
   S.nviews = d->n_views;
@@ -204,6 +210,10 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   Workspace& w = s->ws;
   w.tri_rect = reinterpret_cast<int4*>(base + L.tri_rect);
   w.tri_margin = reinterpret_cast<int*>(base + L.tri_margin);
+  w.tri_z = reinterpret_cast<float2*>(base + L.tri_z);
+  w.pverts = reinterpret_cast<int4*>(base + L.pverts);
+  w.vbits = reinterpret_cast<uint8_t*>(base + L.vbits);
+  w.max_pairs = L.max_pairs;
   w.tile_count = reinterpret_cast<uint32_t*>(base + L.tile_count);
   w.tile_off = reinterpret_cast<uint32_t*>(base + L.tile_off);
   w.tile_cur = reinterpret_cast<uint32_t*>(base + L.tile_cur);
@@ -227,6 +237,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   s->grid_fast = sms * bps;
   s->grid_heavy = sms * estimate_blocks_per_sm();
   if (s->cfg.pairs_per_item <= 0) s->cfg.pairs_per_item = 16;
+  if (s->cfg.pairs_per_item > kMaxPairsPerItem) s->cfg.pairs_per_item = kMaxPairsPerItem;
   *out = s;
   return SGE_OK;
 }
@@ -275,12 +286,20 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
   int rc = views_of(s, view_ids, n_views, vl);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  EstimateArgs a{seed, iter, pairs_per_view, s->cfg.pairs_per_item, grad_sums, counts, loss_out, delta_f_out};
+  EstimateArgs a{seed, iter, pairs_per_view, s->cfg.pairs_per_item, 0, pairs_per_view, grad_sums, counts, loss_out,
+                 delta_f_out};
   cudaError_t e = cudaSuccess;
   if (delta_f_out)
     e = cudaMemsetAsync(delta_f_out, 0, sizeof(float) * (size_t)n_views * pairs_per_view * s->dev.W * s->dev.H, st);
   if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
-  if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, a, s->grid_fast, s->grid_heavy, st);
+  // pairs run in blocks of at most max_pairs_per_call (the projected-vertex buffer holds one block)
+  for (int p0 = 0; p0 < pairs_per_view && e == cudaSuccess; p0 += s->ws.max_pairs) {
+    EstimateArgs b = a;
+    b.pair_begin = p0;
+    b.pair_count = pairs_per_view - p0 < s->ws.max_pairs ? pairs_per_view - p0 : s->ws.max_pairs;
+    e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
+    if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, b, s->grid_fast, s->grid_heavy, st);
+  }
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
 }
 
@@ -294,7 +313,7 @@ int sge_estimate_grad_plain(sge_scene* s, uint64_t seed, uint32_t iter, const in
   int rc = views_of(s, view_ids, n_views, vl);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  EstimateArgs a{seed, iter, pairs_per_view, 1, grad_sums, counts, loss_out, nullptr};
+  EstimateArgs a{seed, iter, pairs_per_view, 1, 0, pairs_per_view, grad_sums, counts, loss_out, nullptr};
   cudaError_t e = launch_binning(s->dev, s->ws, vl, st);
   for (int j = 0; j < n_views && e == cudaSuccess; ++j)
     for (int n = 0; n < pairs_per_view && e == cudaSuccess; ++n)

@@ -82,6 +82,12 @@ __device__ __forceinline__ PVert project(const float* m, float x, float y, float
   return v;
 }
 
+// int64 -> float, correctly rounded; values that fit 32 bits take the cheaper
+// 32-bit conversion, which rounds the same value to the same float.
+__device__ __forceinline__ float ll2f_rn(long long v) {
+  return (v == (long long)(int)v) ? __int2float_rn((int)v) : __ll2float_rn(v);
+}
+
 // ---------------------------------------------------------------- triangle setup
 // Edge function of the edge opposite vertex k (a = k+1, b = k+2 mod 3):
 //   E_k(P) = (Xb-Xa)(Py-Ya) - (Yb-Ya)(Px-Xa),   E_0+E_1+E_2 = twice the signed area.
@@ -125,7 +131,7 @@ __device__ __forceinline__ void setup_tri(const PVert& v0, const PVert& v1, cons
     t.b[k] = sg * (B.X - A.X);
     t.bias[k] = (t.a[k] > 0 || (t.a[k] == 0 && t.b[k] > 0)) ? 0 : -1;
   }
-  t.inv_area = __fdiv_rn(1.0f, __ll2float_rn(area > 0 ? area : -area));
+  t.inv_area = __fdiv_rn(1.0f, ll2f_rn(area > 0 ? area : -area));
   t.z[0] = v0.z; t.z[1] = v1.z; t.z[2] = v2.z;
   t.iw[0] = v0.iw; t.iw[1] = v1.iw; t.iw[2] = v2.iw;
 }
@@ -138,7 +144,7 @@ __device__ __forceinline__ uint32_t ordered_bits(float z) {
 // Barycentric weights lambda_k = E_k / area as floats.
 __device__ __forceinline__ void lambdas(const long long e[3], float inv_area, float l[3]) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) l[k] = __fmul_rn(__ll2float_rn(e[k]), inv_area);
+  for (int k = 0; k < 3; ++k) l[k] = __fmul_rn(ll2f_rn(e[k]), inv_area);
 }
 
 __device__ __forceinline__ float interp_depth(const float l[3], const float z[3]) {
@@ -168,9 +174,14 @@ struct Foot {
   float fx, fy;
 };
 
+// i mod n in [0, n); one add or subtract for the i in [-n, 2n) a texel lookup produces
 __device__ __forceinline__ int wrap_i(int i, int n) {
-  int r = i % n;
-  return r < 0 ? r + n : r;
+  int r = i < 0 ? i + n : (i >= n ? i - n : i);
+  if (r < 0 || r >= n) {
+    r = i % n;
+    r = r < 0 ? r + n : r;
+  }
+  return r;
 }
 __device__ __forceinline__ int clamp_i(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
 

@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/sge.h"
+#include "sge.h"
 
 namespace sge {
 
@@ -12,7 +12,9 @@ constexpr int SGE_MAX_TEX_DEV = SGE_MAX_TEXTURES;
 constexpr int MAX_READ = 4;              // albedo, normal, roughness, metallic
 constexpr int TILE = 16;                 // tile edge in pixels; one CTA thread per pixel
 constexpr int TILE_PX = TILE * TILE;     // 256 threads
-constexpr int kLightBin = 256;           // bins up to this size use the staged fast path
+constexpr int kLightBin = 256;           // bins up to this size use the fast path
+constexpr int kMaxPairsPerItem = 64;     // longest run of pairs one work item takes
+constexpr int kNotDrawn = (int)0x80000000;  // projected X of a vertex its triangles drop
 constexpr int ROLE_ALBEDO = SGE_ROLE_ALBEDO, ROLE_NORMAL = SGE_ROLE_NORMAL;
 constexpr int ROLE_ROUGHNESS = SGE_ROLE_ROUGHNESS, ROLE_METALLIC = SGE_ROLE_METALLIC;
 constexpr int SHADE_UNLIT = SGE_SHADE_UNLIT, SHADE_LAMBERT = SGE_SHADE_LAMBERT, SHADE_GGX = SGE_SHADE_GGX;
@@ -24,6 +26,7 @@ struct TexDev {
   int role;
   int read;          // does the shading model read this texture (so its texels contribute)?
   long long offset;  // first parameter index of this texture in theta
+  int index;         // position of this texture in the scene's list
 };
 
 // Device view of a scene, passed to kernels by value.
@@ -40,6 +43,7 @@ struct SceneDev {
   TexDev tex[SGE_MAX_TEX_DEV];
   int nread;                 // textures the shading model reads (at most one per role)
   int read_k[MAX_READ];      // their indices in tex[]
+  TexDev rtex[MAX_READ];     // copies of tex[read_k[r]], so kernels index them with constants
   const float* mvp;
   const float* cam_pos;
   int nviews;
@@ -63,6 +67,9 @@ struct ViewList {
 struct Workspace {
   int4* tri_rect;        // [max_views][nt] tile rectangle (x0,y0,x1,y1) of each triangle's bin span
   int* tri_margin;       // [max_views][nt] perturbation margin of each triangle, fixed-point units
+  float2* tri_z;         // [max_views][nt] depth interval of each triangle under any perturbation
+  int4* pverts;          // [max_views][max_pairs][nv][2] projected perturbed vertices (X, Y, z, iw), sides +/-
+  uint8_t* vbits;        // [max_views][max_pairs][nv] bits 0-2: s = -1 for x,y,z; 3: side + drawable; 4: side -
   uint32_t* tile_count;  // [max_views][n_tiles]
   uint32_t* tile_off;    // [max_views][n_tiles + 1] exclusive scan of counts
   uint32_t* tile_cur;    // [max_views][n_tiles] fill cursors
@@ -75,6 +82,7 @@ struct Workspace {
   float* dfbuf;              // [H*W] staged loss differences
   long long bin_capacity;
   int max_views;
+  int max_pairs;
 };
 
 // ---- kernels launchers (all asynchronous on `st`)
@@ -85,8 +93,10 @@ cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewLis
 struct EstimateArgs {
   uint64_t seed;
   uint32_t iter;
-  int pairs;
+  int pairs;           // pairs per view of the whole call
   int pairs_per_item;
+  int pair_begin;      // the block of pairs this launch covers: [pair_begin, pair_begin + pair_count)
+  int pair_count;
   float* grad;
   uint32_t* counts;
   float* loss;
@@ -97,6 +107,9 @@ cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewLi
                             const EstimateArgs& a, int grid_fast, int grid_heavy, cudaStream_t st);
 cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                         int grid, cudaStream_t st);
+// Perturbed, projected vertices of both sides for every (view slot, pair) of a block of pairs.
+cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
+                               cudaStream_t st);
 int estimate_blocks_per_sm();
 int fast_blocks_per_sm(int shading);
 

@@ -33,7 +33,8 @@ constexpr long long kBinEntries = SGE_STATIC_BIN_ENTRIES;
 constexpr size_t al(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffRect = 0;
 constexpr size_t kOffMargin = kOffRect + al(sizeof(int4) * kMaxTriangles);
-constexpr size_t kOffCount = kOffMargin + al(sizeof(int) * kMaxTriangles);
+constexpr size_t kOffZ = kOffMargin + al(sizeof(int) * kMaxTriangles);
+constexpr size_t kOffCount = kOffZ + al(sizeof(float2) * kMaxTriangles);
 constexpr size_t kOffTileOff = kOffCount + al(sizeof(uint32_t) * kMaxTiles);
 constexpr size_t kOffCur = kOffTileOff + al(sizeof(uint32_t) * (kMaxTiles + 1));
 constexpr size_t kOffItems = kOffCur + al(sizeof(uint32_t) * kMaxTiles);
@@ -118,7 +119,7 @@ extern "C" int sge_render_idb_static(const sge_scene_desc* d, int32_t view, uint
   int first_of_role[4] = {-1, -1, -1, -1};
   for (int k = 0; k < d->n_textures; ++k) {
     const sge_texture& t = d->textures[k];
-    S.tex[k] = TexDev{t.texels, t.width, t.height, t.channels, t.eps, t.role, 0, off};
+    S.tex[k] = TexDev{t.texels, t.width, t.height, t.channels, t.eps, t.role, 0, off, k};
     off += (long long)t.width * t.height * t.channels;
     if (first_of_role[t.role] < 0) first_of_role[t.role] = k;
   }
@@ -149,10 +150,13 @@ extern "C" int sge_render_idb_static(const sge_scene_desc* d, int32_t view, uint
   S.tiles_y = (d->height + TILE - 1) / TILE;
 
   char* b = static_cast<char*>(base);
+  // every field the binning and render kernels use points into the scratch; the
+  // estimator's buffers (projected vertices, staged keys) stay NULL and are never touched
   Workspace ws;
   memset(&ws, 0, sizeof(ws));
   ws.tri_rect = reinterpret_cast<int4*>(b + kOffRect);
   ws.tri_margin = reinterpret_cast<int*>(b + kOffMargin);
+  ws.tri_z = reinterpret_cast<float2*>(b + kOffZ);
   ws.tile_count = reinterpret_cast<uint32_t*>(b + kOffCount);
   ws.tile_off = reinterpret_cast<uint32_t*>(b + kOffTileOff);
   ws.tile_cur = reinterpret_cast<uint32_t*>(b + kOffCur);

@@ -42,7 +42,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(sge_texture), sizeof(sge_scene_desc), sizeof(sge_config), sizeof(sge_opt));
   printf("%zu %zu %zu %zu\n", offsetof(sge_scene_desc, textures), offsetof(sge_scene_desc, mvp),
          offsetof(sge_scene_desc, targets), offsetof(sge_scene_desc, ambient));
-  printf("%zu %zu\n", offsetof(sge_opt, beta1), offsetof(sge_opt, t));
+  printf("%zu %zu %zu\n", offsetof(sge_opt, beta1), offsetof(sge_opt, t), offsetof(sge_config, max_pairs_per_call));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -55,7 +55,7 @@ int main(void) {
     S = _abi.SceneDesc
     want = [ctypes.sizeof(_abi.Texture), ctypes.sizeof(S), ctypes.sizeof(_abi.Config), ctypes.sizeof(_abi.Opt),
             S.textures.offset, S.mvp.offset, S.targets.offset, S.ambient.offset,
-            _abi.Opt.beta1.offset, _abi.Opt.t.offset]
+            _abi.Opt.beta1.offset, _abi.Opt.t.offset, _abi.Config.max_pairs_per_call.offset]
     assert got == want
 
 
