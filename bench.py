@@ -36,8 +36,13 @@ UNIT = "pixel-pairs/s"
 WORKLOAD = "sphere8k_tex512_r512_8views_x_64pairs"
 N_VIEWS, PAIRS, RENDER = 8, 64, 512
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# lane-instructions one pixel pair costs in the estimator kernel; see the design doc (roofline)
-ALU_OPS_PER_PIXEL_PAIR = None
+# Roofline of the dominant kernel (k_estimate_fast): it is bound by instruction issue on the
+# SMs' integer/FP lanes, not by HBM or tensor cores.  Per-unit figure: thread instructions the
+# kernel executes per antithetic pixel pair of the workload (smsp__inst_executed x active threads
+# per warp / pixel pairs), and its DRAM traffic per launch, both from the ncu capture summarised
+# in profiles/k_estimate_fast_sphere8k_r512.md (same kernel source).
+ALU_INSTR_PER_PIXEL_PAIR = 1389.0
+DRAM_BYTES_PER_LAUNCH = 101.42e6
 
 
 def dist_env():
@@ -177,12 +182,12 @@ def run_ours(args):
     lr_tex = [t[1] for t in g.textures]
     n_total = N_VIEWS * PAIRS
     st = torch.cuda.Stream(device=dev)
-    step_no = [1]
 
     def iteration(it, t):
         loss.zero_()
         g.estimate_grad(1, it, views, PAIRS, grad, counts, loss=loss, stream=st)
-        g.step(STEP_ADAM, grad, counts, n_total, g.textures and sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+        # Adam with the paper's settings: beta1 0.9, beta2 0.999, learning rate = eps (Section 5)
+        g.step(STEP_ADAM, grad, counts, n_total, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
 
     # contributions of one iteration (parameter gradients credited), counted exactly
     with torch.cuda.stream(st):
@@ -288,12 +293,13 @@ def run_ours(args):
     clocks = clk.summary()
     sm_clock_mhz = peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    roofline = None
-    if ALU_OPS_PER_PIXEL_PAIR:
-        peak = n_sm * 128 * sm_clock_mhz * 1e6 / 1e12  # lane-ops/s in T
-        achieved = ALU_OPS_PER_PIXEL_PAIR * px_per_step / (est_ms / 1000.0) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": "k_estimate (sge_estimate_grad)"}
+    # peak: every SM issues one instruction per lane per cycle on its 128 FP32/INT32 lanes
+    peak = n_sm * 128 * sm_clock_mhz * 1e6 / 1e12
+    achieved = ALU_INSTR_PER_PIXEL_PAIR * px_per_step / (est_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+                "frac": achieved / peak, "traffic": DRAM_BYTES_PER_LAUNCH,
+                "kernel": "k_estimate_fast (timed as the whole sge_estimate_grad call)",
+                "peak_source": f"{n_sm} SMs x 128 lanes x {sm_clock_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -311,7 +317,9 @@ def run_ours(args):
             "batched_over_plain": plain_ms / (1000.0 * t_total / args.steps),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 6 * args.steps,
+            # per iteration: 3 binning kernels, the vertex pass, the fast and the heavy-bin
+            # estimator, the background-loss kernel and the step kernel
+            "gpu_launches": 8 * args.steps,
             "clocks": clocks}
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
