@@ -174,6 +174,18 @@ int sge_estimate_grad_plain(sge_scene *scene, uint64_t seed, uint32_t iter, cons
                             int32_t n_views, int32_t pairs_per_view, float *grad_sums,
                             uint32_t *counts, float *loss_out, sge_stream_t stream);
 
+/* Image error of the unperturbed scene, f(theta) = sum over pixels of
+ * || I_p(theta) - I_p ||^2 (Table 1), per view: loss_out[j] (device [n_views]
+ * float32) ACCUMULATES view view_ids[j]'s error.  The forward value of the
+ * autograd form whose backward is sge_estimate_grad + sge_gradient. */
+int sge_loss(sge_scene *scene, const int32_t *view_ids, int32_t n_views, float *loss_out, sge_stream_t stream);
+
+/* The gradient estimate of Eq. 9 from accumulated sums: out[i] = scale *
+ * grad_sums[i] / (2 eps_i n_pairs_total) (device [d] float32; scale is a device
+ * float32 scalar, NULL for 1).  Leaves grad_sums untouched. */
+int sge_gradient(sge_scene *scene, const float *grad_sums, int64_t n_pairs_total, const float *scale, float *out,
+                 sge_stream_t stream);
+
 /* Descent step D (Section 5) on every parameter group, then zero grad_sums and
  * counts.  g_i = grad_sums[i] / (2 eps_i n_pairs_total) (Eq. 9; for
  * SGE_STEP_SGD_MEAN, / (2 eps_i max(counts[i], 1))).  SGD: theta -= lr g.  Adam:

@@ -19,8 +19,8 @@ from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_TEXTURES, MAX_VIEWS_PER_
                    STEP_SGD, STEP_SGD_MEAN, SGEError)
 from ._build import build
 
-__all__ = ["Scene", "SGEError", "build", "load", "STEP_SGD", "STEP_ADAM", "STEP_SGD_MEAN", "OK",
-           "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
+__all__ = ["Scene", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
+           "STEP_SGD_MEAN", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
 
 
 def load(build_if_missing: bool = False):
@@ -222,6 +222,22 @@ class Scene:
         _abi.check(_abi.load().sge_estimate_grad_plain(self._h, int(seed), int(it), arr, n, int(pairs_per_view),
                                                        _ptr(grad), _ptr(counts), _ptr(loss), _stream_ptr(stream)))
 
+    def loss(self, view_ids: Sequence[int], out=None, stream=None):
+        """Image error f(theta) of the unperturbed scene per listed view (Table 1), [n] float32."""
+        torch = _torch()
+        out = torch.zeros(len(view_ids), dtype=torch.float32, device=self.device) if out is None else out
+        arr, n = self._views(view_ids)
+        _abi.check(_abi.load().sge_loss(self._h, arr, n, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def gradient(self, grad, n_pairs_total: int, scale=None, out=None, stream=None):
+        """Eq. 9's estimate from accumulated sums: scale * grad / (2 eps N), flat [d] float32."""
+        torch = _torch()
+        out = torch.empty(self.n_params, dtype=torch.float32, device=self.device) if out is None else out
+        _abi.check(_abi.load().sge_gradient(self._h, _ptr(grad), int(n_pairs_total), _ptr(scale), _ptr(out),
+                                            _stream_ptr(stream)))
+        return out
+
     def step(self, kind: int, grad, counts, n_pairs_total: int, lr_pos: float, lr_tex: Sequence[float],
              m=None, v=None, t: int = 1, beta1: float = 0.9, beta2: float = 0.999, adam_eps: float = 1e-8,
              stream=None) -> None:
@@ -234,3 +250,59 @@ class Scene:
         o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), int(t)
         _abi.check(_abi.load().sge_step(self._h, C.byref(o), _ptr(grad), _ptr(counts), int(n_pairs_total),
                                         _ptr(m), _ptr(v), _stream_ptr(stream)))
+
+
+def _make_function():
+    torch = _torch()
+
+    class SGEFunction(torch.autograd.Function):
+        """f(theta) = sum over views of the image error (forward: render + L2 in the library);
+        backward: per view, the per-pixel stochastic estimate of Eq. 9 over `pairs`
+        antithetic pairs for (seed, iteration), summed over the views
+        (sge_estimate_grad + sge_gradient), times the incoming gradient.  `params` must
+        be the scene's own parameter tensors."""
+
+        @staticmethod
+        def forward(ctx, scene, spec, *params):
+            for p, q in zip(params, scene.param_groups()):
+                if p.data_ptr() != q.data_ptr():
+                    raise ValueError("SGEFunction: params must be the scene's own parameter tensors")
+            ctx.scene, ctx.spec = scene, spec
+            return scene.loss(spec["views"]).sum()
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            scene, spec = ctx.scene, ctx.spec
+            grad, counts = scene.new_grad_buffers()
+            scene.estimate_grad(spec["seed"], spec["iter"], spec["views"], spec["pairs"], grad, counts)
+            scale = grad_out.reshape(1).to(dtype=torch.float32).contiguous()
+            # the forward sums the views' errors, so its gradient sums the per-view estimates:
+            # Eq. 9 averaged over the pairs of each view only
+            flat = scene.gradient(grad, spec["pairs"], scale=scale)
+            outs, o = [], 0
+            for g in scene.param_groups():
+                outs.append(flat[o:o + g.numel()].view_as(g))
+                o += g.numel()
+            return (None, None, *outs)
+
+    return SGEFunction
+
+
+_fn_cache = {}
+
+
+def __getattr__(name):
+    if name == "SGEFunction":
+        if "f" not in _fn_cache:
+            _fn_cache["f"] = _make_function()
+        return _fn_cache["f"]
+    raise AttributeError(name)
+
+
+def sge_loss(scene: Scene, seed: int, it: int, views: Sequence[int], pairs: int):
+    """Differentiable image error: forward renders, backward estimates (Eq. 9) with the given seeds."""
+    fn = __getattr__("SGEFunction")
+    params = scene.param_groups()
+    for p in params:
+        p.requires_grad_(True)
+    return fn.apply(scene, {"seed": int(seed), "iter": int(it), "views": list(views), "pairs": int(pairs)}, *params)

@@ -18,7 +18,7 @@ STEP_SGD, STEP_ADAM, STEP_SGD_MEAN = 0, 1, 2
 
 EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_targets", "sge_validate",
            "sge_render_idb", "sge_estimate_grad", "sge_estimate_grad_plain", "sge_step", "sge_status",
-           "sge_destroy_scene", "sge_last_error", "sge_render_idb_static")
+           "sge_destroy_scene", "sge_last_error", "sge_render_idb_static", "sge_loss", "sge_gradient")
 
 
 class Texture(C.Structure):
@@ -86,6 +86,8 @@ def load(build_if_missing: bool = False):
         L.sge_step.argtypes = [P, P, P, P, I64, P, P, P]
         L.sge_status.argtypes = [P, P, C.POINTER(I32)]
         L.sge_render_idb_static.argtypes = [P, I32, U64, U32, U32, I32, P, P, P, P, P]
+        L.sge_loss.argtypes = [P, P, I32, P, P]
+        L.sge_gradient.argtypes = [P, P, I64, P, P, P]
         L.sge_destroy_scene.argtypes = [P]
         L.sge_destroy_scene.restype = None
         L.sge_last_error.argtypes = []

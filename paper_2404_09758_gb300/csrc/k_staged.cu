@@ -92,6 +92,49 @@ __global__ void __launch_bounds__(TILE_PX) k_render(SceneDev S, Workspace ws, in
   if (rgb) rgb[3 * p] = sf.rgb.x, rgb[3 * p + 1] = sf.rgb.y, rgb[3 * p + 2] = sf.rgb.z;
 }
 
+// Unperturbed render of one view reduced to its image error f = sum_p || I_p(theta) - I_p ||^2
+// (Table 1): the forward value of the autograd form.  Adds the view's sum to loss[slot].
+__global__ void __launch_bounds__(TILE_PX) k_render_loss(SceneDev S, Workspace ws, int slot, int view, float* loss) {
+  __shared__ RSmem sm[1];
+  __shared__ float red[TILE_PX / 32];
+  const int tile = blockIdx.x;
+  const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+  const int dx = threadIdx.x % TILE, dy = threadIdx.x / TILE;
+  const int px = tx * TILE + dx, py = ty * TILE + dy;
+  const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
+  if (threadIdx.x < 16) sm[0].m[threadIdx.x] = S.mvp[16 * view + threadIdx.x];
+  __syncthreads();
+  unsigned long long best[1];
+  const int sides[1] = {0};
+  raster_tile<1>(S, ws, sm, slot, tile, 0, sides, best, rx, ry, dx, dy);
+  float f = 0.0f;
+  if (px < S.W && py < S.H) {
+    float3 c = f3(S.bg[0], S.bg[1], S.bg[2]);
+    if (best[0] != ~0ull) {
+      const int tri = (int)(best[0] & 0xFFFFFFFFu);
+      Tri t;
+      setup_from_scene(S, sm[0].m, tri, 0, 0, rx, ry, t);
+      long long e[3];
+      cover(t, dx, dy, e);
+      Surf sf;
+      surface(S, view, tri, t, e, 0, 0, sf);
+      c = sf.rgb;
+    }
+    const float* tp = S.targets + (((long long)view * S.H + py) * S.W + px) * 3;
+    const float d0 = c.x - __ldg(tp), d1 = c.y - __ldg(tp + 1), d2 = c.z - __ldg(tp + 2);
+    f = d0 * d0 + d1 * d1 + d2 * d2;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sum = 0.0f;
+    for (int i = 0; i < TILE_PX / 32; ++i) sum += red[i];
+    atomicAdd(loss + slot, sum);
+  }
+}
+
 // Plain path, step R: both sides' depth|ID and UV buffers of one estimate.
 __global__ void __launch_bounds__(TILE_PX) k_raster_pair(SceneDev S, Workspace ws, int slot, int view, uint64_t key) {
   __shared__ RSmem sm[2];
@@ -208,6 +251,12 @@ __global__ void k_validate(SceneDev S, uint32_t* status) {
 cudaError_t launch_render(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key, int side,
                           unsigned long long* keys, float2* uv, float* rgb, cudaStream_t st) {
   k_render<<<n_tiles(S), TILE_PX, 0, st>>>(S, ws, slot, view, key, side, keys, uv, rgb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_render_loss(const SceneDev& S, const Workspace& ws, int slot, int view, float* loss,
+                               cudaStream_t st) {
+  k_render_loss<<<n_tiles(S), TILE_PX, 0, st>>>(S, ws, slot, view, loss);
   return cudaGetLastError();
 }
 

@@ -45,7 +45,51 @@ __global__ void k_step(StepGroups G, int kind, float* grad, uint32_t* counts, fl
   }
 }
 
+// g_i = scale * grad_i / (2 eps_i n_total): the estimate of Eq. 9 (scale: device scalar or NULL).
+__global__ void k_gradient(StepGroups G, const float* grad, float inv_n, const float* scale, float* out) {
+  const long long d = G.begin[G.n];
+  const float sc = scale ? *scale : 1.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (long long)gridDim.x * blockDim.x) {
+    int g = 0;
+#pragma unroll 1
+    while (g + 1 < G.n && i >= G.begin[g + 1]) ++g;
+    out[i] = sc * (grad[i] * inv_n / (2.0f * G.eps[g]));
+  }
+}
+
+StepGroups groups_of(const SceneDev& S) {
+  StepGroups G;
+  G.n = 1 + S.ntex;
+  G.begin[0] = 0;
+  G.theta[0] = const_cast<float*>(S.pos);
+  G.eps[0] = S.eps_pos;
+  G.lr[0] = 0.0f;
+  for (int k = 0; k < S.ntex; ++k) {
+    G.begin[k + 1] = S.tex[k].offset;
+    G.theta[k + 1] = const_cast<float*>(S.tex[k].ptr);
+    G.eps[k + 1] = S.tex[k].eps;
+    G.lr[k + 1] = 0.0f;
+  }
+  G.begin[G.n] = S.n_params;
+  return G;
+}
+
+int grid_for(long long n) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long blocks = (n + 255) / 256;
+  if (blocks > 8ll * sms) blocks = 8ll * sms;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
 }  // namespace
+
+cudaError_t launch_gradient(const SceneDev& S, const float* grad, long long n_total, const float* scale, float* out,
+                            cudaStream_t st) {
+  k_gradient<<<grid_for(S.n_params), 256, 0, st>>>(groups_of(S), grad, (float)(1.0 / (double)n_total), scale, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32_t* counts, long long n_total,
                         float* m, float* v, cudaStream_t st) {

@@ -340,6 +340,29 @@ int sge_step(sge_scene* s, const sge_opt* o, float* grad_sums, uint32_t* counts,
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_step");
 }
 
+int sge_loss(sge_scene* s, const int32_t* view_ids, int32_t n_views, float* loss_out, sge_stream_t stream) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  if (!loss_out) return fail(SGE_ERR_INVALID_ARG, "loss_out must be non-NULL");
+  ViewList vl;
+  int rc = views_of(s, view_ids, n_views, vl);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_binning(s->dev, s->ws, vl, st);
+  for (int j = 0; j < n_views && e == cudaSuccess; ++j) e = launch_render_loss(s->dev, s->ws, j, vl.id[j], loss_out, st);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_loss");
+}
+
+int sge_gradient(sge_scene* s, const float* grad_sums, int64_t n_pairs_total, const float* scale, float* out,
+                 sge_stream_t stream) {
+  if (!s || !grad_sums || !out) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  if (n_pairs_total < 1) return fail(SGE_ERR_INVALID_ARG, "n_pairs_total must be >= 1");
+  if (s->desc.eps_pos <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "eps_pos must be > 0 to form Eq. 9's estimate");
+  for (int k = 0; k < s->dev.ntex; ++k)
+    if (s->dev.tex[k].eps <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be > 0", k);
+  cudaError_t e = launch_gradient(s->dev, grad_sums, n_pairs_total, scale, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_gradient");
+}
+
 int sge_status(sge_scene* s, sge_stream_t stream, int32_t* device_status) {
   if (!s || !device_status) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
   uint32_t v = 0;

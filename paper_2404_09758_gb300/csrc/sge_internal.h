@@ -120,6 +120,12 @@ cudaError_t launch_render(const SceneDev& S, const Workspace& ws, int slot, int 
 cudaError_t launch_plain_pair(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key,
                               const EstimateArgs& a, float loss_scale, cudaStream_t st);
 
+// Image error of unperturbed renders (forward of the autograd form), added to loss[slot].
+cudaError_t launch_render_loss(const SceneDev& S, const Workspace& ws, int slot, int view, float* loss,
+                               cudaStream_t st);
+// out = scale * grad / (2 eps n_total) per parameter (Eq. 9).
+cudaError_t launch_gradient(const SceneDev& S, const float* grad, long long n_total, const float* scale, float* out,
+                            cudaStream_t st);
 cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32_t* counts,
                         long long n_total, float* m, float* v, cudaStream_t st);
 cudaError_t launch_validate(const SceneDev& S, uint32_t* status, cudaStream_t st);
