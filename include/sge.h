@@ -41,6 +41,8 @@ extern "C" {
 
 #define SGE_MAX_TEXTURES 8
 #define SGE_MAX_VIEWS_PER_CALL 64
+#define SGE_MAX_BATCH 64        /* assets of one sge_estimate_grad_batch call */
+#define SGE_MAX_BATCH_VIEWS 8   /* views per asset of one batched call        */
 
 typedef enum {
     SGE_OK = 0,
@@ -98,7 +100,7 @@ typedef struct {
 /* Tuning knobs; zero-initialise for defaults. */
 typedef struct {
     int32_t max_views_per_call; /* views per estimate call the workspace is sized for (default n_views, <= 64) */
-    int64_t bin_capacity;       /* triangle-tile bin entries over those views (default 16 * n_triangles * views) */
+    int64_t bin_capacity;       /* triangle-tile bin entries over those views (default (6 n_triangles + 8 tiles) * views) */
     int32_t pairs_per_item;     /* antithetic pairs one CTA runs per (view, tile) item (default 16, <= 64) */
     int32_t blocks_per_sm;      /* persistent CTAs per SM (default: as many as fit) */
     int32_t max_pairs_per_call; /* pairs per view projected at once (default 64); more run in blocks */
@@ -195,6 +197,49 @@ int sge_gradient(sge_scene *scene, const float *grad_sums, int64_t n_pairs_total
 int sge_step(sge_scene *scene, const sge_opt *opt, float *grad_sums, uint32_t *counts,
              int64_t n_pairs_total, float *adam_m, float *adam_v, sge_stream_t stream);
 
+/* One asset of a batched call: a scene with its views and its own outputs. */
+typedef struct {
+    sge_scene *scene;          /* distinct within one call                                  */
+    const int32_t *view_ids;   /* host, n_views distinct view indices of this scene         */
+    int32_t n_views;           /* 1..SGE_MAX_BATCH_VIEWS and <= its max_views_per_call      */
+    float *grad_sums;          /* device [d of this scene] float32, accumulates             */
+    uint32_t *counts;          /* device [d] uint32, accumulates                            */
+    float *loss_out;           /* device [n_views] float32 or NULL, accumulates             */
+} sge_batch_entry;
+
+/* Launch shape of a batched call; zero fields take the defaults.  sge_autotune_batch
+ * measures the choices and returns the fastest. */
+typedef struct {
+    int32_t pairs_per_item;    /* antithetic pairs one CTA runs per (view, tile) item (default 8, <= 64) */
+    int32_t blocks_per_sm;     /* persistent CTAs per SM of the fast kernel (default: as many as fit)    */
+    int32_t light_bin;         /* tiles whose bin holds at most this many triangles take the fast
+                                  kernel, the rest the general one (default and maximum 256)             */
+} sge_batch_tuning;
+
+/* sge_estimate_grad for several scenes (assets of different sizes, textures and
+ * view counts) in one call: every estimate of every entry, pairs_per_view pairs per
+ * view, from (seed, iter, view, pair) exactly as sge_estimate_grad would draw them
+ * for that scene, each entry's sums, counts and losses into its own buffers.  The
+ * estimates of all entries with the same shading model run in one persistent
+ * launch of each estimator kernel (per block of max_pairs_per_call pairs, the
+ * smallest of the entries'); binning and vertex passes are per entry.  Results
+ * equal sge_estimate_grad's per entry up to the order of float additions.  The
+ * paper runs one asset at a time; batching is this library's addition.  The first
+ * batched call of a scene (and the first after sge_set_targets) also writes the
+ * scene's launch descriptor into its workspace on `stream`. */
+int sge_estimate_grad_batch(const sge_batch_entry *entries, int32_t n_entries, uint64_t seed, uint32_t iter,
+                            int32_t pairs_per_view, const sge_batch_tuning *tuning, sge_stream_t stream);
+
+/* Autotuner of sge_estimate_grad_batch's launch shape for these entries: times
+ * candidate shapes (pairs per item 1..64, 1 or 2 CTAs per SM, light-bin limit
+ * 64/128/256; a coordinate search from the defaults), each as one untimed call then
+ * the mean of `repeats` calls (CUDA events on `stream`), and returns the fastest in
+ * *out and its time in *best_ms (may be NULL).  Runs real estimates into the
+ * entries' buffers and zeroes grad_sums, counts and loss_out before returning.
+ * Synchronises `stream`; not for use under stream capture. */
+int sge_autotune_batch(const sge_batch_entry *entries, int32_t n_entries, int32_t pairs_per_view, int32_t repeats,
+                       sge_batch_tuning *out, float *best_ms, sge_stream_t stream);
+
 /* Synchronise `stream`, return the device status word (SGE_OK or the first
  * device-side error) in *device_status and clear it. */
 int sge_status(sge_scene *scene, sge_stream_t stream, int32_t *device_status);
@@ -221,6 +266,18 @@ int sge_status(sge_scene *scene, sge_stream_t stream, int32_t *device_status);
 int sge_render_idb_static(const sge_scene_desc *desc, int32_t view, uint64_t seed, uint32_t iter,
                           uint32_t pair, int32_t side, uint64_t *depth_id, float *uv, float *rgb,
                           int32_t *device_status, sge_stream_t stream);
+
+/* Timing of the dominant kernel, for benchmarks (the paper has no counterpart).
+ * While enabled, each sge_estimate_grad call records a pair of CUDA events on its
+ * stream right before and right after each launch of its fast estimator kernel (the
+ * one that runs tiles with light bins), up to 256 launches between reads.
+ * sge_kernel_time synchronises on those events and returns the total milliseconds
+ * between the pairs and the number of launches timed, then starts a new count.
+ * Enabling creates the events (host objects, no device memory); disabling (and
+ * sge_destroy_scene) releases them.  Calls made under stream capture must not be
+ * timed. */
+int sge_kernel_timing(sge_scene *scene, int32_t enable);
+int sge_kernel_time(sge_scene *scene, float *total_ms, int32_t *launches);
 
 /* Release the host object (never the borrowed device memory). */
 void sge_destroy_scene(sge_scene *scene);

@@ -19,7 +19,7 @@ from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_TEXTURES, MAX_VIEWS_PER_
                    STEP_SGD, STEP_SGD_MEAN, SGEError)
 from ._build import build
 
-__all__ = ["Scene", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
+__all__ = ["Scene", "Batch", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
            "STEP_SGD_MEAN", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
 
 
@@ -222,6 +222,16 @@ class Scene:
         _abi.check(_abi.load().sge_estimate_grad_plain(self._h, int(seed), int(it), arr, n, int(pairs_per_view),
                                                        _ptr(grad), _ptr(counts), _ptr(loss), _stream_ptr(stream)))
 
+    def kernel_timing(self, enable: bool) -> None:
+        """Record CUDA events around each fast-estimator launch of estimate_grad (benchmarks)."""
+        _abi.check(_abi.load().sge_kernel_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self):
+        """(total ms, launches) of the fast estimator since the last read (synchronises)."""
+        ms, n = C.c_float(0.0), C.c_int32(0)
+        _abi.check(_abi.load().sge_kernel_time(self._h, C.byref(ms), C.byref(n)))
+        return float(ms.value), int(n.value)
+
     def loss(self, view_ids: Sequence[int], out=None, stream=None):
         """Image error f(theta) of the unperturbed scene per listed view (Table 1), [n] float32."""
         torch = _torch()
@@ -250,6 +260,48 @@ class Scene:
         o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), int(t)
         _abi.check(_abi.load().sge_step(self._h, C.byref(o), _ptr(grad), _ptr(counts), int(n_pairs_total),
                                         _ptr(m), _ptr(v), _stream_ptr(stream)))
+
+
+class Batch:
+    """Several scenes (assets) estimated together: sge_estimate_grad_batch runs every
+    estimate of every asset in one persistent launch per estimator kernel, each
+    asset's sums into its own buffers.
+
+        b = Batch([(scene, views, grad, counts), ...])       # or (scene, views, grad, counts, loss)
+        b.autotune(pairs)                                     # optional: pick the launch shape
+        b.estimate_grad(seed, it, pairs)
+    """
+
+    def __init__(self, entries):
+        if not 1 <= len(entries) <= _abi.MAX_BATCH:
+            raise ValueError(f"a batch holds 1..{_abi.MAX_BATCH} entries")
+        self.scenes = []
+        self._keep = []
+        self._arr = (_abi.BatchEntry * len(entries))()
+        for i, e in enumerate(entries):
+            scene, views, grad, counts = e[:4]
+            loss = e[4] if len(e) > 4 else None
+            varr, n = Scene._views(views)
+            self._keep.append((varr, grad, counts, loss))
+            self.scenes.append(scene)
+            E = self._arr[i]
+            E.scene, E.view_ids, E.n_views = scene._h.value, C.addressof(varr), n
+            E.grad_sums, E.counts, E.loss_out = _ptr(grad), _ptr(counts), _ptr(loss)
+        self.tuning = _abi.BatchTuning()
+
+    def estimate_grad(self, seed: int, it: int, pairs_per_view: int, stream=None) -> None:
+        _abi.check(_abi.load().sge_estimate_grad_batch(self._arr, len(self.scenes), int(seed), int(it),
+                                                       int(pairs_per_view), C.byref(self.tuning),
+                                                       _stream_ptr(stream)))
+
+    def autotune(self, pairs_per_view: int, repeats: int = 2, stream=None) -> float:
+        """Pick the launch shape for these entries (zeroes their buffers); returns its ms."""
+        t = _abi.BatchTuning()
+        ms = C.c_float(0.0)
+        _abi.check(_abi.load().sge_autotune_batch(self._arr, len(self.scenes), int(pairs_per_view), int(repeats),
+                                                  C.byref(t), C.byref(ms), _stream_ptr(stream)))
+        self.tuning = t
+        return float(ms.value)
 
 
 def _make_function():

@@ -12,13 +12,16 @@ from . import _build
 
 MAX_TEXTURES = 8
 MAX_VIEWS_PER_CALL = 64
+MAX_BATCH = 64
+MAX_BATCH_VIEWS = 8
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_BIN_OVERFLOW, ERR_BAD_INDEX, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
 STEP_SGD, STEP_ADAM, STEP_SGD_MEAN = 0, 1, 2
 
 EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_targets", "sge_validate",
            "sge_render_idb", "sge_estimate_grad", "sge_estimate_grad_plain", "sge_step", "sge_status",
-           "sge_destroy_scene", "sge_last_error", "sge_render_idb_static", "sge_loss", "sge_gradient")
+           "sge_destroy_scene", "sge_last_error", "sge_render_idb_static", "sge_loss", "sge_gradient",
+           "sge_estimate_grad_batch", "sge_autotune_batch", "sge_kernel_timing", "sge_kernel_time")
 
 
 class Texture(C.Structure):
@@ -41,6 +44,15 @@ class Config(C.Structure):
     _fields_ = [("max_views_per_call", C.c_int32), ("bin_capacity", C.c_int64),
                 ("pairs_per_item", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("max_pairs_per_call", C.c_int32)]
+
+
+class BatchEntry(C.Structure):
+    _fields_ = [("scene", C.c_void_p), ("view_ids", C.c_void_p), ("n_views", C.c_int32),
+                ("grad_sums", C.c_void_p), ("counts", C.c_void_p), ("loss_out", C.c_void_p)]
+
+
+class BatchTuning(C.Structure):
+    _fields_ = [("pairs_per_item", C.c_int32), ("blocks_per_sm", C.c_int32), ("light_bin", C.c_int32)]
 
 
 class Opt(C.Structure):
@@ -88,6 +100,10 @@ def load(build_if_missing: bool = False):
         L.sge_render_idb_static.argtypes = [P, I32, U64, U32, U32, I32, P, P, P, P, P]
         L.sge_loss.argtypes = [P, P, I32, P, P]
         L.sge_gradient.argtypes = [P, P, I64, P, P, P]
+        L.sge_estimate_grad_batch.argtypes = [P, I32, U64, U32, I32, P, P]
+        L.sge_autotune_batch.argtypes = [P, I32, I32, I32, P, C.POINTER(C.c_float), P]
+        L.sge_kernel_timing.argtypes = [P, I32]
+        L.sge_kernel_time.argtypes = [P, C.POINTER(C.c_float), C.POINTER(I32)]
         L.sge_destroy_scene.argtypes = [P]
         L.sge_destroy_scene.restype = None
         L.sge_last_error.argtypes = []

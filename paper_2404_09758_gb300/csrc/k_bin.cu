@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt) 
   for (int i = beg; i < end; ++i) {
     uint32_t c = ws.tile_count[i];
     sum += c;
-    ne += c > 0 && c <= (uint32_t)kLightBin;
-    nh += c > (uint32_t)kLightBin;
+    ne += c > 0 && c <= (uint32_t)ws.light_bin;
+    nh += c > (uint32_t)ws.light_bin;
   }
   // block exclusive scan of (sum, ne, nh)
   uint32_t xs = sum, xn = ne, xh = nh;
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt) 
       int slot = i / nt, tile = i - slot * nt;
       const uint32_t it = ((uint32_t)slot << 24) | (uint32_t)tile;
       // light items from the front of the list, heavy ones from the back
-      if (c <= (uint32_t)kLightBin) ws.items[noff++] = it;
+      if (c <= (uint32_t)ws.light_bin) ws.items[noff++] = it;
       else ws.items[n - 1 - hoff++] = it;
     }
     off += c;

@@ -180,24 +180,29 @@ __device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem& tb
   }
 }
 
-__global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+// the batched kernels keep their asset after the kernel's own shared memory, 16-byte aligned
+constexpr size_t kHeavyBatchOff = (sizeof(Smem) + 15) & ~(size_t)15;
+
+__device__ __forceinline__ void clear_table(TableSmem& tb) {
+  for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
+    tb.key[s] = EMPTY;
+    tb.A[s] = 0.0f;
+    tb.n[s] = 0u;
+    tb.cnt[s] = 0u;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tb.S[c][s] = 0.0f;
+  }
+}
+
+// Every heavy work item of one scene's call (the table starts and ends each item empty).
+__device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& ws, const ViewList& vl,
+                                            const EstimateArgs& a, Smem& sm) {
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
   const int n_chunks = (a.pair_count + a.pairs_per_item - 1) / a.pairs_per_item;
   const long long n_work = (long long)ws.counters[4] * n_chunks;
   const int n_all = vl.n * ntl;
-
-  for (int s = tid; s < TABLE; s += blockDim.x) {
-    sm.tab.key[s] = EMPTY;
-    sm.tab.A[s] = 0.0f;
-    sm.tab.n[s] = 0u;
-    sm.tab.cnt[s] = 0u;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) sm.tab.S[c][s] = 0.0f;
-  }
 
   for (;;) {
     __syncthreads();
@@ -309,6 +314,33 @@ __global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspac
   }
 }
 
+__global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  clear_table(sm.tab);
+  heavy_items(S, ws, vl, a, sm);
+}
+
+// Batched form: the assets of P in order, each until its heavy items run out.
+__global__ void __launch_bounds__(TILE_PX) k_estimate_heavy_batch(const BatchArgs P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  BatchSmem& b = *reinterpret_cast<BatchSmem*>(smem_raw + kHeavyBatchOff);
+  clear_table(sm.tab);
+  for (int ai = 0; ai < P.n; ++ai) {
+    __syncthreads();
+    load_asset(P, ai, b);
+    __syncthreads();
+    heavy_items(b.d.S, b.d.ws, b.vl, b.a, sm);
+  }
+}
+
+__global__ void k_put_desc(const AssetDesc d, AssetDesc* dst) {
+  const int4* src = reinterpret_cast<const int4*>(&d);
+  int4* out = reinterpret_cast<int4*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(AssetDesc) / 16); i += blockDim.x) out[i] = src[i];
+}
+
 // Loss of pixels in tiles no triangle can reach: the background on both sides.
 __global__ void k_background_loss(SceneDev S, Workspace ws, ViewList vl, float* loss) {
   const int slot = blockIdx.y, tile = blockIdx.x;
@@ -344,14 +376,47 @@ int estimate_blocks_per_sm() {
   return cached;
 }
 
+int heavy_batch_blocks_per_sm() {
+  static int cached = -1;
+  if (cached < 0) {
+    int n = 0;
+    const int bytes = (int)(kHeavyBatchOff + sizeof(BatchSmem));
+    cudaFuncSetAttribute(k_estimate_heavy_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy_batch, TILE_PX, bytes);
+    cached = n > 0 ? n : 1;
+  }
+  return cached;
+}
+
+cudaError_t launch_put_desc(const AssetDesc& d, AssetDesc* dst, cudaStream_t st) {
+  k_put_desc<<<1, 64, 0, st>>>(d, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heavy_batch(const BatchArgs& P, int grid, cudaStream_t st) {
+  const int bytes = (int)(kHeavyBatchOff + sizeof(BatchSmem));
+  cudaError_t e = cudaFuncSetAttribute(k_estimate_heavy_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  k_estimate_heavy_batch<<<grid, TILE_PX, bytes, st>>>(P);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
-                            int grid_fast, int grid_heavy, cudaStream_t st) {
-  cudaError_t e = launch_fast(S, ws, vl, a, grid_fast, st);
+                            int grid_fast, int grid_heavy, cudaStream_t st, const cudaEvent_t* ev_fast) {
+  cudaError_t e = ev_fast ? cudaEventRecord(ev_fast[0], st) : cudaSuccess;
+  if (e == cudaSuccess) e = launch_fast(S, ws, vl, a, grid_fast, st);
+  if (e == cudaSuccess && ev_fast) e = cudaEventRecord(ev_fast[1], st);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_estimate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return e;
   k_estimate_heavy<<<grid_heavy, TILE_PX, sizeof(Smem), st>>>(S, ws, vl, a);
   if (a.loss && a.pair_begin == 0) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_background_loss(const SceneDev& S, const Workspace& ws, const ViewList& vl, float* loss,
+                                   cudaStream_t st) {
+  k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, loss);
   return cudaGetLastError();
 }
 

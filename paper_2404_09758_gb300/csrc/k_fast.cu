@@ -221,13 +221,13 @@ __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE>& sm, int
   }
 }
 
+// Every light work item of one scene's call, taken one at a time from the scene's work
+// counter until none is left.
 template <int SH>
-__global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
-    k_estimate_fast(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
+__device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& ws, const ViewList& vl,
+                                           const EstimateArgs& a, FastSmem<Model<SH>::TABLE>& sm) {
   constexpr int NREAD = Model<SH>::NREAD;
   constexpr int TABLE = Model<SH>::TABLE;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FastSmem<TABLE>& sm = *reinterpret_cast<FastSmem<TABLE>*>(smem_raw);
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
@@ -610,8 +610,58 @@ __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
 }
 
 template <int SH>
+__global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
+    k_estimate_fast(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fast_items<SH>(S, ws, vl, a, *reinterpret_cast<FastSmem<Model<SH>::TABLE>*>(smem_raw));
+}
+
+// The batched kernel keeps its asset after FastSmem, 16-byte aligned.
+template <int SH>
+__host__ __device__ constexpr size_t fast_batch_off() {
+  return (sizeof(FastSmem<Model<SH>::TABLE>) + 15) & ~(size_t)15;
+}
+
+// Batched form: the assets of P in order, each until its light items run out.
+template <int SH>
+__global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1) k_estimate_fast_batch(const BatchArgs P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& sm = *reinterpret_cast<FastSmem<Model<SH>::TABLE>*>(smem_raw);
+  BatchSmem& b = *reinterpret_cast<BatchSmem*>(smem_raw + fast_batch_off<SH>());
+  for (int ai = 0; ai < P.n; ++ai) {
+    __syncthreads();
+    load_asset(P, ai, b);
+    __syncthreads();
+    fast_items<SH>(b.d.S, b.d.ws, b.vl, b.a, sm);
+  }
+}
+
+template <int SH>
 size_t fast_smem() {
   return sizeof(FastSmem<Model<SH>::TABLE>);
+}
+
+template <int SH>
+size_t fast_batch_smem() {
+  return fast_batch_off<SH>() + sizeof(BatchSmem);
+}
+
+template <int SH>
+cudaError_t launch_fast_batch_t(const BatchArgs& P, int grid, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_estimate_fast_batch<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_batch_smem<SH>());
+  if (e != cudaSuccess) return e;
+  k_estimate_fast_batch<SH><<<grid, TILE_PX, fast_batch_smem<SH>(), st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int SH>
+int fast_batch_blocks_per_sm_t() {
+  int n = 0;
+  cudaFuncSetAttribute(k_estimate_fast_batch<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fast_batch_smem<SH>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_fast_batch<SH>, TILE_PX, fast_batch_smem<SH>());
+  return n > 0 ? n : 1;
 }
 
 template <int SH>
@@ -639,6 +689,18 @@ cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& 
   if (S.shading == SHADE_UNLIT) return launch_fast_t<SHADE_UNLIT>(S, ws, vl, a, grid, st);
   if (S.shading == SHADE_LAMBERT) return launch_fast_t<SHADE_LAMBERT>(S, ws, vl, a, grid, st);
   return launch_fast_t<SHADE_GGX>(S, ws, vl, a, grid, st);
+}
+
+cudaError_t launch_fast_batch(const BatchArgs& P, int shading, int grid, cudaStream_t st) {
+  if (shading == SHADE_UNLIT) return launch_fast_batch_t<SHADE_UNLIT>(P, grid, st);
+  if (shading == SHADE_LAMBERT) return launch_fast_batch_t<SHADE_LAMBERT>(P, grid, st);
+  return launch_fast_batch_t<SHADE_GGX>(P, grid, st);
+}
+
+int fast_batch_blocks_per_sm(int shading) {
+  if (shading == SHADE_UNLIT) return fast_batch_blocks_per_sm_t<SHADE_UNLIT>();
+  if (shading == SHADE_LAMBERT) return fast_batch_blocks_per_sm_t<SHADE_LAMBERT>();
+  return fast_batch_blocks_per_sm_t<SHADE_GGX>();
 }
 
 int fast_blocks_per_sm(int shading) {

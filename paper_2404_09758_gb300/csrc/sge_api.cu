@@ -17,6 +17,13 @@ struct sge_scene {
   SceneDev dev;
   Workspace ws;
   int grid_fast, grid_heavy;  // persistent CTAs of the two estimator kernels
+  AssetDesc* desc_dev;        // the scene's AssetDesc in its workspace (batched calls)
+  bool desc_dirty;            // desc_dev must be rewritten before the next batched call
+  // kernel timing (sge_kernel_timing): event pairs around the fast kernel's launches
+  static constexpr int kMaxTimed = 256;
+  cudaEvent_t tev[2 * kMaxTimed];
+  int n_tev;                  // event pairs created (0 = timing off)
+  int n_timed;                // pairs recorded since the last sge_kernel_time
 };
 
 namespace {
@@ -38,7 +45,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-  size_t tri_rect, tri_margin, tri_z, pverts, vbits, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf, total;
+  size_t tri_rect, tri_margin, tri_z, pverts, vbits, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf,
+      desc, total;
   int max_views, max_pairs;
   long long bin_capacity;
 };
@@ -77,7 +85,7 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   if (L.max_views > SGE_MAX_VIEWS_PER_CALL) L.max_views = SGE_MAX_VIEWS_PER_CALL;
   const long long ntl = (long long)tiles_of(d->width) * tiles_of(d->height);
   L.bin_capacity = (c && c->bin_capacity > 0) ? c->bin_capacity
-                                               : (6ll * d->n_triangles + ntl) * (long long)L.max_views;
+                                               : (6ll * d->n_triangles + 8ll * ntl) * (long long)L.max_views;
   if (L.bin_capacity >= (1ll << 32)) return fail(SGE_ERR_INVALID_ARG, "bin_capacity must be < 2^32");
   const long long npx = (long long)d->width * d->height;
   size_t o = 0;
@@ -97,6 +105,7 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   L.keys = take(sizeof(unsigned long long) * 2 * (size_t)npx);
   L.uvbuf = take(sizeof(float2) * 2 * (size_t)npx);
   L.dfbuf = take(sizeof(float) * (size_t)npx);
+  L.desc = take(sizeof(AssetDesc));
   L.total = o;
   return SGE_OK;
 }
@@ -154,6 +163,14 @@ void make_dev(const sge_scene_desc* d, SceneDev& S) {
   S.ambient = d->ambient;
   S.tiles_x = tiles_of(d->width);
   S.tiles_y = tiles_of(d->height);
+}
+
+// The binning arms the estimator kernels' work counters; every further block of pairs of the
+// same call re-arms them.
+cudaError_t rearm_work(const Workspace& ws, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(ws.counters + 1, 0, sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.counters + 5, 0, sizeof(uint32_t), st);
+  return e;
 }
 
 int views_of(const sge_scene* s, const int32_t* view_ids, int32_t n, ViewList& vl) {
@@ -225,6 +242,11 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   w.dfbuf = reinterpret_cast<float*>(base + L.dfbuf);
   w.bin_capacity = L.bin_capacity;
   w.max_views = L.max_views;
+  w.light_bin = kLightBin;
+  s->desc_dev = reinterpret_cast<AssetDesc*>(base + L.desc);
+  s->desc_dirty = true;
+  s->n_tev = 0;
+  s->n_timed = 0;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -252,6 +274,7 @@ int sge_set_targets(sge_scene* s, const float* targets) {
   if (!s || !targets) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
   s->desc.targets = targets;
   s->dev.targets = targets;
+  s->desc_dirty = true;
   return SGE_OK;
 }
 
@@ -297,8 +320,11 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
     EstimateArgs b = a;
     b.pair_begin = p0;
     b.pair_count = pairs_per_view - p0 < s->ws.max_pairs ? pairs_per_view - p0 : s->ws.max_pairs;
-    e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
-    if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, b, s->grid_fast, s->grid_heavy, st);
+    if (p0 > 0) e = rearm_work(s->ws, st);
+    if (e == cudaSuccess) e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
+    const cudaEvent_t* ev = nullptr;
+    if (s->n_tev && s->n_timed < sge_scene::kMaxTimed) ev = s->tev + 2 * s->n_timed++;
+    if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, b, s->grid_fast, s->grid_heavy, st, ev);
   }
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
 }
@@ -363,6 +389,172 @@ int sge_gradient(sge_scene* s, const float* grad_sums, int64_t n_pairs_total, co
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_gradient");
 }
 
+int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t seed, uint32_t iter,
+                            int32_t pairs_per_view, const sge_batch_tuning* tuning, sge_stream_t stream) {
+  if (!entries) return fail(SGE_ERR_INVALID_ARG, "entries is NULL");
+  if (n < 1 || n > SGE_MAX_BATCH) return fail(SGE_ERR_INVALID_ARG, "n_entries %d out of [1, %d]", n, SGE_MAX_BATCH);
+  if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
+  sge_batch_tuning tu{};
+  if (tuning) tu = *tuning;
+  if (tu.pairs_per_item <= 0) tu.pairs_per_item = 8;
+  if (tu.pairs_per_item > kMaxPairsPerItem) tu.pairs_per_item = kMaxPairsPerItem;
+  if (tu.light_bin <= 0 || tu.light_bin > kLightBin) tu.light_bin = kLightBin;
+  ViewList vls[SGE_MAX_BATCH];
+  int max_pairs = 1 << 30;
+  for (int i = 0; i < n; ++i) {
+    const sge_batch_entry& E = entries[i];
+    if (!E.scene) return fail(SGE_ERR_INVALID_ARG, "entries[%d].scene is NULL", i);
+    if (!E.grad_sums || !E.counts) return fail(SGE_ERR_INVALID_ARG, "entries[%d]: grad_sums and counts must be non-NULL", i);
+    if (E.n_views > SGE_MAX_BATCH_VIEWS)
+      return fail(SGE_ERR_INVALID_ARG, "entries[%d].n_views %d above %d", i, E.n_views, SGE_MAX_BATCH_VIEWS);
+    int rc = views_of(E.scene, E.view_ids, E.n_views, vls[i]);
+    if (rc) return rc;
+    for (int j = 0; j < i; ++j)
+      if (entries[j].scene == E.scene) return fail(SGE_ERR_INVALID_ARG, "scene of entries[%d] listed twice", i);
+    if (E.scene->ws.max_pairs < max_pairs) max_pairs = E.scene->ws.max_pairs;
+  }
+  // assets in decreasing triangle count: the long items first, the short ones balance the tail
+  int order[SGE_MAX_BATCH];
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 1; i < n; ++i)
+    for (int j = i; j > 0 && entries[order[j]].scene->dev.nt > entries[order[j - 1]].scene->dev.nt; --j) {
+      int t = order[j];
+      order[j] = order[j - 1];
+      order[j - 1] = t;
+    }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  int sms = 0, dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    sge_scene* s = entries[i].scene;
+    if (s->desc_dirty) {
+      AssetDesc d;
+      memset(&d, 0, sizeof(d));
+      d.S = s->dev;
+      d.ws = s->ws;
+      e = launch_put_desc(d, s->desc_dev, st);
+      if (e == cudaSuccess) s->desc_dirty = false;
+    }
+    Workspace w = s->ws;
+    w.light_bin = tu.light_bin;
+    if (e == cudaSuccess) e = launch_binning(s->dev, w, vls[i], st);
+    if (e == cudaSuccess && entries[i].loss_out) e = launch_background_loss(s->dev, w, vls[i], entries[i].loss_out, st);
+  }
+  // one persistent launch per kernel and shading model over every asset, per block of pairs
+  for (int p0 = 0; p0 < pairs_per_view && e == cudaSuccess; p0 += max_pairs) {
+    const int pc = pairs_per_view - p0 < max_pairs ? pairs_per_view - p0 : max_pairs;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+      sge_scene* s = entries[i].scene;
+      EstimateArgs b{seed, iter, pairs_per_view, tu.pairs_per_item, p0, pc, entries[i].grad_sums, entries[i].counts,
+                     entries[i].loss_out, nullptr};
+      if (p0 > 0) e = rearm_work(s->ws, st);
+      if (e == cudaSuccess) e = launch_vertex_pass(s->dev, s->ws, vls[i], b, st);
+    }
+    for (int sh = SGE_SHADE_UNLIT; sh <= SGE_SHADE_GGX && e == cudaSuccess; ++sh) {
+      BatchArgs P;
+      memset(&P, 0, sizeof(P));
+      P.seed = seed;
+      P.iter = iter;
+      P.pairs = pairs_per_view;
+      P.pairs_per_item = tu.pairs_per_item;
+      P.pair_begin = p0;
+      P.pair_count = pc;
+      for (int k = 0; k < n; ++k) {
+        const int i = order[k];
+        sge_scene* s = entries[i].scene;
+        if (s->dev.shading != sh) continue;
+        BatchAsset& A = P.as[P.n++];
+        A.desc = s->desc_dev;
+        A.grad = entries[i].grad_sums;
+        A.counts = entries[i].counts;
+        A.loss = entries[i].loss_out;
+        A.n_views = vls[i].n;
+        for (int v = 0; v < vls[i].n; ++v) A.view[v] = vls[i].id[v];
+      }
+      if (P.n == 0) continue;
+      const int bps = tu.blocks_per_sm > 0 ? tu.blocks_per_sm : fast_batch_blocks_per_sm(sh);
+      e = launch_fast_batch(P, sh, sms * bps, st);
+      if (e == cudaSuccess) e = launch_heavy_batch(P, sms * heavy_batch_blocks_per_sm(), st);
+    }
+  }
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad_batch");
+}
+
+int sge_autotune_batch(const sge_batch_entry* entries, int32_t n, int32_t pairs_per_view, int32_t repeats,
+                       sge_batch_tuning* out, float* best_ms, sge_stream_t stream) {
+  if (!out) return fail(SGE_ERR_INVALID_ARG, "out is NULL");
+  if (repeats < 1) repeats = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  if (e != cudaSuccess) return cuda_fail(e, "sge_autotune_batch");
+  int rc = SGE_OK;
+  // time one launch shape: one untimed call, then the mean of `repeats` calls
+  auto time_of = [&](const sge_batch_tuning& t, float& ms) -> int {
+    int r = sge_estimate_grad_batch(entries, n, 0x5eed, 0, pairs_per_view, &t, stream);
+    if (r) return r;
+    cudaError_t c = cudaEventRecord(ev[0], st);
+    for (int k = 0; k < repeats && c == cudaSuccess; ++k) {
+      r = sge_estimate_grad_batch(entries, n, 0x5eed, 1 + k, pairs_per_view, &t, stream);
+      if (r) return r;
+    }
+    if (c == cudaSuccess) c = cudaEventRecord(ev[1], st);
+    if (c == cudaSuccess) c = cudaEventSynchronize(ev[1]);
+    if (c == cudaSuccess) c = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    if (c != cudaSuccess) return cuda_fail(c, "sge_autotune_batch");
+    ms /= (float)repeats;
+    return SGE_OK;
+  };
+  sge_batch_tuning best{8, 0, kLightBin};
+  if (best.pairs_per_item > pairs_per_view) best.pairs_per_item = pairs_per_view;
+  float best_t = 0.0f;
+  rc = time_of(best, best_t);
+  // coordinate search: pairs per item, then CTAs per SM, then the light-bin limit
+  const int ppi[] = {1, 2, 4, 8, 16, 32, 64};
+  for (int k = 0; k < 7 && !rc; ++k) {
+    if (ppi[k] > pairs_per_view || ppi[k] == best.pairs_per_item) continue;
+    sge_batch_tuning t = best;
+    t.pairs_per_item = ppi[k];
+    float ms = 0.0f;
+    rc = time_of(t, ms);
+    if (!rc && ms < best_t) best = t, best_t = ms;
+  }
+  for (int bps = 1; bps <= 2 && !rc; ++bps) {
+    sge_batch_tuning t = best;
+    t.blocks_per_sm = bps;
+    float ms = 0.0f;
+    rc = time_of(t, ms);
+    if (!rc && ms < best_t) best = t, best_t = ms;
+  }
+  const int lb[] = {64, 128};
+  for (int k = 0; k < 2 && !rc; ++k) {
+    sge_batch_tuning t = best;
+    t.light_bin = lb[k];
+    float ms = 0.0f;
+    rc = time_of(t, ms);
+    if (!rc && ms < best_t) best = t, best_t = ms;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (rc) return rc;
+  // the trials accumulated into the entries' buffers: leave them zeroed
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    const sge_scene* s = entries[i].scene;
+    e = cudaMemsetAsync(entries[i].grad_sums, 0, sizeof(float) * (size_t)s->dev.n_params, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(entries[i].counts, 0, sizeof(uint32_t) * (size_t)s->dev.n_params, st);
+    if (e == cudaSuccess && entries[i].loss_out)
+      e = cudaMemsetAsync(entries[i].loss_out, 0, sizeof(float) * (size_t)entries[i].n_views, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sge_autotune_batch");
+  *out = best;
+  if (best_ms) *best_ms = best_t;
+  return SGE_OK;
+}
+
 int sge_status(sge_scene* s, sge_stream_t stream, int32_t* device_status) {
   if (!s || !device_status) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
   uint32_t v = 0;
@@ -376,6 +568,44 @@ int sge_status(sge_scene* s, sge_stream_t stream, int32_t* device_status) {
   return SGE_OK;
 }
 
-void sge_destroy_scene(sge_scene* s) { delete s; }
+int sge_kernel_timing(sge_scene* s, int32_t enable) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  if (enable && !s->n_tev) {
+    for (int i = 0; i < 2 * sge_scene::kMaxTimed; ++i) {
+      cudaError_t e = cudaEventCreate(&s->tev[i]);
+      if (e != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(s->tev[j]);
+        return cuda_fail(e, "sge_kernel_timing");
+      }
+    }
+    s->n_tev = 2 * sge_scene::kMaxTimed;
+  } else if (!enable && s->n_tev) {
+    for (int i = 0; i < s->n_tev; ++i) cudaEventDestroy(s->tev[i]);
+    s->n_tev = 0;
+  }
+  s->n_timed = 0;
+  return SGE_OK;
+}
+
+int sge_kernel_time(sge_scene* s, float* total_ms, int32_t* launches) {
+  if (!s || !total_ms || !launches) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  float sum = 0.0f;
+  for (int k = 0; k < s->n_timed; ++k) {
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(s->tev[2 * k + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->tev[2 * k], s->tev[2 * k + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "sge_kernel_time");
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = s->n_timed;
+  s->n_timed = 0;
+  return SGE_OK;
+}
+
+void sge_destroy_scene(sge_scene* s) {
+  if (s) sge_kernel_timing(s, 0);
+  delete s;
+}
 
 }  // extern "C"

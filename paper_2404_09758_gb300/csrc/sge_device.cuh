@@ -452,4 +452,25 @@ __device__ __forceinline__ float loss_diff(float3 ip, float3 im, float3 t, float
   return df;
 }
 
+// One asset of a batched launch as the per-scene code expects it, in shared memory.
+struct BatchSmem {
+  AssetDesc d;
+  ViewList vl;
+  EstimateArgs a;
+};
+
+// Load asset ai of P into b (all threads of the CTA; the caller synchronises around it).
+__device__ __forceinline__ void load_asset(const BatchArgs& P, int ai, BatchSmem& b) {
+  const BatchAsset& A = P.as[ai];
+  const int4* src = reinterpret_cast<const int4*>(A.desc);
+  int4* dst = reinterpret_cast<int4*>(&b.d);
+  for (int i = threadIdx.x; i < (int)(sizeof(AssetDesc) / 16); i += blockDim.x) dst[i] = src[i];
+  if (threadIdx.x == 0) {
+    b.vl.n = A.n_views;
+    b.a = EstimateArgs{P.seed, P.iter, P.pairs, P.pairs_per_item, P.pair_begin, P.pair_count,
+                       A.grad, A.counts, A.loss, nullptr};
+  }
+  if (threadIdx.x < SGE_MAX_BATCH_VIEWS) b.vl.id[threadIdx.x] = A.view[threadIdx.x];
+}
+
 }  // namespace sge

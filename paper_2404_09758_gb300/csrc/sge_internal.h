@@ -83,6 +83,38 @@ struct Workspace {
   long long bin_capacity;
   int max_views;
   int max_pairs;
+  int light_bin;  // bins of at most this many triangles are light items (fast kernel)
+};
+
+// What a batched launch needs of one scene, kept in the scene's workspace (written on the
+// stream by launch_put_desc) so that the launch's parameter holds one pointer per asset.
+struct __align__(16) AssetDesc {
+  SceneDev S;
+  Workspace ws;
+};
+static_assert(sizeof(AssetDesc) % 16 == 0, "AssetDesc is copied as 16-byte words");
+
+// One asset of a batched estimate call.
+struct BatchAsset {
+  const AssetDesc* desc;  // device
+  float* grad;
+  uint32_t* counts;
+  float* loss;
+  int n_views;
+  int view[SGE_MAX_BATCH_VIEWS];
+};
+
+// A batched call: every estimate of several scenes (one shading model) in one persistent launch.
+// Assets are taken in order; each asset's items come from its own work counters.
+struct BatchArgs {
+  uint64_t seed;
+  uint32_t iter;
+  int pairs;           // pairs per view of the whole call
+  int pairs_per_item;
+  int pair_begin;
+  int pair_count;
+  int n;
+  BatchAsset as[SGE_MAX_BATCH];
 };
 
 // ---- kernels launchers (all asynchronous on `st`)
@@ -103,8 +135,10 @@ struct EstimateArgs {
   float* delta_f;
 };
 // Both estimator kernels: the fast path over light bins, the general one over heavy bins.
+// ev_fast (two events, or NULL) are recorded on st right before and after the fast kernel.
 cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl,
-                            const EstimateArgs& a, int grid_fast, int grid_heavy, cudaStream_t st);
+                            const EstimateArgs& a, int grid_fast, int grid_heavy, cudaStream_t st,
+                            const cudaEvent_t* ev_fast = nullptr);
 cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                         int grid, cudaStream_t st);
 // Perturbed, projected vertices of both sides for every (view slot, pair) of a block of pairs.
@@ -112,6 +146,16 @@ cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const Vie
                                cudaStream_t st);
 int estimate_blocks_per_sm();
 int fast_blocks_per_sm(int shading);
+
+// Batched form of the two estimator kernels over BatchArgs' assets.
+// Image error of background-only tiles (both sides show the background), added to loss[slot].
+cudaError_t launch_background_loss(const SceneDev& S, const Workspace& ws, const ViewList& vl, float* loss,
+                                   cudaStream_t st);
+cudaError_t launch_put_desc(const AssetDesc& d, AssetDesc* dst, cudaStream_t st);
+cudaError_t launch_fast_batch(const BatchArgs& P, int shading, int grid, cudaStream_t st);
+cudaError_t launch_heavy_batch(const BatchArgs& P, int grid, cudaStream_t st);
+int fast_batch_blocks_per_sm(int shading);
+int heavy_batch_blocks_per_sm();
 
 // Staged path: render one side of one estimate into keys/uv/rgb.
 cudaError_t launch_render(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key,

@@ -165,6 +165,7 @@ extern "C" int sge_render_idb_static(const sge_scene_desc* d, int32_t view, uint
   ws.counters = reinterpret_cast<uint32_t*>(b + kOffCounters);
   ws.bin_capacity = kBinEntries;
   ws.max_views = 1;
+  ws.light_bin = kLightBin;
 
   cudaStream_t st = (cudaStream_t)stream;
   ViewList vl;

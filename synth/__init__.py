@@ -343,17 +343,18 @@ def config_uneven(n_assets: int = 32, n_views: int = 4, pairs: int = 8, render: 
                   tri_lo: int = 1000, tri_hi: int = 200_000,
                   tex_choices=(256, 512, 1024, 2048)) -> List[Scene]:
     """Assets with triangle counts log-uniform in [tri_lo, tri_hi] and square RGB textures."""
-    scenes = []
-    for k in range(n_assets):
-        rng = np.random.default_rng(100 + k)
-        t = math.exp(rng.uniform(math.log(tri_lo), math.log(tri_hi)))
-        n_lat = max(2, int(round(math.sqrt(t / 4.0))))
-        tex = int(rng.choice(tex_choices))
-        s = sphere_scene(f"asset{k}_lat{n_lat}_tex{tex}", 2 * n_lat, n_lat, tex, render,
-                         random_eyes(n_views, seed=1000 + k), seed_target=100 + k,
-                         pairs_per_view=pairs)
-        scenes.append(s)
-    return scenes
+    return [uneven_asset(k, n_views, pairs, render, tri_lo, tri_hi, tex_choices) for k in range(n_assets)]
+
+
+def uneven_asset(k: int, n_views: int = 4, pairs: int = 8, render: int = 512, tri_lo: int = 1000,
+                 tri_hi: int = 200_000, tex_choices=(256, 512, 1024, 2048)) -> Scene:
+    """Asset k of config_uneven (each asset has its own seeds, so it can be made alone)."""
+    rng = np.random.default_rng(100 + k)
+    t = math.exp(rng.uniform(math.log(tri_lo), math.log(tri_hi)))
+    n_lat = max(2, int(round(math.sqrt(t / 4.0))))
+    tex = int(rng.choice(tex_choices))
+    return sphere_scene(f"asset{k}_lat{n_lat}_tex{tex}", 2 * n_lat, n_lat, tex, render,
+                        random_eyes(n_views, seed=1000 + k), seed_target=100 + k, pairs_per_view=pairs)
 
 
 def config_scale(n_views: int = 16, pairs: int = 16, render: int = 2048, tex: int = 2048,

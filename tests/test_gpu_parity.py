@@ -101,6 +101,9 @@ ESTIMATE_CASES = {
     # 8K triangles at 96x96: light and heavy bins mixed, pixels with more candidates than kept
     "dense_mixed_bins": (lambda: _sphere(64, 64, 64, 96, 96, synth.random_eyes(2, 6), True), [1, 0], 3,
                          {"pairs_per_item": 2}),
+    # 5 pairs projected in blocks of 2 (max_pairs_per_call): three launches of each estimator kernel
+    "pair_blocks": (lambda: _sphere(64, 64, 128, 96, 96, synth.random_eyes(2, 7)), [0, 1], 5,
+                    {"max_pairs_per_call": 2, "pairs_per_item": 2}),
 }
 
 
