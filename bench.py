@@ -424,14 +424,98 @@ def run_uneven(args):
     print(json.dumps(line), flush=True)
 
 
+def run_scale(args):
+    """Scale configuration: 1,048,576-triangle displaced grid sphere, four 2048^2 RGB maps,
+    GGX with one light, 2048^2 render, 16 views x 16 antithetic pairs per iteration, the
+    iteration (estimate + Adam step) captured in a CUDA graph.  A second configuration."""
+    import torch
+
+    import synth
+    from paper_2404_09758_gb300 import STEP_ADAM, Scene
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = synth.config_scale()
+    nv, pairs = sc.n_views, sc.pairs_per_view
+    ts = Scene.from_arrays(synth.target_scene(sc))
+    targets = ts.render_targets()
+    torch.cuda.synchronize()
+    del ts
+    g = Scene.from_arrays(sc, targets=targets, max_pairs_per_call=pairs)
+    grad, counts = g.new_grad_buffers()
+    m = torch.zeros(g.n_params, device=dev)
+    v = torch.zeros(g.n_params, device=dev)
+    loss = torch.zeros(nv, device=dev)
+    views = list(range(nv))
+    lr_tex = [t[1] for t in g.textures]
+    st = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(st):
+        g.estimate_grad(1, 0, views, pairs, grad, counts, stream=st)
+    st.synchronize()
+    contributions = int(counts.to(torch.int64).sum().item())
+    assert g.status(st) == 0
+    grad.zero_()
+    counts.zero_()
+
+    def iteration(it, t):
+        loss.zero_()
+        g.estimate_grad(1, it, views, pairs, grad, counts, loss=loss, stream=st)
+        g.step(STEP_ADAM, grad, counts, nv * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+
+    for w in range(args.warmup):
+        iteration(w, w + 1)
+    st.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        iteration(1000, 1)
+    st.synchronize()
+    graph.replay()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(st):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(st)
+                graph.replay()
+                ev[k][1].record(st)
+        torch.cuda.synchronize()
+    t_total = sum(a.elapsed_time(c) for a, c in ev) / 1000.0
+    g.kernel_timing(True)
+    with torch.cuda.stream(st):
+        for k in range(2):
+            g.estimate_grad(1, 2000 + k, views, pairs, grad, counts, stream=st)
+    fast_ms, fast_n = g.kernel_time()
+    g.kernel_timing(False)
+    assert g.status(st) == 0
+    px_per_step = nv * pairs * sc.width * sc.height
+    line = {"metric": METRIC, "value": px_per_step * args.steps / t_total, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gridsphere1m_4x2048_ggx_r2048_16views_x_16pairs", "views": nv,
+                       "pairs_per_view": pairs, "render": f"{sc.width}x{sc.height}",
+                       "triangles": int(sc.pos_idx.shape[0]), "params": int(g.n_params),
+                       "l2": "inputs larger than L2; 256 MB flush between timed steps",
+                       "graph": "estimate + Adam step captured in one CUDA graph"},
+            "param_gradients_per_s": contributions * args.steps / t_total,
+            "contributions_per_step": contributions,
+            "fast_kernel_ms": fast_ms / max(fast_n, 1),
+            "gpu_launches": 9 * args.steps,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["batched", "uneven"], default="batched",
-                    help="batched: the headline configuration; uneven: 32 assets in one batched call")
+    ap.add_argument("--workload", choices=["batched", "uneven", "scale"], default="batched",
+                    help="batched: the headline configuration; uneven: 32 assets in one batched call; "
+                         "scale: 1M triangles, GGX, 2048^2")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -439,6 +523,8 @@ def main():
         run_reference(args)
     elif args.workload == "uneven":
         run_uneven(args)
+    elif args.workload == "scale":
+        run_scale(args)
     else:
         run_ours(args)
 

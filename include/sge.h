@@ -267,17 +267,24 @@ int sge_render_idb_static(const sge_scene_desc *desc, int32_t view, uint64_t see
                           uint32_t pair, int32_t side, uint64_t *depth_id, float *uv, float *rgb,
                           int32_t *device_status, sge_stream_t stream);
 
-/* Timing of the dominant kernel, for benchmarks (the paper has no counterpart).
- * While enabled, each sge_estimate_grad call records a pair of CUDA events on its
- * stream right before and right after each launch of its fast estimator kernel (the
- * one that runs tiles with light bins), up to 256 launches between reads.
- * sge_kernel_time synchronises on those events and returns the total milliseconds
- * between the pairs and the number of launches timed, then starts a new count.
- * Enabling creates the events (host objects, no device memory); disabling (and
- * sge_destroy_scene) releases them.  Calls made under stream capture must not be
- * timed. */
+/* Timing of the estimator kernels, for benchmarks (the paper has no counterpart).
+ * While enabled, each sge_estimate_grad call records CUDA events on its stream right
+ * before and right after each launch of its fast estimator kernel (the one that runs
+ * tiles with light bins) and after the following heavy-bin kernel, up to 256 launches
+ * between reads.  sge_kernel_time synchronises on those events and returns the total
+ * milliseconds of the fast launches, of the heavy ones (heavy_ms may be NULL) and the
+ * number of launches timed, then starts a new count.  Enabling creates the events
+ * (host objects, no device memory); disabling (and sge_destroy_scene) releases them.
+ * Calls made under stream capture must not be timed. */
 int sge_kernel_timing(sge_scene *scene, int32_t enable);
-int sge_kernel_time(sge_scene *scene, float *total_ms, int32_t *launches);
+int sge_kernel_time(sge_scene *scene, float *total_ms, float *heavy_ms, int32_t *launches);
+
+/* Work list of the scene's last estimate call (after its binning and pruning):
+ * tiles x views taken by the fast kernel (light_items), by the heavy-bin kernel
+ * (heavy_items) and the triangle-tile bin entries before pruning.  Synchronises
+ * `stream`.  For tuning sge_batch_tuning.light_bin and for diagnostics. */
+int sge_bin_stats(sge_scene *scene, sge_stream_t stream, int64_t *light_items, int64_t *heavy_items,
+                  int64_t *bin_entries);
 
 /* Release the host object (never the borrowed device memory). */
 void sge_destroy_scene(sge_scene *scene);

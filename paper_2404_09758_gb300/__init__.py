@@ -226,11 +226,20 @@ class Scene:
         """Record CUDA events around each fast-estimator launch of estimate_grad (benchmarks)."""
         _abi.check(_abi.load().sge_kernel_timing(self._h, 1 if enable else 0))
 
-    def kernel_time(self):
-        """(total ms, launches) of the fast estimator since the last read (synchronises)."""
-        ms, n = C.c_float(0.0), C.c_int32(0)
-        _abi.check(_abi.load().sge_kernel_time(self._h, C.byref(ms), C.byref(n)))
+    def kernel_time(self, with_heavy: bool = False):
+        """(total ms, launches) of the fast estimator since the last read (synchronises);
+        with_heavy: (fast ms, heavy-bin kernel ms, launches)."""
+        ms, hms, n = C.c_float(0.0), C.c_float(0.0), C.c_int32(0)
+        _abi.check(_abi.load().sge_kernel_time(self._h, C.byref(ms), C.byref(hms), C.byref(n)))
+        if with_heavy:
+            return float(ms.value), float(hms.value), int(n.value)
         return float(ms.value), int(n.value)
+
+    def bin_stats(self, stream=None):
+        """(light items, heavy items, bin entries) of the last estimate call (synchronises)."""
+        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        _abi.check(_abi.load().sge_bin_stats(self._h, _stream_ptr(stream), C.byref(a), C.byref(b), C.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
 
     def loss(self, view_ids: Sequence[int], out=None, stream=None):
         """Image error f(theta) of the unperturbed scene per listed view (Table 1), [n] float32."""

@@ -106,7 +106,7 @@ __global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
 
 // One CTA: exclusive scan of the per-(slot, tile) counts, list of non-empty tiles,
 // fill cursors, and the estimate kernel's work counter.
-__global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt) {
+__global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt, int list_items) {
   __shared__ uint32_t wsum[32], wne[32], wnh[32];
   int tid = threadIdx.x;
   const int per = (n + blockDim.x - 1) / blockDim.x;
@@ -154,18 +154,21 @@ __global__ void __launch_bounds__(1024) k_bin_scan(Workspace ws, int n, int nt) 
       int slot = i / nt, tile = i - slot * nt;
       const uint32_t it = ((uint32_t)slot << 24) | (uint32_t)tile;
       // light items from the front of the list, heavy ones from the back
-      if (c <= (uint32_t)ws.light_bin) ws.items[noff++] = it;
-      else ws.items[n - 1 - hoff++] = it;
+      if (list_items) {
+        if (c <= (uint32_t)ws.light_bin) ws.items[noff++] = it;
+        else ws.items[n - 1 - hoff++] = it;
+      }
     }
     off += c;
   }
   if (tid == blockDim.x - 1) {
     ws.tile_off[n] = off;
     bool overflow = (long long)off > ws.bin_capacity;
-    ws.counters[0] = overflow ? 0u : noff;
+    // (without the list, k_bin_prune lists the items after pruning the bins)
+    ws.counters[0] = overflow || !list_items ? 0u : noff;
     ws.counters[1] = 0u;
     ws.counters[2] = off;
-    ws.counters[4] = overflow ? 0u : hoff;
+    ws.counters[4] = overflow || !list_items ? 0u : hoff;
     ws.counters[5] = 0u;
     if (overflow) atomicCAS(ws.counters + 3, 0u, (uint32_t)SGE_ERR_BIN_OVERFLOW);
   }
@@ -186,15 +189,17 @@ __global__ void k_bin_fill(SceneDev S, Workspace ws) {
 
 }  // namespace
 
-cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st) {
+cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st, bool prune) {
   int nt = n_tiles(S);
   cudaError_t e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * (size_t)vl.n * nt, st);
   if (e != cudaSuccess) return e;
   dim3 grid((S.nt + 255) / 256, vl.n);
   k_bin_rect_count<<<grid, 256, 0, st>>>(S, ws, vl);
-  k_bin_scan<<<1, 1024, 0, st>>>(ws, vl.n * nt, nt);
+  k_bin_scan<<<1, 1024, 0, st>>>(ws, vl.n * nt, nt, prune ? 0 : 1);
   k_bin_fill<<<grid, 256, 0, st>>>(S, ws);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess && prune) e = launch_prune(S, ws, vl, st);
+  return e;
 }
 
 }  // namespace sge

@@ -180,6 +180,23 @@ __device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem& tb
   }
 }
 
+// Triangle tri of side sd (0: theta + s eps, 1: theta - s eps) set up from the vertex pass's
+// projected perturbed vertices of one (view slot, pair) (vb = its first vertex record).
+__device__ __forceinline__ void setup_from_pverts(const SceneDev& S, const Workspace& ws, long long vb, int tri,
+                                                  int sd, long long rx, long long ry, Tri& t) {
+  PVert v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int4 q = __ldg(ws.pverts + 2 * (vb + __ldg(S.pidx + 3 * tri + k)) + sd);
+    v[k].X = q.x;
+    v[k].Y = q.y;
+    v[k].z = __int_as_float(q.z);
+    v[k].iw = __int_as_float(q.w);
+    v[k].ok = q.x != kNotDrawn;
+  }
+  setup_tri(v[0], v[1], v[2], rx, ry, t);
+}
+
 // the batched kernels keep their asset after the kernel's own shared memory, 16-byte aligned
 constexpr size_t kHeavyBatchOff = (sizeof(Smem) + 15) & ~(size_t)15;
 
@@ -219,7 +236,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
     const bool valid = px < S.W && py < S.H;
     const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
     const uint32_t bin_beg = ws.tile_off[slot * ntl + tile];
-    const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - bin_beg);
+    const int nb = (int)ws.tile_live[slot * ntl + tile];  // pruned and compacted by k_bin_prune
     const int p0 = a.pair_begin + chunk * a.pairs_per_item;
     const int p1 = min(a.pair_begin + a.pair_count, p0 + a.pairs_per_item);
     if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
@@ -230,11 +247,21 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
     }
     float loss_acc = 0.0f;
 
+    // this pixel's candidate triangles (16-bit indices into the live list, ascending; more than
+    // kHeavyCand: test every live triangle)
+    const long long ti = (long long)slot * ntl + tile;
+    const int4 cw0 = ws.cand[ti * 2 * TILE_PX + tid], cw1 = ws.cand[ti * 2 * TILE_PX + TILE_PX + tid];
+    const uint32_t cand[kHeavyCand / 2] = {(uint32_t)cw0.x, (uint32_t)cw0.y, (uint32_t)cw0.z, (uint32_t)cw0.w,
+                                          (uint32_t)cw1.x, (uint32_t)cw1.y, (uint32_t)cw1.z, (uint32_t)cw1.w};
+    const int ncand = ws.ncand[ti * TILE_PX + tid];
+    const bool all_live = ncand > kHeavyCand;
+
     for (int pair = p0; pair < p1; ++pair) {
       const uint64_t pkey = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)pair);
+      const long long vb = ((long long)slot * ws.max_pairs + (pair - a.pair_begin)) * S.nv;
       unsigned long long best[2] = {~0ull, ~0ull};
       int bestj[2] = {-1, -1}, bestc[2] = {-1, -1};
-      int last_c = 0;
+      int last_c = 0, q = 0;
       for (int c0 = 0; c0 < nb; c0 += BIN_CHUNK) {
         const int cnt = min(BIN_CHUNK, nb - c0);
         __syncthreads();
@@ -243,12 +270,12 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
 #pragma unroll
           for (int sd = 0; sd < 2; ++sd) {
             Tri t;
-            setup_from_scene(S, sm.m, tri, pkey, sd == 0 ? 1 : -1, rx, ry, t);
+            setup_from_pverts(S, ws, vb, tri, sd, rx, ry, t);
             store_tri(sm.side[sd], tid, t, tri);
           }
         }
         __syncthreads();
-        for (int j = 0; j < cnt; ++j) {
+        auto test = [&](int j) {
 #pragma unroll
           for (int sd = 0; sd < 2; ++sd) {
             unsigned long long k = test_key(sm.side[sd], j, dx, dy);
@@ -256,6 +283,17 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
               best[sd] = k;
               bestj[sd] = j;
               bestc[sd] = c0;
+            }
+          }
+        };
+        if (valid) {
+          if (all_live) {
+            for (int j = 0; j < cnt; ++j) test(j);
+          } else {
+            for (; q < ncand; ++q) {
+              const int j = (int)((cand[q >> 1] >> (16 * (q & 1))) & 0xFFFFu) - c0;
+              if (j >= cnt) break;
+              test(j);
             }
           }
         }
@@ -274,7 +312,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
         const int side = sd == 0 ? 1 : -1;
         Tri t;
         if (bestc[sd] == last_c) load_tri(sm.side[sd], bestj[sd], t);
-        else setup_from_scene(S, sm.m, tri, pkey, side, rx, ry, t);
+        else setup_from_pverts(S, ws, vb, tri, sd, rx, ry, t);
         long long e[3];
         cover(t, dx, dy, e);
         surface(S, view, tri, t, e, pkey, side, sf[sd]);
@@ -410,6 +448,8 @@ cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewLi
   e = cudaFuncSetAttribute(k_estimate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
   if (e != cudaSuccess) return e;
   k_estimate_heavy<<<grid_heavy, TILE_PX, sizeof(Smem), st>>>(S, ws, vl, a);
+  if (ev_fast) e = cudaEventRecord(ev_fast[2], st);
+  if (e != cudaSuccess) return e;
   if (a.loss && a.pair_begin == 0) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);
   return cudaGetLastError();
 }

@@ -42,7 +42,10 @@ constexpr uint32_t NOSLOT = 0xFFFFu;
 template <int SH>
 struct Model {
   static constexpr int NREAD = SH == SHADE_UNLIT ? 1 : (SH == SHADE_LAMBERT ? 2 : 4);
-  static constexpr int TABLE = SH == SHADE_UNLIT ? 512 : 1024;
+  // at about one texel per pixel a tile's bilinear footprints hold ~300 texels per read texture;
+  // the lit models (2 or 4 textures) run one CTA per SM (register-bound), so their tables can
+  // take the shared memory the second CTA of the unlit model would use
+  static constexpr int TABLE = SH == SHADE_UNLIT ? 512 : 2048;
 };
 
 // One side of a staged triangle (the unperturbed set-up also keeps its margin).
@@ -63,7 +66,6 @@ struct FastSmem {
   float uv[NB][6];
   int vid[NB][3];
   int btri[NB];          // triangle id of each bin entry
-  float2 zr[NB];         // depth interval of each bin triangle under any perturbation
   uint32_t sgn9[2][NB];  // bit 3k+c: coordinate c of corner k has s = -1 (by pair parity)
   float A_tri[NB];
   uint32_t n_tri[NB];
@@ -221,6 +223,194 @@ __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE>& sm, int
   }
 }
 
+// ---------------------------------------------------------------- bin pruning
+// Unperturbed set-up of a bin triangle with its perturbation margin and depth interval; a
+// triangle not drawable unperturbed (zero area, a vertex behind the near limit) gets tri = -2:
+// a perturbed version may still be drawable, so it is a candidate everywhere.
+__device__ __forceinline__ void stage_unperturbed(const SceneDev& S, const Workspace& ws, const float* m, int slot,
+                                                  int tri, long long rx, long long ry, TriS& d, float2& zr) {
+  Tri t;
+  setup_from_scene(S, m, tri, 0, 0, rx, ry, t);
+  store_side(d, t, tri);
+  if (!t.ok) d.tri = -2;
+  d.margin = ws.tri_margin[(long long)slot * S.nt + tri];
+  zr = ws.tri_z[(long long)slot * S.nt + tri];
+}
+
+// Does every perturbed version of t cover pixel (dx, dy)?  Each vertex moves at most margin per
+// axis, so at most sqrt(2) margin: a pixel farther than that from each edge line stays inside.
+__device__ __forceinline__ bool surely_covers(const TriS& t, int dx, int dy) {
+  if (t.tri < 0 || t.margin == 0x7FFFFFFF) return false;
+  bool sure = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
+    const float fa = (float)t.a[k], fb = (float)t.b[k];
+    const float reach = 1.41422f * (float)t.margin * sqrtf(fa * fa + fb * fb) * 1.0001f + 2.0f;
+    sure = sure && ((float)e > reach);
+  }
+  return sure;
+}
+
+// Can some perturbed version of t be the visible triangle at pixel (dx, dy)?  No if its
+// margin-widened edge functions miss the pixel, or if it lies entirely behind the far end of
+// a triangle that surely covers the pixel (zsure).
+__device__ __forceinline__ bool maybe_visible(const TriS& t, float2 zr, float zsure, int dx, int dy) {
+  if (t.tri == -2 || t.margin == 0x7FFFFFFF) return true;
+  bool maybe = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
+    const long long reach = (long long)t.margin * (long long)(abs(t.a[k]) + abs(t.b[k]));
+    maybe = maybe && (e + reach >= 0);
+  }
+  return maybe && zr.x <= zsure;
+}
+
+struct PruneSmem {
+  TriS t[NB];
+  float2 zr[NB];
+  uint32_t id[NB];
+  uint8_t live[NB];
+  float m[16];
+  int wsum[TILE_PX / 32];
+  int n_live;
+};
+
+// Exclusive prefix of flag over the CTA (256 threads); returns this thread's position and
+// the total in *total.
+__device__ __forceinline__ int block_prefix(int flag, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, flag);
+  const int in_warp = __popc(b & ((1u << lane) - 1u));
+  __syncthreads();
+  if (lane == 0) wsum[wid] = __popc(b);
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < TILE_PX / 32; ++w) {
+    before += w < wid ? wsum[w] : 0;
+    all += wsum[w];
+  }
+  *total = all;
+  return before + in_warp;
+}
+
+// Per (view slot, tile): drop from the bin every triangle that no perturbation of the call can
+// make visible at any pixel of the tile (outside all margin-widened pixel tests, or behind a
+// triangle that surely covers the pixel), compact the rest to the front of the bin's range,
+// record their number in tile_live and list the tile as a light item (<= light_bin live
+// triangles) or a heavy one, and store each pixel's candidate triangles in cand/ncand (light:
+// up to CMAX 8-bit live indices; heavy: up to kHeavyCand 16-bit ones).  The pruned triangles
+// never change any render of the call in this tile.
+__global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws, ViewList vl) {
+  __shared__ PruneSmem sm;
+  const int slot = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
+  const int ntl = n_tiles(S), n_all = vl.n * ntl;
+  if ((long long)ws.tile_off[n_all] > ws.bin_capacity) return;  // overflow: the bins were not stored
+  const uint32_t beg = ws.tile_off[slot * ntl + tile];
+  const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - beg);
+  if (nb == 0) return;
+  const int view = vl.id[slot];
+  const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+  const int dx = tid % TILE, dy = tid / TILE;
+  const bool valid = tx * TILE + dx < S.W && ty * TILE + dy < S.H;
+  const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
+  if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
+  __syncthreads();
+  auto stage = [&](int c0, int cnt) {
+    if (tid < cnt) {
+      const int tri = (int)ws.bins[beg + c0 + tid];
+      sm.id[tid] = (uint32_t)tri;
+      stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid]);
+      sm.live[tid] = 0;
+    }
+  };
+  // pass 1: nearest far end of the triangles that surely cover this pixel
+  float zsure = 3.4e38f;
+  for (int c0 = 0; c0 < nb; c0 += NB) {
+    const int cnt = min(NB, nb - c0);
+    __syncthreads();
+    stage(c0, cnt);
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j)
+      if (surely_covers(sm.t[j], dx, dy)) zsure = fminf(zsure, sm.zr[j].y);
+  }
+  // pass 2: mark and compact the triangles some pixel may see (a single chunk is still staged)
+  int n_live = 0;
+  for (int c0 = 0; c0 < nb; c0 += NB) {
+    const int cnt = min(NB, nb - c0);
+    if (nb > NB) {
+      __syncthreads();
+      stage(c0, cnt);
+    }
+    __syncthreads();
+    if (valid)
+      for (int j = 0; j < cnt; ++j)
+        if (!sm.live[j] && maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) sm.live[j] = 1;
+    __syncthreads();
+    const int f = tid < cnt ? sm.live[tid] : 0;
+    int total;
+    const int pos = block_prefix(f, sm.wsum, &total);
+    // positions only move towards the front, past entries this CTA has already read
+    if (f) ws.bins[beg + n_live + pos] = sm.id[tid];
+    n_live += total;
+  }
+  if (tid == 0) {
+    ws.tile_live[slot * ntl + tile] = (uint32_t)n_live;
+    const uint32_t it = ((uint32_t)slot << 24) | (uint32_t)tile;
+    if (n_live <= ws.light_bin) ws.items[atomicAdd(ws.counters + 0, 1u)] = it;
+    else ws.items[n_all - 1 - (int)atomicAdd(ws.counters + 4, 1u)] = it;
+  }
+  const long long ci = ((long long)slot * ntl + tile) * 2 * TILE_PX + tid;
+  if (n_live > ws.light_bin) {
+    // heavy tile: up to kHeavyCand candidates as 16-bit indices into the live list, found a
+    // chunk of live triangles at a time (ascending)
+    uint32_t cand[kHeavyCand / 2] = {};
+    int ncand = 0;
+    for (int c0 = 0; c0 < n_live; c0 += NB) {
+      const int cnt = min(NB, n_live - c0);
+      __syncthreads();
+      if (tid < cnt) {
+        const int tri = (int)ws.bins[beg + c0 + tid];
+        stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid]);
+      }
+      __syncthreads();
+      for (int j = 0; j < cnt; ++j) {
+        if (!maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) continue;
+        const uint32_t bits = (uint32_t)(c0 + j) << (16 * (ncand & 1));
+#pragma unroll
+        for (int wd = 0; wd < kHeavyCand / 2; ++wd)
+          if ((ncand >> 1) == wd) cand[wd] |= bits;
+        ++ncand;
+      }
+    }
+    ws.cand[ci] = make_int4((int)cand[0], (int)cand[1], (int)cand[2], (int)cand[3]);
+    ws.cand[ci + TILE_PX] = make_int4((int)cand[4], (int)cand[5], (int)cand[6], (int)cand[7]);
+    ws.ncand[((long long)slot * ntl + tile) * TILE_PX + tid] = (uint8_t)min(ncand, 255);
+    return;
+  }
+  // pass 3: each pixel's candidates among the live triangles, in their compacted order
+  __syncthreads();
+  if (tid < n_live) {
+    const int tri = (int)ws.bins[beg + tid];
+    stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid]);
+  }
+  __syncthreads();
+  uint32_t cand[CMAX / 4] = {};
+  int ncand = 0;
+  for (int j = 0; j < n_live; ++j) {
+    if (!maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) continue;
+    const uint32_t bits = (uint32_t)j << (8 * (ncand & 3));
+#pragma unroll
+    for (int wd = 0; wd < CMAX / 4; ++wd)
+      if ((ncand >> 2) == wd) cand[wd] |= bits;
+    ++ncand;
+  }
+  ws.cand[ci] = make_int4((int)cand[0], (int)cand[1], (int)cand[2], (int)cand[3]);
+  ws.ncand[((long long)slot * ntl + tile) * TILE_PX + tid] = (uint8_t)min(ncand, 255);
+}
+
 // Every light work item of one scene's call, taken one at a time from the scene's work
 // counter until none is left.
 template <int SH>
@@ -249,7 +439,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     const bool valid = px < S.W && py < S.H;
     const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
     const uint32_t bin_beg = ws.tile_off[slot * ntl + tile];
-    const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - bin_beg);
+    const int nb = (int)ws.tile_live[slot * ntl + tile];
     const int p0 = a.pair_begin + chunk * a.pairs_per_item;
     const int p1 = min(a.pair_begin + a.pair_count, p0 + a.pairs_per_item);
     if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
@@ -257,18 +447,11 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     clear_item_table(sm);
     __syncthreads();
 
-    // ---- per item: stage the bin unperturbed, build per-pixel candidate lists
+    // ---- per item: the bin's live triangles (pruned and compacted by k_bin_prune) and this
+    //      pixel's candidates among them
     if (tid < nb) {
       const int tri = (int)ws.bins[bin_beg + tid];
       sm.btri[tid] = tri;
-      Tri t;
-      setup_from_scene(S, sm.m, tri, 0, 0, rx, ry, t);
-      store_side(sm.side[0][tid], t, tri);
-      // not drawable unperturbed (zero area, or a vertex behind the near limit): a perturbed
-      // version may still be, so it stays a candidate for every pixel of the tile
-      if (!t.ok) sm.side[0][tid].tri = -2;
-      sm.side[0][tid].margin = ws.tri_margin[(long long)slot * S.nt + tri];
-      sm.zr[tid] = ws.tri_z[(long long)slot * S.nt + tri];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         sm.vid[tid][k] = __ldg(S.pidx + 3 * tri + k);
@@ -284,47 +467,10 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       sm.A_tri[tid] = 0.0f;
       sm.n_tri[tid] = 0u;
     }
-    __syncthreads();
-    // nearest far end of the triangles that cover this pixel whatever the perturbation
-    float zsure = 3.4e38f;
-    for (int j = 0; j < nb; ++j) {
-      const TriS& t = sm.side[0][j];
-      if (t.tri < 0 || t.margin == 0x7FFFFFFF) continue;
-      // every vertex moves at most margin per axis, so at most sqrt(2) margin: a pixel
-      // farther than that from each edge line stays inside every perturbed version
-      bool sure = true;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
-        const float fa = (float)t.a[k], fb = (float)t.b[k];
-        const float reach = 1.41422f * (float)t.margin * sqrtf(fa * fa + fb * fb) * 1.0001f + 2.0f;
-        sure = sure && ((float)e > reach);
-      }
-      if (sure) zsure = fminf(zsure, sm.zr[j].y);
-    }
-    uint32_t cand[CMAX / 4] = {};
-    int ncand = 0;
-    for (int j = 0; j < nb; ++j) {
-      const TriS& t = sm.side[0][j];
-      bool maybe = true;
-      if (t.tri != -2 && t.margin != 0x7FFFFFFF) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
-          const long long reach = (long long)t.margin * (long long)(abs(t.a[k]) + abs(t.b[k]));
-          maybe = maybe && (e + reach >= 0);
-        }
-        // surely behind a surely covering triangle: can never be the visible one
-        maybe = maybe && sm.zr[j].x <= zsure;
-      }
-      if (maybe) {
-        const uint32_t bits = (uint32_t)j << (8 * (ncand & 3));
-#pragma unroll
-        for (int wd = 0; wd < CMAX / 4; ++wd)
-          if ((ncand >> 2) == wd) cand[wd] |= bits;
-        ++ncand;
-      }
-    }
+    const long long ci = ((long long)slot * ntl + tile) * TILE_PX + tid;
+    const int4 cw = ws.cand[ci + ((long long)slot * ntl + tile) * TILE_PX];
+    const uint32_t cand[CMAX / 4] = {(uint32_t)cw.x, (uint32_t)cw.y, (uint32_t)cw.z, (uint32_t)cw.w};
+    const int ncand = ws.ncand[ci];
     const bool all_bin = ncand > CMAX;
     float3 tgt = f3(0.f, 0.f, 0.f);
     if (valid) {
@@ -336,7 +482,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     for (int pair = p0; pair < p1; ++pair) {
       const uint64_t pkey = sm.pk[pair - p0];
       const int par = pair & 1;
-      // the previous pair is complete (and the candidate build is done with side[0])
+      // the previous pair is complete (and the item's set-up is done)
       __syncthreads();
       // ---- F: fold the previous pair's credits with its signs (other parity buffers)
       if (pair > p0) fold(S, sm, nb, par ^ 1);
@@ -689,6 +835,11 @@ cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& 
   if (S.shading == SHADE_UNLIT) return launch_fast_t<SHADE_UNLIT>(S, ws, vl, a, grid, st);
   if (S.shading == SHADE_LAMBERT) return launch_fast_t<SHADE_LAMBERT>(S, ws, vl, a, grid, st);
   return launch_fast_t<SHADE_GGX>(S, ws, vl, a, grid, st);
+}
+
+cudaError_t launch_prune(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st) {
+  k_bin_prune<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fast_batch(const BatchArgs& P, int shading, int grid, cudaStream_t st) {

@@ -21,7 +21,7 @@ struct sge_scene {
   bool desc_dirty;            // desc_dev must be rewritten before the next batched call
   // kernel timing (sge_kernel_timing): event pairs around the fast kernel's launches
   static constexpr int kMaxTimed = 256;
-  cudaEvent_t tev[2 * kMaxTimed];
+  cudaEvent_t tev[4 * kMaxTimed];  // per timed call: before/after the fast kernel, after the heavy one
   int n_tev;                  // event pairs created (0 = timing off)
   int n_timed;                // pairs recorded since the last sge_kernel_time
 };
@@ -46,7 +46,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t tri_rect, tri_margin, tri_z, pverts, vbits, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf,
-      desc, total;
+      desc, tile_live, cand, ncand, total;
   int max_views, max_pairs;
   long long bin_capacity;
 };
@@ -106,6 +106,9 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   L.uvbuf = take(sizeof(float2) * 2 * (size_t)npx);
   L.dfbuf = take(sizeof(float) * (size_t)npx);
   L.desc = take(sizeof(AssetDesc));
+  L.tile_live = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
+  L.cand = take(sizeof(int4) * (size_t)(L.max_views * ntl) * 2 * TILE_PX);
+  L.ncand = take((size_t)(L.max_views * ntl) * TILE_PX);
   L.total = o;
   return SGE_OK;
 }
@@ -237,6 +240,9 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   w.bins = reinterpret_cast<uint32_t*>(base + L.bins);
   w.items = reinterpret_cast<uint32_t*>(base + L.items);
   w.counters = reinterpret_cast<uint32_t*>(base + L.counters);
+  w.tile_live = reinterpret_cast<uint32_t*>(base + L.tile_live);
+  w.cand = reinterpret_cast<int4*>(base + L.cand);
+  w.ncand = reinterpret_cast<uint8_t*>(base + L.ncand);
   w.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
   w.uvbuf = reinterpret_cast<float2*>(base + L.uvbuf);
   w.dfbuf = reinterpret_cast<float*>(base + L.dfbuf);
@@ -314,7 +320,7 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
   cudaError_t e = cudaSuccess;
   if (delta_f_out)
     e = cudaMemsetAsync(delta_f_out, 0, sizeof(float) * (size_t)n_views * pairs_per_view * s->dev.W * s->dev.H, st);
-  if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
+  if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st, true);
   // pairs run in blocks of at most max_pairs_per_call (the projected-vertex buffer holds one block)
   for (int p0 = 0; p0 < pairs_per_view && e == cudaSuccess; p0 += s->ws.max_pairs) {
     EstimateArgs b = a;
@@ -323,7 +329,7 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
     if (p0 > 0) e = rearm_work(s->ws, st);
     if (e == cudaSuccess) e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
     const cudaEvent_t* ev = nullptr;
-    if (s->n_tev && s->n_timed < sge_scene::kMaxTimed) ev = s->tev + 2 * s->n_timed++;
+    if (s->n_tev && s->n_timed < sge_scene::kMaxTimed) ev = s->tev + 4 * s->n_timed++;
     if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, b, s->grid_fast, s->grid_heavy, st, ev);
   }
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
@@ -439,7 +445,7 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
     }
     Workspace w = s->ws;
     w.light_bin = tu.light_bin;
-    if (e == cudaSuccess) e = launch_binning(s->dev, w, vls[i], st);
+    if (e == cudaSuccess) e = launch_binning(s->dev, w, vls[i], st, true);
     if (e == cudaSuccess && entries[i].loss_out) e = launch_background_loss(s->dev, w, vls[i], entries[i].loss_out, st);
   }
   // one persistent launch per kernel and shading model over every asset, per block of pairs
@@ -571,14 +577,14 @@ int sge_status(sge_scene* s, sge_stream_t stream, int32_t* device_status) {
 int sge_kernel_timing(sge_scene* s, int32_t enable) {
   if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
   if (enable && !s->n_tev) {
-    for (int i = 0; i < 2 * sge_scene::kMaxTimed; ++i) {
+    for (int i = 0; i < 4 * sge_scene::kMaxTimed; ++i) {
       cudaError_t e = cudaEventCreate(&s->tev[i]);
       if (e != cudaSuccess) {
         for (int j = 0; j < i; ++j) cudaEventDestroy(s->tev[j]);
         return cuda_fail(e, "sge_kernel_timing");
       }
     }
-    s->n_tev = 2 * sge_scene::kMaxTimed;
+    s->n_tev = 4 * sge_scene::kMaxTimed;
   } else if (!enable && s->n_tev) {
     for (int i = 0; i < s->n_tev; ++i) cudaEventDestroy(s->tev[i]);
     s->n_tev = 0;
@@ -587,19 +593,36 @@ int sge_kernel_timing(sge_scene* s, int32_t enable) {
   return SGE_OK;
 }
 
-int sge_kernel_time(sge_scene* s, float* total_ms, int32_t* launches) {
+int sge_kernel_time(sge_scene* s, float* total_ms, float* heavy_ms, int32_t* launches) {
   if (!s || !total_ms || !launches) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
-  float sum = 0.0f;
+  float sum = 0.0f, hsum = 0.0f;
   for (int k = 0; k < s->n_timed; ++k) {
-    float ms = 0.0f;
-    cudaError_t e = cudaEventSynchronize(s->tev[2 * k + 1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->tev[2 * k], s->tev[2 * k + 1]);
+    float ms = 0.0f, hms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(s->tev[4 * k + 2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, s->tev[4 * k], s->tev[4 * k + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&hms, s->tev[4 * k + 1], s->tev[4 * k + 2]);
     if (e != cudaSuccess) return cuda_fail(e, "sge_kernel_time");
     sum += ms;
+    hsum += hms;
   }
   *total_ms = sum;
+  if (heavy_ms) *heavy_ms = hsum;
   *launches = s->n_timed;
   s->n_timed = 0;
+  return SGE_OK;
+}
+
+int sge_bin_stats(sge_scene* s, sge_stream_t stream, int64_t* light_items, int64_t* heavy_items,
+                  int64_t* bin_entries) {
+  if (!s || !light_items || !heavy_items || !bin_entries) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  uint32_t c[6] = {0, 0, 0, 0, 0, 0};
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(c, s->ws.counters, sizeof(c), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sge_bin_stats");
+  *light_items = c[0];
+  *heavy_items = c[4];
+  *bin_entries = c[2];
   return SGE_OK;
 }
 

@@ -14,6 +14,7 @@ constexpr int TILE = 16;                 // tile edge in pixels; one CTA thread 
 constexpr int TILE_PX = TILE * TILE;     // 256 threads
 constexpr int kLightBin = 256;           // bins up to this size use the fast path
 constexpr int kMaxPairsPerItem = 64;     // longest run of pairs one work item takes
+constexpr int kHeavyCand = 16;           // candidate triangles kept per pixel of a heavy tile
 constexpr int kNotDrawn = (int)0x80000000;  // projected X of a vertex its triangles drop
 constexpr int ROLE_ALBEDO = SGE_ROLE_ALBEDO, ROLE_NORMAL = SGE_ROLE_NORMAL;
 constexpr int ROLE_ROUGHNESS = SGE_ROLE_ROUGHNESS, ROLE_METALLIC = SGE_ROLE_METALLIC;
@@ -75,6 +76,10 @@ struct Workspace {
   uint32_t* tile_cur;    // [max_views][n_tiles] fill cursors
   uint32_t* bins;        // [bin_capacity] triangle ids grouped by (view slot, tile)
   uint32_t* items;       // [max_views * n_tiles] (view slot << 24 | tile): light bins first, heavy from the end
+  uint32_t* tile_live;   // [max_views][n_tiles] triangles left at the front of each bin by k_bin_prune
+  int4* cand;            // [max_views][n_tiles][2][256] candidate triangles of each pixel: live indices,
+                         // 8-bit in the first word of a light tile, 16-bit in both words of a heavy one
+  uint8_t* ncand;        // [max_views][n_tiles][256] their number (> 16: test every live triangle)
   uint32_t* counters;    // [0] light items, [1] their work counter, [2] total bin entries, [3] status,
                          // [4] heavy items, [5] their work counter
   unsigned long long* keys;  // [2][H*W] staged depth|ID buffers (both sides)
@@ -119,8 +124,13 @@ struct BatchArgs {
 
 // ---- kernels launchers (all asynchronous on `st`)
 // Tile binning of every triangle for each view of `vl`, conservative for any
-// perturbation of at most eps_pos per coordinate.  Fills ws bins / items.
-cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st);
+// perturbation of at most eps_pos per coordinate.  Fills ws bins / items.  With `prune`
+// (the estimators), k_bin_prune then drops from each bin the triangles no perturbation can
+// make visible in the tile, lists the items by their live counts and stores each pixel's
+// candidate triangles.
+cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st,
+                           bool prune = false);
+cudaError_t launch_prune(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st);
 
 struct EstimateArgs {
   uint64_t seed;
@@ -135,7 +145,8 @@ struct EstimateArgs {
   float* delta_f;
 };
 // Both estimator kernels: the fast path over light bins, the general one over heavy bins.
-// ev_fast (two events, or NULL) are recorded on st right before and after the fast kernel.
+// ev_fast (three events, or NULL) are recorded on st right before and after the fast kernel
+// and after the heavy one.
 cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl,
                             const EstimateArgs& a, int grid_fast, int grid_heavy, cudaStream_t st,
                             const cudaEvent_t* ev_fast = nullptr);
