@@ -217,7 +217,10 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
-  const int n_chunks = (a.pair_count + a.pairs_per_item - 1) / a.pairs_per_item;
+  // heavy items cost many times a light one: a quarter of the run of pairs per work unit
+  // spreads the few of them over more CTAs
+  const int ppi = max(1, a.pairs_per_item / 4);
+  const int n_chunks = (a.pair_count + ppi - 1) / ppi;
   const long long n_work = (long long)ws.counters[4] * n_chunks;
   const int n_all = vl.n * ntl;
 
@@ -237,8 +240,8 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
     const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
     const uint32_t bin_beg = ws.tile_off[slot * ntl + tile];
     const int nb = (int)ws.tile_live[slot * ntl + tile];  // pruned and compacted by k_bin_prune
-    const int p0 = a.pair_begin + chunk * a.pairs_per_item;
-    const int p1 = min(a.pair_begin + a.pair_count, p0 + a.pairs_per_item);
+    const int p0 = a.pair_begin + chunk * ppi;
+    const int p1 = min(a.pair_begin + a.pair_count, p0 + ppi);
     if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
     float3 tgt = f3(0.f, 0.f, 0.f);
     if (valid) {

@@ -55,12 +55,13 @@ def run_both(sc, targets, seed, it, views, pairs, plain=False, footprint=0, gpu_
             df = torch.empty(len(views), pairs, sc.height, sc.width, device=g.device)
         g.estimate_grad(seed, it, views, pairs, grad, counts, loss=loss, delta_f=df)
     st = g.status()
+    bins = g.bin_stats() if not plain else None
     torch.cuda.synchronize()
     osc = oracle.OracleScene(sc, targets, footprint=footprint)
     res = oracle.estimate(osc, seed, it, views, pairs, per_pixel=want_df and not plain)
     out = dict(status=st, grad=grad.cpu().numpy().astype(np.float64),
                counts=counts.cpu().numpy().astype(np.int64).astype(np.uint64),
-               loss=loss.cpu().numpy().astype(np.float64), S=res[0], C=res[1], oloss=res[2])
+               loss=loss.cpu().numpy().astype(np.float64), S=res[0], C=res[1], oloss=res[2], bins=bins)
     if df is not None:
         out.update(df=df.cpu().numpy().astype(np.float64), odf=res[3], fmax=res[4], cond=res[5])
     return out

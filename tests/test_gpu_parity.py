@@ -101,6 +101,12 @@ ESTIMATE_CASES = {
     # 8K triangles at 96x96: light and heavy bins mixed, pixels with more candidates than kept
     "dense_mixed_bins": (lambda: _sphere(64, 64, 64, 96, 96, synth.random_eyes(2, 6), True), [1, 0], 3,
                          {"pairs_per_item": 2}),
+    # 32K triangles at 160^2 (unlit), 32K at 256^2 (Lambert), 64K at 256^2 (GGX): dense meshes whose
+    # tiles mix light bins and bins of more than 256 live triangles (the general kernel)
+    "dense_unlit": (lambda: _sphere(128, 128, 64, 160, 160, synth.random_eyes(2, 8), True), [0, 1], 2, {}),
+    "dense_lambert": (lambda: synth.config_autograd(n_views=2, pairs=2, render=256, tex=64), [1, 0], 2, {}),
+    "dense_ggx": (lambda: synth.config_scale(n_views=2, pairs=2, render=256, tex=64, n_lon=256, n_lat=128),
+                  [0, 1], 2, {"pairs_per_item": 1}),
     # 5 pairs projected in blocks of 2 (max_pairs_per_call): three launches of each estimator kernel
     "pair_blocks": (lambda: _sphere(64, 64, 128, 96, 96, synth.random_eyes(2, 7)), [0, 1], 5,
                     {"max_pairs_per_call": 2, "pairs_per_item": 2}),
@@ -115,6 +121,9 @@ def test_estimate_grad_matches_oracle(case):
     r = run_both(sc, tg, seed=11, it=2, views=views, pairs=pairs, gpu_kwargs=kw)
     assert_parity(sc, r)
     assert r["C"].sum() > 0 and np.abs(r["S"]).sum() > 0
+    if case in ("dense_unlit", "dense_lambert", "dense_ggx"):
+        light, heavy, _ = r["bins"]
+        assert light > 0 and heavy > 0, r["bins"]
 
 
 @pytest.mark.parametrize("case", ["plain_256_1view", "sphere8k_3views_ragged", "lambert_subdiv"])
