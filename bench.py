@@ -41,8 +41,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # kernel executes per antithetic pixel pair of the workload (smsp__inst_executed x active threads
 # per warp / pixel pairs), and its DRAM traffic per launch, both from the ncu capture summarised
 # in profiles/k_estimate_fast_sphere8k_r512.md (same kernel source).
-ALU_INSTR_PER_PIXEL_PAIR = 1389.0
-DRAM_BYTES_PER_LAUNCH = 101.42e6
+ALU_INSTR_PER_PIXEL_PAIR = 1067.0
+DRAM_BYTES_PER_LAUNCH = 126.52e6
 
 
 def dist_env():

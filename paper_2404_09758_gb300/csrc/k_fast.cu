@@ -226,28 +226,39 @@ __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE>& sm, int
 // ---------------------------------------------------------------- bin pruning
 // Unperturbed set-up of a bin triangle with its perturbation margin and depth interval; a
 // triangle not drawable unperturbed (zero area, a vertex behind the near limit) gets tri = -2:
-// a perturbed version may still be drawable, so it is a candidate everywhere.
+// a perturbed version may still be drawable, so it is a candidate everywhere.  reach[k]: how far
+// (edge-function units) a pixel must lie inside edge k to stay inside under every perturbation;
+// each vertex moves at most margin per axis, so at most sqrt(2) margin (+ slack); -1: never sure.
 __device__ __forceinline__ void stage_unperturbed(const SceneDev& S, const Workspace& ws, const float* m, int slot,
-                                                  int tri, long long rx, long long ry, TriS& d, float2& zr) {
+                                                  int tri, long long rx, long long ry, TriS& d, float2& zr,
+                                                  long long (&reach)[3]) {
   Tri t;
   setup_from_scene(S, m, tri, 0, 0, rx, ry, t);
   store_side(d, t, tri);
   if (!t.ok) d.tri = -2;
   d.margin = ws.tri_margin[(long long)slot * S.nt + tri];
   zr = ws.tri_z[(long long)slot * S.nt + tri];
+  const bool can = d.tri >= 0 && d.margin != 0x7FFFFFFF;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    long long r = -1;
+    if (can) {
+      const float fa = (float)d.a[k], fb = (float)d.b[k];
+      r = (long long)ceilf(1.41422f * (float)d.margin * sqrtf(fa * fa + fb * fb) * 1.0001f + 2.0f);
+    }
+    reach[k] = r;
+  }
 }
 
-// Does every perturbed version of t cover pixel (dx, dy)?  Each vertex moves at most margin per
-// axis, so at most sqrt(2) margin: a pixel farther than that from each edge line stays inside.
-__device__ __forceinline__ bool surely_covers(const TriS& t, int dx, int dy) {
-  if (t.tri < 0 || t.margin == 0x7FFFFFFF) return false;
+// Does every perturbed version of t cover pixel (dx, dy)?  (exact integer comparisons against the
+// staged reach)
+__device__ __forceinline__ bool surely_covers(const TriS& t, const long long (&reach)[3], int dx, int dy) {
+  if (reach[0] < 0) return false;
   bool sure = true;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
-    const float fa = (float)t.a[k], fb = (float)t.b[k];
-    const float reach = 1.41422f * (float)t.margin * sqrtf(fa * fa + fb * fb) * 1.0001f + 2.0f;
-    sure = sure && ((float)e > reach);
+    sure = sure && e > reach[k];
   }
   return sure;
 }
@@ -270,11 +281,12 @@ __device__ __forceinline__ bool maybe_visible(const TriS& t, float2 zr, float zs
 struct PruneSmem {
   TriS t[NB];
   float2 zr[NB];
+  long long reach[NB][3];
   uint32_t id[NB];
   uint8_t live[NB];
+  uint16_t remap[NB];  // compacted position of each live entry of a single-chunk bin
   float m[16];
   int wsum[TILE_PX / 32];
-  int n_live;
 };
 
 // Exclusive prefix of flag over the CTA (256 threads); returns this thread's position and
@@ -294,6 +306,47 @@ __device__ __forceinline__ int block_prefix(int flag, int* wsum, int* total) {
   }
   *total = all;
   return before + in_warp;
+}
+
+// Candidate list of one pixel: up to kHeavyCand 16-bit entries (light tiles repack them as 8-bit).
+struct CandList {
+  uint32_t w[kHeavyCand / 2];
+  int n;
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < kHeavyCand / 2; ++i) w[i] = 0u;
+    n = 0;
+  }
+  __device__ __forceinline__ void push(uint32_t j) {
+    const uint32_t bits = j << (16 * (n & 1));
+#pragma unroll
+    for (int i = 0; i < kHeavyCand / 2; ++i)
+      if ((n >> 1) == i) w[i] |= bits;
+    ++n;
+  }
+  __device__ __forceinline__ uint32_t get(int q) const {
+    uint32_t v = 0;
+#pragma unroll
+    for (int i = 0; i < kHeavyCand / 2; ++i)
+      if ((q >> 1) == i) v = w[i];
+    return (v >> (16 * (q & 1))) & 0xFFFFu;
+  }
+};
+
+// Store a pixel's list: 8-bit indices (light tile, <= CMAX kept) or 16-bit ones.
+__device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_index, int tid, const CandList& c,
+                                            bool wide) {
+  const long long ci = tile_index * 2 * TILE_PX + tid;
+  if (wide) {
+    ws.cand[ci] = make_int4((int)c.w[0], (int)c.w[1], (int)c.w[2], (int)c.w[3]);
+    ws.cand[ci + TILE_PX] = make_int4((int)c.w[4], (int)c.w[5], (int)c.w[6], (int)c.w[7]);
+  } else {
+    uint32_t b[CMAX / 4] = {};
+    const int k = min(c.n, CMAX);
+    for (int q = 0; q < k; ++q) b[q >> 2] |= c.get(q) << (8 * (q & 3));
+    ws.cand[ci] = make_int4((int)b[0], (int)b[1], (int)b[2], (int)b[3]);
+  }
+  ws.ncand[tile_index * TILE_PX + tid] = (uint8_t)min(c.n, 255);
 }
 
 // Per (view slot, tile): drop from the bin every triangle that no perturbation of the call can
@@ -316,14 +369,15 @@ __global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws,
   const int dx = tid % TILE, dy = tid / TILE;
   const bool valid = tx * TILE + dx < S.W && ty * TILE + dy < S.H;
   const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
+  const long long tix = (long long)slot * ntl + tile;
   if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
   __syncthreads();
-  auto stage = [&](int c0, int cnt) {
+  auto stage = [&](int c0, int cnt, bool from_live) {
     if (tid < cnt) {
       const int tri = (int)ws.bins[beg + c0 + tid];
       sm.id[tid] = (uint32_t)tri;
-      stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid]);
-      sm.live[tid] = 0;
+      stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid], sm.reach[tid]);
+      if (!from_live) sm.live[tid] = 0;
     }
   };
   // pass 1: nearest far end of the triangles that surely cover this pixel
@@ -331,84 +385,80 @@ __global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws,
   for (int c0 = 0; c0 < nb; c0 += NB) {
     const int cnt = min(NB, nb - c0);
     __syncthreads();
-    stage(c0, cnt);
+    stage(c0, cnt, false);
     __syncthreads();
     for (int j = 0; j < cnt; ++j)
-      if (surely_covers(sm.t[j], dx, dy)) zsure = fminf(zsure, sm.zr[j].y);
+      if (surely_covers(sm.t[j], sm.reach[j], dx, dy)) zsure = fminf(zsure, sm.zr[j].y);
   }
-  // pass 2: mark and compact the triangles some pixel may see (a single chunk is still staged)
+  // pass 2: mark and compact the triangles some pixel may see (a single chunk is still staged;
+  // its pixels' candidate lists are found on the way, by bin position, and renumbered below)
+  const bool single = nb <= NB;
+  CandList cl;
+  cl.clear();
   int n_live = 0;
   for (int c0 = 0; c0 < nb; c0 += NB) {
     const int cnt = min(NB, nb - c0);
-    if (nb > NB) {
+    if (!single) {
       __syncthreads();
-      stage(c0, cnt);
+      stage(c0, cnt, false);
     }
     __syncthreads();
-    if (valid)
-      for (int j = 0; j < cnt; ++j)
-        if (!sm.live[j] && maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) sm.live[j] = 1;
+    if (valid) {
+      if (single) {
+        for (int j = 0; j < cnt; ++j)
+          if (maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
+            sm.live[j] = 1;
+            if (cl.n < kHeavyCand) cl.push((uint32_t)j);
+            else ++cl.n;
+          }
+      } else {
+        for (int j = 0; j < cnt; ++j)
+          if (!sm.live[j] && maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) sm.live[j] = 1;
+      }
+    }
     __syncthreads();
     const int f = tid < cnt ? sm.live[tid] : 0;
     int total;
     const int pos = block_prefix(f, sm.wsum, &total);
     // positions only move towards the front, past entries this CTA has already read
-    if (f) ws.bins[beg + n_live + pos] = sm.id[tid];
+    if (f) {
+      ws.bins[beg + n_live + pos] = sm.id[tid];
+      if (single) sm.remap[tid] = (uint16_t)pos;
+    }
     n_live += total;
   }
   if (tid == 0) {
-    ws.tile_live[slot * ntl + tile] = (uint32_t)n_live;
+    ws.tile_live[tix] = (uint32_t)n_live;
     const uint32_t it = ((uint32_t)slot << 24) | (uint32_t)tile;
     if (n_live <= ws.light_bin) ws.items[atomicAdd(ws.counters + 0, 1u)] = it;
     else ws.items[n_all - 1 - (int)atomicAdd(ws.counters + 4, 1u)] = it;
   }
-  const long long ci = ((long long)slot * ntl + tile) * 2 * TILE_PX + tid;
-  if (n_live > ws.light_bin) {
-    // heavy tile: up to kHeavyCand candidates as 16-bit indices into the live list, found a
-    // chunk of live triangles at a time (ascending)
-    uint32_t cand[kHeavyCand / 2] = {};
-    int ncand = 0;
-    for (int c0 = 0; c0 < n_live; c0 += NB) {
-      const int cnt = min(NB, n_live - c0);
-      __syncthreads();
-      if (tid < cnt) {
-        const int tri = (int)ws.bins[beg + c0 + tid];
-        stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid]);
-      }
-      __syncthreads();
-      for (int j = 0; j < cnt; ++j) {
-        if (!maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) continue;
-        const uint32_t bits = (uint32_t)(c0 + j) << (16 * (ncand & 1));
-#pragma unroll
-        for (int wd = 0; wd < kHeavyCand / 2; ++wd)
-          if ((ncand >> 1) == wd) cand[wd] |= bits;
-        ++ncand;
-      }
-    }
-    ws.cand[ci] = make_int4((int)cand[0], (int)cand[1], (int)cand[2], (int)cand[3]);
-    ws.cand[ci + TILE_PX] = make_int4((int)cand[4], (int)cand[5], (int)cand[6], (int)cand[7]);
-    ws.ncand[((long long)slot * ntl + tile) * TILE_PX + tid] = (uint8_t)min(ncand, 255);
+  const bool wide = n_live > ws.light_bin;  // heavy tile: 16-bit indices
+  if (single) {
+    __syncthreads();
+    CandList out;
+    out.clear();
+    const int k = min(cl.n, kHeavyCand);
+    for (int q = 0; q < k; ++q) out.push(sm.remap[cl.get(q)]);
+    out.n = cl.n;
+    store_cands(ws, tix, tid, out, wide);
     return;
   }
-  // pass 3: each pixel's candidates among the live triangles, in their compacted order
-  __syncthreads();
-  if (tid < n_live) {
-    const int tri = (int)ws.bins[beg + tid];
-    stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid]);
+  // pass 3 (bins of more than one chunk): each pixel's candidates among the live triangles, in
+  // their compacted order, a chunk of live triangles at a time (ascending)
+  for (int c0 = 0; c0 < n_live; c0 += NB) {
+    const int cnt = min(NB, n_live - c0);
+    __syncthreads();
+    stage(c0, cnt, true);
+    __syncthreads();
+    if (valid)
+      for (int j = 0; j < cnt; ++j)
+        if (maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
+          if (cl.n < kHeavyCand) cl.push((uint32_t)(c0 + j));
+          else ++cl.n;
+        }
   }
-  __syncthreads();
-  uint32_t cand[CMAX / 4] = {};
-  int ncand = 0;
-  for (int j = 0; j < n_live; ++j) {
-    if (!maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) continue;
-    const uint32_t bits = (uint32_t)j << (8 * (ncand & 3));
-#pragma unroll
-    for (int wd = 0; wd < CMAX / 4; ++wd)
-      if ((ncand >> 2) == wd) cand[wd] |= bits;
-    ++ncand;
-  }
-  ws.cand[ci] = make_int4((int)cand[0], (int)cand[1], (int)cand[2], (int)cand[3]);
-  ws.ncand[((long long)slot * ntl + tile) * TILE_PX + tid] = (uint8_t)min(ncand, 255);
+  store_cands(ws, tix, tid, cl, wide);
 }
 
 // Every light work item of one scene's call, taken one at a time from the scene's work
