@@ -25,7 +25,11 @@ namespace sge {
 namespace {
 
 constexpr int BIN_CHUNK = 256;     // triangles staged per pass (one per thread)
-constexpr int TABLE = 2048;        // hash-table slots (power of two)
+// hash-table slots (power of two): unlit tiles credit one texture, the lit models up to four
+template <int SH_LIT>
+struct HeavyTable {
+  static constexpr int SLOTS = SH_LIT ? 4096 : 2048;
+};
 constexpr int MAX_PROBE = 32;
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 
@@ -38,17 +42,19 @@ struct SideSmem {
   int tri[BIN_CHUNK];  // -1 when not drawn on this side
 };
 
+template <int HT>
 struct TableSmem {
-  uint32_t key[TABLE];
-  float A[TABLE];
-  uint32_t n[TABLE];
-  float S[4][TABLE];
-  uint32_t cnt[TABLE];
+  uint32_t key[HT];
+  float A[HT];
+  uint32_t n[HT];
+  float S[4][HT];
+  uint32_t cnt[HT];
 };
 
+template <int HT>
 struct Smem {
   SideSmem side[2];
-  TableSmem tab;
+  TableSmem<HT> tab;
   float m[16];
   float red[TILE_PX / 32];
   uint32_t item;
@@ -108,17 +114,19 @@ __device__ __forceinline__ unsigned long long test_key(const SideSmem& s, int j,
   return ((unsigned long long)ordered_bits(d) << 32) | (uint32_t)tri;
 }
 
+template <int HT>
 __device__ __forceinline__ uint32_t slot_hash(uint32_t k) {
   k ^= k >> 16;
   k *= 0x7feb352du;
   k ^= k >> 15;
-  return k & (TABLE - 1);
+  return k & (HT - 1);
 }
 
 // Credit df to key: shared-memory table, or global atomics when the table is full.
-__device__ __forceinline__ void credit(const SceneDev& S, TableSmem& tb, uint32_t key, float df, uint64_t pkey,
+template <int HT>
+__device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT>& tb, uint32_t key, float df, uint64_t pkey,
                                        float* grad, uint32_t* counts) {
-  uint32_t slot = slot_hash(key);
+  uint32_t slot = slot_hash<HT>(key);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
     uint32_t k = *(volatile uint32_t*)&tb.key[slot];
@@ -128,7 +136,7 @@ __device__ __forceinline__ void credit(const SceneDev& S, TableSmem& tb, uint32_
       atomicAdd(&tb.n[slot], 1u);
       return;
     }
-    slot = (slot + 1) & (TABLE - 1);
+    slot = (slot + 1) & (HT - 1);
   }
   long long base;
   int nch;
@@ -141,8 +149,9 @@ __device__ __forceinline__ void credit(const SceneDev& S, TableSmem& tb, uint32_
 }
 
 // Fold the pair's per-key sums into the per-channel accumulators (signs of this pair).
-__device__ __forceinline__ void fold(const SceneDev& S, TableSmem& tb, uint64_t pkey) {
-  for (int slot = threadIdx.x; slot < TABLE; slot += blockDim.x) {
+template <int HT>
+__device__ __forceinline__ void fold(const SceneDev& S, TableSmem<HT>& tb, uint64_t pkey) {
+  for (int slot = threadIdx.x; slot < HT; slot += blockDim.x) {
     uint32_t key = tb.key[slot];
     if (key == EMPTY) continue;
     uint32_t nn = tb.n[slot];
@@ -158,8 +167,9 @@ __device__ __forceinline__ void fold(const SceneDev& S, TableSmem& tb, uint64_t 
   }
 }
 
-__device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem& tb, float* grad, uint32_t* counts) {
-  for (int slot = threadIdx.x; slot < TABLE; slot += blockDim.x) {
+template <int HT>
+__device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem<HT>& tb, float* grad, uint32_t* counts) {
+  for (int slot = threadIdx.x; slot < HT; slot += blockDim.x) {
     uint32_t key = tb.key[slot];
     if (key != EMPTY) {
       long long base;
@@ -198,10 +208,14 @@ __device__ __forceinline__ void setup_from_pverts(const SceneDev& S, const Works
 }
 
 // the batched kernels keep their asset after the kernel's own shared memory, 16-byte aligned
-constexpr size_t kHeavyBatchOff = (sizeof(Smem) + 15) & ~(size_t)15;
+template <int HT>
+constexpr size_t heavy_batch_off() {
+  return (sizeof(Smem<HT>) + 15) & ~(size_t)15;
+}
 
-__device__ __forceinline__ void clear_table(TableSmem& tb) {
-  for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
+template <int HT>
+__device__ __forceinline__ void clear_table(TableSmem<HT>& tb) {
+  for (int s = threadIdx.x; s < HT; s += blockDim.x) {
     tb.key[s] = EMPTY;
     tb.A[s] = 0.0f;
     tb.n[s] = 0u;
@@ -212,8 +226,9 @@ __device__ __forceinline__ void clear_table(TableSmem& tb) {
 }
 
 // Every heavy work item of one scene's call (the table starts and ends each item empty).
+template <int HT>
 __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& ws, const ViewList& vl,
-                                            const EstimateArgs& a, Smem& sm) {
+                                            const EstimateArgs& a, Smem<HT>& sm) {
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
@@ -253,9 +268,15 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
     // this pixel's candidate triangles (16-bit indices into the live list, ascending; more than
     // kHeavyCand: test every live triangle)
     const long long ti = (long long)slot * ntl + tile;
-    const int4 cw0 = ws.cand[ti * 2 * TILE_PX + tid], cw1 = ws.cand[ti * 2 * TILE_PX + TILE_PX + tid];
-    const uint32_t cand[kHeavyCand / 2] = {(uint32_t)cw0.x, (uint32_t)cw0.y, (uint32_t)cw0.z, (uint32_t)cw0.w,
-                                          (uint32_t)cw1.x, (uint32_t)cw1.y, (uint32_t)cw1.z, (uint32_t)cw1.w};
+    uint32_t cand[kHeavyCand / 2];
+#pragma unroll
+    for (int w = 0; w < kCandWords; ++w) {
+      const int4 cw = ws.cand[(ti * kCandWords + w) * TILE_PX + tid];
+      cand[4 * w] = (uint32_t)cw.x;
+      cand[4 * w + 1] = (uint32_t)cw.y;
+      cand[4 * w + 2] = (uint32_t)cw.z;
+      cand[4 * w + 3] = (uint32_t)cw.w;
+    }
     const int ncand = ws.ncand[ti * TILE_PX + tid];
     const bool all_live = ncand > kHeavyCand;
 
@@ -355,24 +376,26 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
   }
 }
 
+template <int HT>
 __global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  Smem<HT>& sm = *reinterpret_cast<Smem<HT>*>(smem_raw);
   clear_table(sm.tab);
-  heavy_items(S, ws, vl, a, sm);
+  heavy_items<HT>(S, ws, vl, a, sm);
 }
 
 // Batched form: the assets of P in order, each until its heavy items run out.
+template <int HT>
 __global__ void __launch_bounds__(TILE_PX) k_estimate_heavy_batch(const BatchArgs P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
-  BatchSmem& b = *reinterpret_cast<BatchSmem*>(smem_raw + kHeavyBatchOff);
+  Smem<HT>& sm = *reinterpret_cast<Smem<HT>*>(smem_raw);
+  BatchSmem& b = *reinterpret_cast<BatchSmem*>(smem_raw + heavy_batch_off<HT>());
   clear_table(sm.tab);
   for (int ai = 0; ai < P.n; ++ai) {
     __syncthreads();
     load_asset(P, ai, b);
     __syncthreads();
-    heavy_items(b.d.S, b.d.ws, b.vl, b.a, sm);
+    heavy_items<HT>(b.d.S, b.d.ws, b.vl, b.a, sm);
   }
 }
 
@@ -404,29 +427,30 @@ __global__ void k_background_loss(SceneDev S, Workspace ws, ViewList vl, float* 
   if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(loss + slot, v);
 }
 
-}  // namespace
-
-int estimate_blocks_per_sm() {
-  static int cached = -1;
-  if (cached < 0) {
-    int n = 0;
-    cudaFuncSetAttribute(k_estimate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy, TILE_PX, sizeof(Smem));
-    cached = n > 0 ? n : 1;
+template <int HT>
+int heavy_blocks_t(bool batch) {
+  int n = 0;
+  if (batch) {
+    const int bytes = (int)(heavy_batch_off<HT>() + sizeof(BatchSmem));
+    cudaFuncSetAttribute(k_estimate_heavy_batch<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy_batch<HT>, TILE_PX, bytes);
+  } else {
+    cudaFuncSetAttribute(k_estimate_heavy<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<HT>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy<HT>, TILE_PX, sizeof(Smem<HT>));
   }
-  return cached;
+  return n > 0 ? n : 1;
 }
 
-int heavy_batch_blocks_per_sm() {
-  static int cached = -1;
-  if (cached < 0) {
-    int n = 0;
-    const int bytes = (int)(kHeavyBatchOff + sizeof(BatchSmem));
-    cudaFuncSetAttribute(k_estimate_heavy_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy_batch, TILE_PX, bytes);
-    cached = n > 0 ? n : 1;
-  }
-  return cached;
+constexpr int kHtUnlit = HeavyTable<0>::SLOTS, kHtLit = HeavyTable<1>::SLOTS;
+
+}  // namespace
+
+int estimate_blocks_per_sm(int shading) {
+  return shading == SHADE_UNLIT ? heavy_blocks_t<kHtUnlit>(false) : heavy_blocks_t<kHtLit>(false);
+}
+
+int heavy_batch_blocks_per_sm(int shading) {
+  return shading == SHADE_UNLIT ? heavy_blocks_t<kHtUnlit>(true) : heavy_blocks_t<kHtLit>(true);
 }
 
 cudaError_t launch_put_desc(const AssetDesc& d, AssetDesc* dst, cudaStream_t st) {
@@ -434,12 +458,31 @@ cudaError_t launch_put_desc(const AssetDesc& d, AssetDesc* dst, cudaStream_t st)
   return cudaGetLastError();
 }
 
-cudaError_t launch_heavy_batch(const BatchArgs& P, int grid, cudaStream_t st) {
-  const int bytes = (int)(kHeavyBatchOff + sizeof(BatchSmem));
-  cudaError_t e = cudaFuncSetAttribute(k_estimate_heavy_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+namespace {
+
+template <int HT>
+cudaError_t launch_heavy_batch_t(const BatchArgs& P, int grid, cudaStream_t st) {
+  const int bytes = (int)(heavy_batch_off<HT>() + sizeof(BatchSmem));
+  cudaError_t e = cudaFuncSetAttribute(k_estimate_heavy_batch<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  k_estimate_heavy_batch<<<grid, TILE_PX, bytes, st>>>(P);
+  k_estimate_heavy_batch<HT><<<grid, TILE_PX, bytes, st>>>(P);
   return cudaGetLastError();
+}
+
+template <int HT>
+cudaError_t launch_heavy_t(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
+                           int grid, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_estimate_heavy<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(Smem<HT>));
+  if (e != cudaSuccess) return e;
+  k_estimate_heavy<HT><<<grid, TILE_PX, sizeof(Smem<HT>), st>>>(S, ws, vl, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_heavy_batch(const BatchArgs& P, int shading, int grid, cudaStream_t st) {
+  return shading == SHADE_UNLIT ? launch_heavy_batch_t<kHtUnlit>(P, grid, st) : launch_heavy_batch_t<kHtLit>(P, grid, st);
 }
 
 cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
@@ -448,10 +491,9 @@ cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewLi
   if (e == cudaSuccess) e = launch_fast(S, ws, vl, a, grid_fast, st);
   if (e == cudaSuccess && ev_fast) e = cudaEventRecord(ev_fast[1], st);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_estimate_heavy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-  if (e != cudaSuccess) return e;
-  k_estimate_heavy<<<grid_heavy, TILE_PX, sizeof(Smem), st>>>(S, ws, vl, a);
-  if (ev_fast) e = cudaEventRecord(ev_fast[2], st);
+  e = S.shading == SHADE_UNLIT ? launch_heavy_t<kHtUnlit>(S, ws, vl, a, grid_heavy, st)
+                               : launch_heavy_t<kHtLit>(S, ws, vl, a, grid_heavy, st);
+  if (e == cudaSuccess && ev_fast) e = cudaEventRecord(ev_fast[2], st);
   if (e != cudaSuccess) return e;
   if (a.loss && a.pair_begin == 0) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);
   return cudaGetLastError();

@@ -336,10 +336,12 @@ struct CandList {
 // Store a pixel's list: 8-bit indices (light tile, <= CMAX kept) or 16-bit ones.
 __device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_index, int tid, const CandList& c,
                                             bool wide) {
-  const long long ci = tile_index * 2 * TILE_PX + tid;
+  const long long ci = tile_index * kCandWords * TILE_PX + tid;
   if (wide) {
-    ws.cand[ci] = make_int4((int)c.w[0], (int)c.w[1], (int)c.w[2], (int)c.w[3]);
-    ws.cand[ci + TILE_PX] = make_int4((int)c.w[4], (int)c.w[5], (int)c.w[6], (int)c.w[7]);
+#pragma unroll
+    for (int w = 0; w < kCandWords; ++w)
+      ws.cand[ci + w * TILE_PX] =
+          make_int4((int)c.w[4 * w], (int)c.w[4 * w + 1], (int)c.w[4 * w + 2], (int)c.w[4 * w + 3]);
   } else {
     uint32_t b[CMAX / 4] = {};
     const int k = min(c.n, CMAX);
@@ -518,7 +520,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       sm.n_tri[tid] = 0u;
     }
     const long long ci = ((long long)slot * ntl + tile) * TILE_PX + tid;
-    const int4 cw = ws.cand[ci + ((long long)slot * ntl + tile) * TILE_PX];
+    const int4 cw = ws.cand[((long long)slot * ntl + tile) * kCandWords * TILE_PX + tid];
     const uint32_t cand[CMAX / 4] = {(uint32_t)cw.x, (uint32_t)cw.y, (uint32_t)cw.z, (uint32_t)cw.w};
     const int ncand = ws.ncand[ci];
     const bool all_bin = ncand > CMAX;

@@ -107,7 +107,7 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   L.dfbuf = take(sizeof(float) * (size_t)npx);
   L.desc = take(sizeof(AssetDesc));
   L.tile_live = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
-  L.cand = take(sizeof(int4) * (size_t)(L.max_views * ntl) * 2 * TILE_PX);
+  L.cand = take(sizeof(int4) * (size_t)(L.max_views * ntl) * kCandWords * TILE_PX);
   L.ncand = take((size_t)(L.max_views * ntl) * TILE_PX);
   L.total = o;
   return SGE_OK;
@@ -263,7 +263,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   }
   int bps = (s->cfg.blocks_per_sm > 0) ? s->cfg.blocks_per_sm : fast_blocks_per_sm(desc->shading);
   s->grid_fast = sms * bps;
-  s->grid_heavy = sms * estimate_blocks_per_sm();
+  s->grid_heavy = sms * estimate_blocks_per_sm(desc->shading);
   if (s->cfg.pairs_per_item <= 0) s->cfg.pairs_per_item = 16;
   if (s->cfg.pairs_per_item > kMaxPairsPerItem) s->cfg.pairs_per_item = kMaxPairsPerItem;
   *out = s;
@@ -482,7 +482,7 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
       if (P.n == 0) continue;
       const int bps = tu.blocks_per_sm > 0 ? tu.blocks_per_sm : fast_batch_blocks_per_sm(sh);
       e = launch_fast_batch(P, sh, sms * bps, st);
-      if (e == cudaSuccess) e = launch_heavy_batch(P, sms * heavy_batch_blocks_per_sm(), st);
+      if (e == cudaSuccess) e = launch_heavy_batch(P, sh, sms * heavy_batch_blocks_per_sm(sh), st);
     }
   }
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad_batch");

@@ -14,7 +14,8 @@ constexpr int TILE = 16;                 // tile edge in pixels; one CTA thread 
 constexpr int TILE_PX = TILE * TILE;     // 256 threads
 constexpr int kLightBin = 256;           // bins up to this size use the fast path
 constexpr int kMaxPairsPerItem = 64;     // longest run of pairs one work item takes
-constexpr int kHeavyCand = 16;           // candidate triangles kept per pixel of a heavy tile
+constexpr int kHeavyCand = 32;           // candidate triangles kept per pixel of a heavy tile
+constexpr int kCandWords = kHeavyCand / 8;  // int4 words of a pixel's candidate list
 constexpr int kNotDrawn = (int)0x80000000;  // projected X of a vertex its triangles drop
 constexpr int ROLE_ALBEDO = SGE_ROLE_ALBEDO, ROLE_NORMAL = SGE_ROLE_NORMAL;
 constexpr int ROLE_ROUGHNESS = SGE_ROLE_ROUGHNESS, ROLE_METALLIC = SGE_ROLE_METALLIC;
@@ -77,8 +78,8 @@ struct Workspace {
   uint32_t* bins;        // [bin_capacity] triangle ids grouped by (view slot, tile)
   uint32_t* items;       // [max_views * n_tiles] (view slot << 24 | tile): light bins first, heavy from the end
   uint32_t* tile_live;   // [max_views][n_tiles] triangles left at the front of each bin by k_bin_prune
-  int4* cand;            // [max_views][n_tiles][2][256] candidate triangles of each pixel: live indices,
-                         // 8-bit in the first word of a light tile, 16-bit in both words of a heavy one
+  int4* cand;            // [max_views][n_tiles][kCandWords][256] candidate triangles of each pixel: live
+                         // indices, 8-bit in the first word of a light tile, 16-bit in all words of a heavy one
   uint8_t* ncand;        // [max_views][n_tiles][256] their number (> 16: test every live triangle)
   uint32_t* counters;    // [0] light items, [1] their work counter, [2] total bin entries, [3] status,
                          // [4] heavy items, [5] their work counter
@@ -155,7 +156,7 @@ cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& 
 // Perturbed, projected vertices of both sides for every (view slot, pair) of a block of pairs.
 cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                                cudaStream_t st);
-int estimate_blocks_per_sm();
+int estimate_blocks_per_sm(int shading);
 int fast_blocks_per_sm(int shading);
 
 // Batched form of the two estimator kernels over BatchArgs' assets.
@@ -164,9 +165,9 @@ cudaError_t launch_background_loss(const SceneDev& S, const Workspace& ws, const
                                    cudaStream_t st);
 cudaError_t launch_put_desc(const AssetDesc& d, AssetDesc* dst, cudaStream_t st);
 cudaError_t launch_fast_batch(const BatchArgs& P, int shading, int grid, cudaStream_t st);
-cudaError_t launch_heavy_batch(const BatchArgs& P, int grid, cudaStream_t st);
+cudaError_t launch_heavy_batch(const BatchArgs& P, int shading, int grid, cudaStream_t st);
 int fast_batch_blocks_per_sm(int shading);
-int heavy_batch_blocks_per_sm();
+int heavy_batch_blocks_per_sm(int shading);
 
 // Staged path: render one side of one estimate into keys/uv/rgb.
 cudaError_t launch_render(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key,
