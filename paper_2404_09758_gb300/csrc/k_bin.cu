@@ -189,16 +189,17 @@ __global__ void k_bin_fill(SceneDev S, Workspace ws) {
 
 }  // namespace
 
-cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st, bool prune) {
+cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st, bool prune,
+                           bool defer_prune) {
   int nt = n_tiles(S);
   cudaError_t e = cudaMemsetAsync(ws.tile_count, 0, sizeof(uint32_t) * (size_t)vl.n * nt, st);
   if (e != cudaSuccess) return e;
   dim3 grid((S.nt + 255) / 256, vl.n);
   k_bin_rect_count<<<grid, 256, 0, st>>>(S, ws, vl);
-  k_bin_scan<<<1, 1024, 0, st>>>(ws, vl.n * nt, nt, prune ? 0 : 1);
+  k_bin_scan<<<1, 1024, 0, st>>>(ws, vl.n * nt, nt, prune || defer_prune ? 0 : 1);
   k_bin_fill<<<grid, 256, 0, st>>>(S, ws);
   e = cudaGetLastError();
-  if (e == cudaSuccess && prune) e = launch_prune(S, ws, vl, st);
+  if (e == cudaSuccess && prune && !defer_prune) e = launch_prune(S, ws, vl, st);
   return e;
 }
 

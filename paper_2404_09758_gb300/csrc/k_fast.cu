@@ -358,15 +358,14 @@ __device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_
 // triangles) or a heavy one, and store each pixel's candidate triangles in cand/ncand (light:
 // up to CMAX 8-bit live indices; heavy: up to kHeavyCand 16-bit ones).  The pruned triangles
 // never change any render of the call in this tile.
-__global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws, ViewList vl) {
-  __shared__ PruneSmem sm;
-  const int slot = blockIdx.y, tile = blockIdx.x, tid = threadIdx.x;
-  const int ntl = n_tiles(S), n_all = vl.n * ntl;
+__device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& ws, int n_views, int view, int slot,
+                                           int tile, int light_bin, PruneSmem& sm) {
+  const int tid = threadIdx.x;
+  const int ntl = n_tiles(S), n_all = n_views * ntl;
   if ((long long)ws.tile_off[n_all] > ws.bin_capacity) return;  // overflow: the bins were not stored
   const uint32_t beg = ws.tile_off[slot * ntl + tile];
   const int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - beg);
   if (nb == 0) return;
-  const int view = vl.id[slot];
   const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
   const int dx = tid % TILE, dy = tid / TILE;
   const bool valid = tx * TILE + dx < S.W && ty * TILE + dy < S.H;
@@ -432,10 +431,10 @@ __global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws,
   if (tid == 0) {
     ws.tile_live[tix] = (uint32_t)n_live;
     const uint32_t it = ((uint32_t)slot << 24) | (uint32_t)tile;
-    if (n_live <= ws.light_bin) ws.items[atomicAdd(ws.counters + 0, 1u)] = it;
+    if (n_live <= light_bin) ws.items[atomicAdd(ws.counters + 0, 1u)] = it;
     else ws.items[n_all - 1 - (int)atomicAdd(ws.counters + 4, 1u)] = it;
   }
-  const bool wide = n_live > ws.light_bin;  // heavy tile: 16-bit indices
+  const bool wide = n_live > light_bin;  // heavy tile: 16-bit indices
   if (single) {
     __syncthreads();
     CandList out;
@@ -461,6 +460,23 @@ __global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws,
         }
   }
   store_cands(ws, tix, tid, cl, wide);
+}
+
+__global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws, ViewList vl) {
+  __shared__ PruneSmem sm;
+  prune_tile(S, ws, vl.n, vl.id[blockIdx.y], blockIdx.y, blockIdx.x, ws.light_bin, sm);
+}
+
+// Batched form: every (tile, view slot, asset) of a batched call in one launch; each CTA reads
+// its asset's scene and workspace from the asset's launch descriptor in device memory.
+__global__ void __launch_bounds__(TILE_PX) k_bin_prune_batch(const BatchArgs P) {
+  __shared__ PruneSmem sm;
+  const BatchAsset& A = P.as[blockIdx.z];
+  const int slot = blockIdx.y;
+  if (slot >= A.n_views) return;
+  const AssetDesc& D = *A.desc;
+  if ((int)blockIdx.x >= D.S.tiles_x * D.S.tiles_y) return;
+  prune_tile(D.S, D.ws, A.n_views, A.view[slot], slot, blockIdx.x, P.light_bin, sm);
 }
 
 // Every light work item of one scene's call, taken one at a time from the scene's work
@@ -891,6 +907,11 @@ cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& 
 
 cudaError_t launch_prune(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st) {
   k_bin_prune<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prune_batch(const BatchArgs& P, int max_tiles, int max_views, cudaStream_t st) {
+  k_bin_prune_batch<<<dim3(max_tiles, max_views, P.n), TILE_PX, 0, st>>>(P);
   return cudaGetLastError();
 }
 

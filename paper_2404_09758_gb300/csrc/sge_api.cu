@@ -443,10 +443,27 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
       e = launch_put_desc(d, s->desc_dev, st);
       if (e == cudaSuccess) s->desc_dirty = false;
     }
-    Workspace w = s->ws;
-    w.light_bin = tu.light_bin;
-    if (e == cudaSuccess) e = launch_binning(s->dev, w, vls[i], st, true);
-    if (e == cudaSuccess && entries[i].loss_out) e = launch_background_loss(s->dev, w, vls[i], entries[i].loss_out, st);
+    if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vls[i], st, true, true);
+    if (e == cudaSuccess && entries[i].loss_out)
+      e = launch_background_loss(s->dev, s->ws, vls[i], entries[i].loss_out, st);
+  }
+  // every asset's bins pruned and listed in one launch
+  {
+    BatchArgs Q;
+    memset(&Q, 0, sizeof(Q));
+    Q.light_bin = tu.light_bin;
+    int max_tiles = 1, max_views = 1;
+    for (int i = 0; i < n; ++i) {
+      const sge_scene* s = entries[i].scene;
+      BatchAsset& A = Q.as[Q.n++];
+      A.desc = s->desc_dev;
+      A.n_views = vls[i].n;
+      for (int v = 0; v < vls[i].n; ++v) A.view[v] = vls[i].id[v];
+      const int nt = s->dev.tiles_x * s->dev.tiles_y;
+      if (nt > max_tiles) max_tiles = nt;
+      if (vls[i].n > max_views) max_views = vls[i].n;
+    }
+    if (e == cudaSuccess) e = launch_prune_batch(Q, max_tiles, max_views, st);
   }
   // one persistent launch per kernel and shading model over every asset, per block of pairs
   for (int p0 = 0; p0 < pairs_per_view && e == cudaSuccess; p0 += max_pairs) {
@@ -467,6 +484,7 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
       P.pairs_per_item = tu.pairs_per_item;
       P.pair_begin = p0;
       P.pair_count = pc;
+      P.light_bin = tu.light_bin;
       for (int k = 0; k < n; ++k) {
         const int i = order[k];
         sge_scene* s = entries[i].scene;

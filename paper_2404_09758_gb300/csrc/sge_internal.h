@@ -119,9 +119,12 @@ struct BatchArgs {
   int pairs_per_item;
   int pair_begin;
   int pair_count;
+  int light_bin;       // tiles with at most this many live triangles are light items
   int n;
   BatchAsset as[SGE_MAX_BATCH];
 };
+// Pruning of every asset of P in one launch (after each asset's binning with defer_prune).
+cudaError_t launch_prune_batch(const BatchArgs& P, int max_tiles, int max_views, cudaStream_t st);
 
 // ---- kernels launchers (all asynchronous on `st`)
 // Tile binning of every triangle for each view of `vl`, conservative for any
@@ -129,8 +132,9 @@ struct BatchArgs {
 // (the estimators), k_bin_prune then drops from each bin the triangles no perturbation can
 // make visible in the tile, lists the items by their live counts and stores each pixel's
 // candidate triangles.
+// defer_prune: the caller prunes later (k_bin_prune_batch): the scan lists no items either.
 cudaError_t launch_binning(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st,
-                           bool prune = false);
+                           bool prune = false, bool defer_prune = false);
 cudaError_t launch_prune(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st);
 
 struct EstimateArgs {
