@@ -348,9 +348,9 @@ def run_ours(args):
             "batched_over_plain": plain_ms / (1000.0 * t_total / args.steps),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            # per iteration: 3 binning kernels, the vertex pass, the fast and the heavy-bin
-            # estimator, the background-loss kernel and the step kernel
-            "gpu_launches": 8 * args.steps,
+            # per iteration: 3 binning kernels, the pruning pass, the vertex pass, the fast and the
+            # heavy-bin estimator, the background-loss kernel and the step kernel
+            "gpu_launches": 9 * args.steps,
             "clocks": clocks}
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
@@ -442,7 +442,9 @@ def run_uneven(args):
                                   "autotune_ms": tune_ms}},
             "param_gradients_per_s": sum(contributions) * args.steps / t_total,
             "contributions_per_asset": contributions,
-            "gpu_launches": (5 * len(assets) + 2 + len(assets)) * args.steps,
+            # per asset: 3 binning kernels, background loss, vertex pass, Adam step; per call: the
+            # batched pruning pass, the fast and the heavy-bin estimator
+            "gpu_launches": (6 * len(assets) + 3) * args.steps,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
