@@ -91,7 +91,8 @@ typedef struct {
     float near_w;           /* a vertex needs clip w > near_w, else its triangle drops    */
     const float *targets;   /* device, [n_views][height][width][3] target images I        */
     float background[3];    /* colour of uncovered pixels                                 */
-    int32_t shading;        /* SGE_SHADE_*                                                */
+    int32_t shading;        /* SGE_SHADE_*; the textures must include the roles it reads:
+                               unlit albedo; Lambert albedo, normal; GGX all four        */
     float light_dir[3];     /* unit vector towards the light, world space                 */
     float light_rgb[3];
     float ambient;
@@ -230,7 +231,8 @@ typedef struct {
 int sge_estimate_grad_batch(const sge_batch_entry *entries, int32_t n_entries, uint64_t seed, uint32_t iter,
                             int32_t pairs_per_view, const sge_batch_tuning *tuning, sge_stream_t stream);
 
-/* Autotuner of sge_estimate_grad_batch's launch shape for these entries: times
+/* Autotuner of sge_estimate_grad_batch's launch shape (no counterpart in the paper,
+ * which runs one asset at a time) for these entries: times
  * candidate shapes (pairs per item 1..64, 1 or 2 CTAs per SM, light-bin limit
  * 64/128/256; a coordinate search from the defaults), each as one untimed call then
  * the mean of `repeats` calls (CUDA events on `stream`), and returns the fastest in
@@ -279,7 +281,8 @@ int sge_render_idb_static(const sge_scene_desc *desc, int32_t view, uint64_t see
 int sge_kernel_timing(sge_scene *scene, int32_t enable);
 int sge_kernel_time(sge_scene *scene, float *total_ms, float *heavy_ms, int32_t *launches);
 
-/* Work list of the scene's last estimate call (after its binning and pruning):
+/* Work list of the scene's last estimate call (after its binning and pruning; a
+ * diagnostic with no counterpart in the paper):
  * tiles x views taken by the fast kernel (light_items), by the heavy-bin kernel
  * (heavy_items) and the triangle-tile bin entries before pruning.  Synchronises
  * `stream`.  For tuning sge_batch_tuning.light_bin and for diagnostics. */

@@ -77,6 +77,15 @@ int check_desc(const sge_scene_desc* d) {
     if (t.role < SGE_ROLE_ALBEDO || t.role > SGE_ROLE_METALLIC) return fail(SGE_ERR_INVALID_ARG, "texture %d bad role", k);
     if (!(t.eps >= 0.0f) || !std::isfinite(t.eps)) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be finite and >= 0", k);
   }
+  // the shading model samples one texture of each role it reads: all must be present
+  const int need = d->shading == SGE_SHADE_UNLIT ? 1 : (d->shading == SGE_SHADE_LAMBERT ? 2 : 4);
+  static const int roles[4] = {SGE_ROLE_ALBEDO, SGE_ROLE_NORMAL, SGE_ROLE_ROUGHNESS, SGE_ROLE_METALLIC};
+  static const char* names[4] = {"albedo", "normal", "roughness", "metallic"};
+  for (int r = 0; r < need; ++r) {
+    bool found = false;
+    for (int k = 0; k < d->n_textures; ++k) found = found || d->textures[k].role == roles[r];
+    if (!found) return fail(SGE_ERR_INVALID_ARG, "shading model %d needs a texture of role %s", d->shading, names[r]);
+  }
   return SGE_OK;
 }
 

@@ -68,3 +68,27 @@ def test_no_cpu_fallback_without_gpu():
     with pytest.raises(RuntimeError):
         Scene(np.zeros((3, 3)), np.zeros((1, 3)), np.zeros((3, 2)), np.zeros((1, 3)), [], 1e-3,
               np.eye(4), np.zeros(3), 8, 8)
+
+
+def test_descriptor_checks_run_on_the_host():
+    """sge_workspace_size validates a scene description without touching a GPU: the textures
+    must include every role the shading model reads."""
+    import ctypes as C
+    from paper_2404_09758_gb300 import _abi
+    L = _abi.load(build_if_missing=True)
+    d = _abi.SceneDesc()
+    fake = 0x1000  # never dereferenced by the host checks
+    d.positions, d.n_vertices, d.eps_pos = fake, 3, 1e-3
+    d.pos_idx, d.n_triangles, d.uvs, d.n_uvs, d.uv_idx = fake, 1, fake, 3, fake
+    d.mvp, d.cam_pos, d.n_views, d.width, d.height, d.near_w, d.targets = fake, fake, 1, 32, 32, 0.1, fake
+    nbytes = C.c_size_t()
+    for shading, roles, ok in ((0, [0], True), (0, [], False), (1, [0], False), (1, [0, 1], True),
+                               (2, [0, 1, 2], False), (2, [0, 1, 2, 3], True)):
+        d.shading, d.n_textures = shading, len(roles)
+        for k, role in enumerate(roles):
+            d.textures[k].texels, d.textures[k].width, d.textures[k].height = fake, 4, 4
+            d.textures[k].channels, d.textures[k].eps, d.textures[k].role = 3, 1.0 / 255.0, role
+        rc = L.sge_workspace_size(C.byref(d), None, C.byref(nbytes))
+        assert (rc == _abi.OK) == ok, (shading, roles, L.sge_last_error())
+        if not ok:
+            assert rc == _abi.ERR_INVALID_ARG and b"role" in L.sge_last_error()
