@@ -39,13 +39,18 @@ constexpr int MAX_PROBE = 16;
 constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t NOSLOT = 0xFFFFu;
 
-template <int SH>
+// GR: the read textures share one size, so every pixel's bilinear footprint is the same texels
+// in all of them and one table entry (keyed by texel) carries all their channels.
+template <int SH, bool GR = false>
 struct Model {
   static constexpr int NREAD = SH == SHADE_UNLIT ? 1 : (SH == SHADE_LAMBERT ? 2 : 4);
-  // at about one texel per pixel a tile's bilinear footprints hold ~300 texels per read texture;
-  // the lit models (2 or 4 textures) run one CTA per SM (register-bound), so their tables can
-  // take the shared memory the second CTA of the unlit model would use
-  static constexpr int TABLE = SH == SHADE_UNLIT ? 512 : 2048;
+  // footprints computed and inserted per side: one for a group, one per texture otherwise
+  static constexpr int NFOOT = GR ? 1 : NREAD;
+  // at about one texel per pixel a tile's bilinear footprints hold ~300 texels per footprint;
+  // the lit models run one CTA per SM (register-bound), so their tables can take the shared
+  // memory the second CTA of the unlit model would use
+  static constexpr int TABLE = SH == SHADE_UNLIT ? 512 : (GR ? 1024 : 2048);
+  static constexpr int TSC = GR ? 4 * NREAD : 4;  // channel sums per table entry
 };
 
 // One side of a staged triangle (the unperturbed set-up also keeps its margin).
@@ -60,7 +65,7 @@ struct __align__(16) TriS {
   int pad[2];
 };
 
-template <int TABLE>
+template <int TABLE, int TSC>
 struct FastSmem {
   TriS side[2][NB];
   float uv[NB][6];
@@ -78,7 +83,7 @@ struct FastSmem {
   uint32_t tn[TABLE];
   uint32_t tstamp[TABLE];
   uint32_t tsb[2][TABLE];  // sign bits of the stamped pair, by pair parity
-  float tS[4][TABLE];
+  float tS[TSC][TABLE];
   uint32_t tcnt[TABLE];
   uint64_t pk[kMaxPairsPerItem];  // sign keys of the run's pairs
   float m[16];
@@ -132,9 +137,9 @@ __device__ __forceinline__ uint32_t hslot(uint32_t k, int table) {
 
 // Find or insert a texel key; the first pixel to touch the entry in this pair draws
 // the pair's signs of the texel's channels (stamp = pair + 1) into tsb[par].
-template <int TABLE>
-__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE>& sm, uint32_t key, uint32_t stamp,
-                                                 const TexDev& T, uint64_t pkey, int par) {
+template <int TABLE, int TSC, int NG>
+__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE, TSC>& sm, uint32_t key, uint32_t stamp,
+                                                 const SceneDev& S, const TexDev& T, uint64_t pkey, int par) {
   uint32_t slot = hslot(key, TABLE);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
@@ -145,9 +150,19 @@ __device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE>& sm, uint32_t k
     }
     if (k == key) {
       if (*(volatile uint32_t*)&sm.tstamp[slot] != stamp && atomicExch(&sm.tstamp[slot], stamp) != stamp) {
-        const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
         uint32_t sb = 0;
-        for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << c;
+        if (NG == 0) {
+          const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
+          for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << c;
+        } else {
+          // a group entry: the texel's channels of every read texture, at bit 4 r + c
+#pragma unroll
+          for (int r = 0; r < NG; ++r) {
+            const TexDev& U = S.rtex[r];
+            const long long base = U.offset + (long long)(key & 0x0FFFFFFFu) * U.c;
+            for (int c = 0; c < U.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << (4 * r + c);
+          }
+        }
         sm.tsb[par][slot] = sb;
       }
       return slot;
@@ -170,8 +185,8 @@ __device__ __forceinline__ long long texel_of(uint32_t pk, int q, int w) {
   return t;
 }
 
-template <int TABLE>
-__device__ __forceinline__ void clear_item_table(FastSmem<TABLE>& sm) {
+template <int TABLE, int TSC>
+__device__ __forceinline__ void clear_item_table(FastSmem<TABLE, TSC>& sm) {
   for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
     sm.tkey[s] = EMPTY;
     sm.tA[s] = 0.0f;
@@ -179,24 +194,31 @@ __device__ __forceinline__ void clear_item_table(FastSmem<TABLE>& sm) {
     sm.tstamp[s] = 0u;
     sm.tcnt[s] = 0u;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) sm.tS[c][s] = 0.0f;
+    for (int c = 0; c < TSC; ++c) sm.tS[c][s] = 0.0f;
   }
 }
 
 // Fold a pair's credits (table entries and triangle corners) into the per-channel sums with
 // that pair's signs (texel signs in tsb[parity], vertex signs in sgn9[parity]).
-template <int TABLE>
-__device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE>& sm, int nb, int parity) {
+template <int TABLE, int TSC>
+__device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE, TSC>& sm, int nb, int parity) {
   for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
     const uint32_t nn = sm.tn[s];
     if (!nn) continue;
     const uint32_t key = sm.tkey[s];
-    const int cn = S.tex[(key >> 28) - 1].c;
     const float A = sm.tA[s];
     const uint32_t sb = sm.tsb[parity][s];
+    if (TSC == 4) {
+      const int cn = S.tex[(key >> 28) - 1].c;
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      if (c < cn) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
+      for (int c = 0; c < 4; ++c)
+        if (c < cn) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
+    } else {
+      // group entry: channel c of read texture r at 4 r + c (unused channels stay 0)
+#pragma unroll
+      for (int c = 0; c < TSC; ++c)
+        if (c % 4 < S.rtex[c / 4].c) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
+    }
     sm.tcnt[s] += nn;
     sm.tA[s] = 0.0f;
     sm.tn[s] = 0u;
@@ -481,11 +503,14 @@ __global__ void __launch_bounds__(TILE_PX) k_bin_prune_batch(const BatchArgs P) 
 
 // Every light work item of one scene's call, taken one at a time from the scene's work
 // counter until none is left.
-template <int SH>
+template <int SH, bool GR>
 __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& ws, const ViewList& vl,
-                                           const EstimateArgs& a, FastSmem<Model<SH>::TABLE>& sm) {
-  constexpr int NREAD = Model<SH>::NREAD;
-  constexpr int TABLE = Model<SH>::TABLE;
+                                           const EstimateArgs& a,
+                                           FastSmem<Model<SH, GR>::TABLE, Model<SH, GR>::TSC>& sm) {
+  constexpr int NREAD = Model<SH, GR>::NREAD;
+  constexpr int NFOOT = Model<SH, GR>::NFOOT;
+  constexpr int TABLE = Model<SH, GR>::TABLE;
+  constexpr int TSC = Model<SH, GR>::TSC;
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
@@ -614,9 +639,9 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       // ---- U: UV buffer values and texel keys of both sides (footprints computed once)
       float2 uvs[2];
       float bary[2][3];
-      float ffx[2][NREAD], ffy[2][NREAD];
-      uint32_t tpk[2][NREAD];       // texel (x0,y0) id | 1<<30 if x1 wrapped | 1<<31 if y1 == y0
-      uint32_t tslot[2][NREAD][2];  // four 16-bit table slots per side and read texture
+      float ffx[2][NFOOT], ffy[2][NFOOT];
+      uint32_t tpk[2][NFOOT];       // texel (x0,y0) id | 1<<30 if x1 wrapped | 1<<31 if y1 == y0
+      uint32_t tslot[2][NFOOT][2];  // four 16-bit table slots per side and footprint
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         uvs[sd] = make_float2(0.f, 0.f);
@@ -635,7 +660,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           for (int k = 0; k < 3; ++k) bary[sd][k] = pw.q[k] / pw.qs;
         }
 #pragma unroll
-        for (int r = 0; r < NREAD; ++r) {
+        for (int r = 0; r < NFOOT; ++r) {
           const TexDev& T = S.rtex[r];
           const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
           ffx[sd][r] = f.fx;
@@ -650,7 +675,8 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           uint32_t sl[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            sl[q] = table_insert(sm, tkey(T.index, foot_texel(f, q, T.w)), (uint32_t)pair + 1, T, pkey, par);
+            sl[q] = table_insert<TABLE, TSC, GR ? NREAD : 0>(sm, tkey(T.index, foot_texel(f, q, T.w)),
+                                                             (uint32_t)pair + 1, S, T, pkey, par);
           tslot[sd][r][0] = sl[0] | (sl[1] << 16);
           tslot[sd][r][1] = sl[2] | (sl[3] << 16);
         }
@@ -667,18 +693,19 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
         for (int r = 0; r < NREAD; ++r) {
           const TexDev& T = S.rtex[r];
-          const float fx = ffx[sd][r], fy = ffy[sd][r];
+          const int fi = GR ? 0 : r;  // the footprint (and table entries) this texture uses
+          const float fx = ffx[sd][fi], fy = ffy[sd][fi];
           const float wq[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
 #pragma unroll
           for (int c = 0; c < 4; ++c) tex[r][c] = 0.0f;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-            const long long texel = texel_of(tpk[sd][r], q, T.w);
+            const uint32_t sl = (tslot[sd][fi][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+            const long long texel = texel_of(tpk[sd][fi], q, T.w);
             const float* src = T.ptr + texel * T.c;
             uint32_t sb;
             if (sl != NOSLOT) {
-              sb = sm.tsb[par][sl];
+              sb = sm.tsb[par][sl] >> (GR ? 4 * r : 0);
             } else {
               sb = 0;
               for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(T.offset + texel * T.c + c)) << c;
@@ -744,9 +771,9 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           atomicAdd(&sm.A_tri[bj[1]], df);
           atomicAdd(&sm.n_tri[bj[1]], 1u);
         }
-        // texels: union of both sides' footprints of every read texture
+        // texels: union of both sides' footprints of every read texture (of the group)
 #pragma unroll
-        for (int r = 0; r < NREAD; ++r) {
+        for (int r = 0; r < NFOOT; ++r) {
           const TexDev& T = S.rtex[r];
           const bool same = bj[0] >= 0 && bj[1] >= 0 && tpk[0][r] == tpk[1][r];
 #pragma unroll
@@ -770,10 +797,14 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
                 atomicAdd(&sm.tA[sl], df);
                 atomicAdd(&sm.tn[sl], 1u);
               } else {
-                const long long base = T.offset + (long long)ids[q] * T.c;
-                for (int c = 0; c < T.c; ++c) {
-                  atomicAdd(a.grad + base + c, sign_neg(pkey, (uint64_t)(base + c)) ? -df : df);
-                  atomicAdd(a.counts + base + c, 1u);
+#pragma unroll
+                for (int g = 0; g < (GR ? NREAD : 1); ++g) {
+                  const TexDev& U = S.rtex[GR ? g : r];
+                  const long long base = U.offset + (long long)ids[q] * U.c;
+                  for (int c = 0; c < U.c; ++c) {
+                    atomicAdd(a.grad + base + c, sign_neg(pkey, (uint64_t)(base + c)) ? -df : df);
+                    atomicAdd(a.counts + base + c, 1u);
+                  }
                 }
               }
             }
@@ -788,11 +819,24 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     for (int s = tid; s < TABLE; s += blockDim.x) {
       const uint32_t key = sm.tkey[s];
       if (key == EMPTY || sm.tcnt[s] == 0) continue;
-      const TexDev& T = S.tex[(key >> 28) - 1];
-      const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
-      for (int c = 0; c < T.c; ++c) {
-        atomicAdd(a.grad + base + c, sm.tS[c][s]);
-        atomicAdd(a.counts + base + c, sm.tcnt[s]);
+      if (!GR) {
+        const TexDev& T = S.tex[(key >> 28) - 1];
+        const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
+        for (int c = 0; c < T.c; ++c) {
+          atomicAdd(a.grad + base + c, sm.tS[c][s]);
+          atomicAdd(a.counts + base + c, sm.tcnt[s]);
+        }
+      } else {
+        // a group entry: the texel of every read texture, channel c of texture r at 4 r + c
+#pragma unroll
+        for (int r = 0; r < NREAD; ++r) {
+          const TexDev& T = S.rtex[r];
+          const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
+          for (int c = 0; c < T.c; ++c) {
+            atomicAdd(a.grad + base + c, sm.tS[(4 * r + c) % TSC][s]);
+            atomicAdd(a.counts + base + c, sm.tcnt[s]);
+          }
+        }
       }
     }
     if (tid < nb) {
@@ -823,36 +867,38 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
   }
 }
 
-template <int SH>
+template <int SH, bool GR>
 __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1)
     k_estimate_fast(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  fast_items<SH>(S, ws, vl, a, *reinterpret_cast<FastSmem<Model<SH>::TABLE>*>(smem_raw));
+  fast_items<SH, GR>(S, ws, vl, a,
+                     *reinterpret_cast<FastSmem<Model<SH, GR>::TABLE, Model<SH, GR>::TSC>*>(smem_raw));
 }
 
-// The batched kernel keeps its asset after FastSmem, 16-byte aligned.
+// The batched kernel keeps its asset after FastSmem, 16-byte aligned.  (Batched calls use the
+// per-texture table: their assets need not share texture sizes.)
 template <int SH>
 __host__ __device__ constexpr size_t fast_batch_off() {
-  return (sizeof(FastSmem<Model<SH>::TABLE>) + 15) & ~(size_t)15;
+  return (sizeof(FastSmem<Model<SH>::TABLE, Model<SH>::TSC>) + 15) & ~(size_t)15;
 }
 
 // Batched form: the assets of P in order, each until its light items run out.
 template <int SH>
 __global__ void __launch_bounds__(TILE_PX, SH == SHADE_UNLIT ? 2 : 1) k_estimate_fast_batch(const BatchArgs P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto& sm = *reinterpret_cast<FastSmem<Model<SH>::TABLE>*>(smem_raw);
+  auto& sm = *reinterpret_cast<FastSmem<Model<SH>::TABLE, Model<SH>::TSC>*>(smem_raw);
   BatchSmem& b = *reinterpret_cast<BatchSmem*>(smem_raw + fast_batch_off<SH>());
   for (int ai = 0; ai < P.n; ++ai) {
     __syncthreads();
     load_asset(P, ai, b);
     __syncthreads();
-    fast_items<SH>(b.d.S, b.d.ws, b.vl, b.a, sm);
+    fast_items<SH, false>(b.d.S, b.d.ws, b.vl, b.a, sm);
   }
 }
 
-template <int SH>
+template <int SH, bool GR>
 size_t fast_smem() {
-  return sizeof(FastSmem<Model<SH>::TABLE>);
+  return sizeof(FastSmem<Model<SH, GR>::TABLE, Model<SH, GR>::TSC>);
 }
 
 template <int SH>
@@ -878,21 +924,22 @@ int fast_batch_blocks_per_sm_t() {
   return n > 0 ? n : 1;
 }
 
-template <int SH>
+template <int SH, bool GR>
 cudaError_t launch_fast_t(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                           int grid, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_estimate_fast<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)fast_smem<SH>());
+  cudaError_t e = cudaFuncSetAttribute(k_estimate_fast<SH, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fast_smem<SH, GR>());
   if (e != cudaSuccess) return e;
-  k_estimate_fast<SH><<<grid, TILE_PX, fast_smem<SH>(), st>>>(S, ws, vl, a);
+  k_estimate_fast<SH, GR><<<grid, TILE_PX, fast_smem<SH, GR>(), st>>>(S, ws, vl, a);
   return cudaGetLastError();
 }
 
-template <int SH>
+template <int SH, bool GR>
 int fast_blocks_per_sm_t() {
   int n = 0;
-  cudaFuncSetAttribute(k_estimate_fast<SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fast_smem<SH>());
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_fast<SH>, TILE_PX, fast_smem<SH>());
+  cudaFuncSetAttribute(k_estimate_fast<SH, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)fast_smem<SH, GR>());
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_fast<SH, GR>, TILE_PX, fast_smem<SH, GR>());
   return n > 0 ? n : 1;
 }
 
@@ -900,9 +947,12 @@ int fast_blocks_per_sm_t() {
 
 cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a, int grid,
                         cudaStream_t st) {
-  if (S.shading == SHADE_UNLIT) return launch_fast_t<SHADE_UNLIT>(S, ws, vl, a, grid, st);
-  if (S.shading == SHADE_LAMBERT) return launch_fast_t<SHADE_LAMBERT>(S, ws, vl, a, grid, st);
-  return launch_fast_t<SHADE_GGX>(S, ws, vl, a, grid, st);
+  if (S.shading == SHADE_UNLIT) return launch_fast_t<SHADE_UNLIT, false>(S, ws, vl, a, grid, st);
+  if (S.shading == SHADE_LAMBERT)
+    return S.grouped ? launch_fast_t<SHADE_LAMBERT, true>(S, ws, vl, a, grid, st)
+                     : launch_fast_t<SHADE_LAMBERT, false>(S, ws, vl, a, grid, st);
+  return S.grouped ? launch_fast_t<SHADE_GGX, true>(S, ws, vl, a, grid, st)
+                   : launch_fast_t<SHADE_GGX, false>(S, ws, vl, a, grid, st);
 }
 
 cudaError_t launch_prune(const SceneDev& S, const Workspace& ws, const ViewList& vl, cudaStream_t st) {
@@ -928,9 +978,9 @@ int fast_batch_blocks_per_sm(int shading) {
 }
 
 int fast_blocks_per_sm(int shading) {
-  if (shading == SHADE_UNLIT) return fast_blocks_per_sm_t<SHADE_UNLIT>();
-  if (shading == SHADE_LAMBERT) return fast_blocks_per_sm_t<SHADE_LAMBERT>();
-  return fast_blocks_per_sm_t<SHADE_GGX>();
+  if (shading == SHADE_UNLIT) return fast_blocks_per_sm_t<SHADE_UNLIT, false>();
+  if (shading == SHADE_LAMBERT) return fast_blocks_per_sm_t<SHADE_LAMBERT, false>();
+  return fast_blocks_per_sm_t<SHADE_GGX, false>();
 }
 
 }  // namespace sge

@@ -159,6 +159,9 @@ void make_dev(const sge_scene_desc* d, SceneDev& S) {
     if (read) S.read_k[S.nread++] = k;
   }
   for (int r = 0; r < S.nread; ++r) S.rtex[r] = S.tex[S.read_k[r]];
+  S.grouped = S.nread > 1;
+  for (int r = 1; r < S.nread; ++r)
+    if (S.rtex[r].w != S.rtex[0].w || S.rtex[r].h != S.rtex[0].h) S.grouped = 0;
   S.mvp = d->mvp;
   S.cam_pos = d->cam_pos;
   S.nviews = d->n_views;

@@ -46,6 +46,7 @@ struct SceneDev {
   int nread;                 // textures the shading model reads (at most one per role)
   int read_k[MAX_READ];      // their indices in tex[]
   TexDev rtex[MAX_READ];     // copies of tex[read_k[r]], so kernels index them with constants
+  int grouped;               // > 1 read textures, all of one size: one footprint serves them all
   const float* mvp;
   const float* cam_pos;
   int nviews;

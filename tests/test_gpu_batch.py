@@ -106,6 +106,38 @@ def test_batch_equals_single_scene_calls(small):
         assert torch.allclose(loss, bufs[k][2], rtol=1e-5)
 
 
+def test_lit_batch_matches_oracle():
+    """Two Lambert assets (one with textures of one size, one with albedo and normal map of
+    different sizes) in one batched call: the lit estimator kernels of the batched form."""
+    import dataclasses
+    import torch
+    from paper_2404_09758_gb300 import Batch
+    a = synth.config_autograd(n_views=2, pairs=2, render=96, tex=64)
+    nrm = synth.Texture(synth.flat_normal_texture(32, 32), a.textures[1].eps, synth.ROLE_NORMAL)
+    b = dataclasses.replace(a, textures=[a.textures[0], nrm],
+                            target_textures=[a.target_textures[0], synth.normal_map_texture(32, 32, seed=6)])
+    scs = [a, b]
+    targets = [oracle.render_targets(sc, synth.target_scene(sc)) for sc in scs]
+    views = [[0, 1], [1]]
+    gs, bufs, entries = [], [], []
+    for sc, tg, vw in zip(scs, targets, views):
+        g = gpu_scene(sc, tg)
+        grad, counts = g.new_grad_buffers()
+        loss = torch.zeros(len(vw), device=g.device)
+        gs.append(g)
+        bufs.append((grad, counts, loss))
+        entries.append((g, vw, grad, counts, loss))
+    Batch(entries).estimate_grad(SEED, ITER, 2)
+    sts = [g.status() for g in gs]
+    torch.cuda.synchronize()
+    for k, (sc, tg, vw) in enumerate(zip(scs, targets, views)):
+        S, Cn, oloss = oracle.estimate(oracle.OracleScene(sc, tg), SEED, ITER, vw, 2)
+        grad, counts, loss = bufs[k]
+        assert_parity(sc, dict(status=sts[k], grad=grad.cpu().numpy().astype(np.float64),
+                               counts=counts.cpu().numpy().astype(np.int64).astype(np.uint64),
+                               loss=loss.cpu().numpy().astype(np.float64), S=S, C=Cn, oloss=oloss))
+
+
 def test_batch_rejects_bad_entries(small):
     import torch
     from paper_2404_09758_gb300 import Batch, SGEError

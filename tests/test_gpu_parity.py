@@ -33,6 +33,15 @@ def _lambert_small():
     return synth.config_autograd(n_views=2, pairs=2, render=96, tex=64)
 
 
+def _lambert_mixed_sizes():
+    """Albedo 64^2 RGBA and normal map 32^2: footprints differ per texture (no texel groups)."""
+    import dataclasses
+    sc = synth.config_autograd(n_views=2, pairs=2, render=96, tex=64)
+    nrm = synth.Texture(synth.flat_normal_texture(32, 32), sc.textures[1].eps, synth.ROLE_NORMAL)
+    return dataclasses.replace(sc, textures=[sc.textures[0], nrm],
+                               target_textures=[sc.target_textures[0], synth.normal_map_texture(32, 32, seed=6)])
+
+
 def _ggx_small():
     return synth.config_scale(n_views=2, pairs=2, render=96, tex=64, n_lon=64, n_lat=32)
 
@@ -95,6 +104,7 @@ ESTIMATE_CASES = {
                                [2, 0, 1], 5, {"pairs_per_item": 2}),
     "sphere8k_128": (lambda: _sphere(64, 64, 512, 128, 128, synth.random_eyes(4, 2)), [0, 1, 2, 3], 4, {}),
     "lambert_subdiv": (_lambert_small, [0, 1], 2, {}),
+    "lambert_mixed_sizes": (_lambert_mixed_sizes, [1, 0], 2, {}),
     "ggx_grid": (_ggx_small, [1, 0], 2, {"pairs_per_item": 1}),
     # 32K triangles at 48x48: bins far above the fast path's limit (the general kernel)
     "dense_heavy_bins": (lambda: _sphere(128, 128, 64, 48, 48, synth.random_eyes(2, 5), True), [0, 1], 3, {}),
