@@ -42,19 +42,19 @@ struct SideSmem {
   int tri[BIN_CHUNK];  // -1 when not drawn on this side
 };
 
-template <int HT>
+template <int HT, int TSC>
 struct TableSmem {
   uint32_t key[HT];
   float A[HT];
   uint32_t n[HT];
-  float S[4][HT];
+  float S[TSC][HT];  // channel sums: 4 per texture (4 x 4 for a texel group key)
   uint32_t cnt[HT];
 };
 
-template <int HT>
+template <int HT, int TSC>
 struct Smem {
   SideSmem side[2];
-  TableSmem<HT> tab;
+  TableSmem<HT, TSC> tab;
   float m[16];
   float red[TILE_PX / 32];
   uint32_t item;
@@ -123,9 +123,9 @@ __device__ __forceinline__ uint32_t slot_hash(uint32_t k) {
 }
 
 // Credit df to key: shared-memory table, or global atomics when the table is full.
-template <int HT>
-__device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT>& tb, uint32_t key, float df, uint64_t pkey,
-                                       float* grad, uint32_t* counts) {
+template <int HT, int TSC, bool GR>
+__device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT, TSC>& tb, uint32_t key, float df,
+                                       uint64_t pkey, float* grad, uint32_t* counts) {
   uint32_t slot = slot_hash<HT>(key);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
@@ -138,55 +138,46 @@ __device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT>& tb, uin
     }
     slot = (slot + 1) & (HT - 1);
   }
-  long long base;
-  int nch;
-  key_params(S, key, base, nch);
-  for (int c = 0; c < nch; ++c) {
-    bool neg = sign_neg(pkey, (uint64_t)(base + c));
-    atomicAdd(grad + base + c, neg ? -df : df);
-    atomicAdd(counts + base + c, 1u);
-  }
+  for_each_channel<GR>(S, key, [&](long long p, int) {
+    atomicAdd(grad + p, sign_neg(pkey, (uint64_t)p) ? -df : df);
+    atomicAdd(counts + p, 1u);
+  });
 }
 
 // Fold the pair's per-key sums into the per-channel accumulators (signs of this pair).
-template <int HT>
-__device__ __forceinline__ void fold(const SceneDev& S, TableSmem<HT>& tb, uint64_t pkey) {
+template <int HT, int TSC, bool GR>
+__device__ __forceinline__ void fold(const SceneDev& S, TableSmem<HT, TSC>& tb, uint64_t pkey) {
   for (int slot = threadIdx.x; slot < HT; slot += blockDim.x) {
     uint32_t key = tb.key[slot];
     if (key == EMPTY) continue;
     uint32_t nn = tb.n[slot];
     if (nn == 0) continue;
     float A = tb.A[slot];
-    long long base;
-    int nch;
-    key_params(S, key, base, nch);
-    for (int c = 0; c < nch; ++c) tb.S[c][slot] += sign_neg(pkey, (uint64_t)(base + c)) ? -A : A;
+    for_each_channel<GR>(S, key, [&](long long p, int c) { tb.S[c][slot] += sign_neg(pkey, (uint64_t)p) ? -A : A; });
     tb.cnt[slot] += nn;
     tb.A[slot] = 0.0f;
     tb.n[slot] = 0u;
   }
 }
 
-template <int HT>
-__device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem<HT>& tb, float* grad, uint32_t* counts) {
+template <int HT, int TSC, bool GR>
+__device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem<HT, TSC>& tb, float* grad,
+                                                uint32_t* counts) {
   for (int slot = threadIdx.x; slot < HT; slot += blockDim.x) {
     uint32_t key = tb.key[slot];
     if (key != EMPTY) {
-      long long base;
-      int nch;
-      key_params(S, key, base, nch);
-      uint32_t cn = tb.cnt[slot];
-      for (int c = 0; c < nch; ++c) {
-        atomicAdd(grad + base + c, tb.S[c][slot]);
-        if (cn) atomicAdd(counts + base + c, cn);
-      }
+      const uint32_t cn = tb.cnt[slot];
+      for_each_channel<GR>(S, key, [&](long long p, int c) {
+        atomicAdd(grad + p, tb.S[c][slot]);
+        if (cn) atomicAdd(counts + p, cn);
+      });
     }
     tb.key[slot] = EMPTY;
     tb.A[slot] = 0.0f;
     tb.n[slot] = 0u;
     tb.cnt[slot] = 0u;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) tb.S[c][slot] = 0.0f;
+    for (int c = 0; c < TSC; ++c) tb.S[c][slot] = 0.0f;
   }
 }
 
@@ -208,27 +199,27 @@ __device__ __forceinline__ void setup_from_pverts(const SceneDev& S, const Works
 }
 
 // the batched kernels keep their asset after the kernel's own shared memory, 16-byte aligned
-template <int HT>
+template <int HT, int TSC>
 constexpr size_t heavy_batch_off() {
-  return (sizeof(Smem<HT>) + 15) & ~(size_t)15;
+  return (sizeof(Smem<HT, TSC>) + 15) & ~(size_t)15;
 }
 
-template <int HT>
-__device__ __forceinline__ void clear_table(TableSmem<HT>& tb) {
+template <int HT, int TSC>
+__device__ __forceinline__ void clear_table(TableSmem<HT, TSC>& tb) {
   for (int s = threadIdx.x; s < HT; s += blockDim.x) {
     tb.key[s] = EMPTY;
     tb.A[s] = 0.0f;
     tb.n[s] = 0u;
     tb.cnt[s] = 0u;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) tb.S[c][s] = 0.0f;
+    for (int c = 0; c < TSC; ++c) tb.S[c][s] = 0.0f;
   }
 }
 
 // Every heavy work item of one scene's call (the table starts and ends each item empty).
-template <int HT>
+template <int HT, int TSC, bool GR>
 __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& ws, const ViewList& vl,
-                                            const EstimateArgs& a, Smem<HT>& sm) {
+                                            const EstimateArgs& a, Smem<HT, TSC>& sm) {
   const int tid = threadIdx.x;
   const int dx = tid % TILE, dy = tid / TILE;
   const int ntl = n_tiles(S);
@@ -354,13 +345,14 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
         for (int sd = 0; sd < 2; ++sd)
 #pragma unroll
           for (int r = 0; r < MAX_READ; ++r) foot[sd][r] = sf[sd].foot[r];
-        for_each_contrib(S, tris, foot, [&](uint32_t key) { credit(S, sm.tab, key, df, pkey, a.grad, a.counts); });
+        for_each_contrib<GR>(S, tris, foot,
+                             [&](uint32_t key) { credit<HT, TSC, GR>(S, sm.tab, key, df, pkey, a.grad, a.counts); });
       }
       __syncthreads();
-      fold(S, sm.tab, pkey);
+      fold<HT, TSC, GR>(S, sm.tab, pkey);
     }
     __syncthreads();
-    flush_and_clear(S, sm.tab, a.grad, a.counts);
+    flush_and_clear<HT, TSC, GR>(S, sm.tab, a.grad, a.counts);
     if (a.loss) {
       float v = loss_acc;
 #pragma unroll
@@ -376,26 +368,27 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
   }
 }
 
-template <int HT>
+template <int HT, int TSC, bool GR>
 __global__ void __launch_bounds__(TILE_PX) k_estimate_heavy(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<HT>& sm = *reinterpret_cast<Smem<HT>*>(smem_raw);
+  Smem<HT, TSC>& sm = *reinterpret_cast<Smem<HT, TSC>*>(smem_raw);
   clear_table(sm.tab);
-  heavy_items<HT>(S, ws, vl, a, sm);
+  heavy_items<HT, TSC, GR>(S, ws, vl, a, sm);
 }
 
-// Batched form: the assets of P in order, each until its heavy items run out.
+// Batched form: the assets of P in order, each until its heavy items run out (per-texture keys:
+// the assets need not share texture sizes).
 template <int HT>
 __global__ void __launch_bounds__(TILE_PX) k_estimate_heavy_batch(const BatchArgs P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<HT>& sm = *reinterpret_cast<Smem<HT>*>(smem_raw);
-  BatchSmem& b = *reinterpret_cast<BatchSmem*>(smem_raw + heavy_batch_off<HT>());
+  Smem<HT, 4>& sm = *reinterpret_cast<Smem<HT, 4>*>(smem_raw);
+  BatchSmem& b = *reinterpret_cast<BatchSmem*>(smem_raw + heavy_batch_off<HT, 4>());
   clear_table(sm.tab);
   for (int ai = 0; ai < P.n; ++ai) {
     __syncthreads();
     load_asset(P, ai, b);
     __syncthreads();
-    heavy_items<HT>(b.d.S, b.d.ws, b.vl, b.a, sm);
+    heavy_items<HT, 4, false>(b.d.S, b.d.ws, b.vl, b.a, sm);
   }
 }
 
@@ -427,30 +420,37 @@ __global__ void k_background_loss(SceneDev S, Workspace ws, ViewList vl, float* 
   if ((threadIdx.x & 31) == 0 && v != 0.0f) atomicAdd(loss + slot, v);
 }
 
-template <int HT>
-int heavy_blocks_t(bool batch) {
+template <int HT, int TSC, bool GR>
+int heavy_blocks_t() {
   int n = 0;
-  if (batch) {
-    const int bytes = (int)(heavy_batch_off<HT>() + sizeof(BatchSmem));
-    cudaFuncSetAttribute(k_estimate_heavy_batch<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy_batch<HT>, TILE_PX, bytes);
-  } else {
-    cudaFuncSetAttribute(k_estimate_heavy<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<HT>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy<HT>, TILE_PX, sizeof(Smem<HT>));
-  }
+  cudaFuncSetAttribute(k_estimate_heavy<HT, TSC, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(Smem<HT, TSC>));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy<HT, TSC, GR>, TILE_PX, sizeof(Smem<HT, TSC>));
   return n > 0 ? n : 1;
 }
 
-constexpr int kHtUnlit = HeavyTable<0>::SLOTS, kHtLit = HeavyTable<1>::SLOTS;
+template <int HT>
+int heavy_batch_blocks_t() {
+  int n = 0;
+  const int bytes = (int)(heavy_batch_off<HT, 4>() + sizeof(BatchSmem));
+  cudaFuncSetAttribute(k_estimate_heavy_batch<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_estimate_heavy_batch<HT>, TILE_PX, bytes);
+  return n > 0 ? n : 1;
+}
+
+// Table shapes: unlit 2,048 slots; lit 4,096 slots with per-texture keys, or 2,048 slots of
+// texel-group keys (16 channel sums each) when the read textures share one size.
+constexpr int kHtUnlit = HeavyTable<0>::SLOTS, kHtLit = HeavyTable<1>::SLOTS, kHtGroup = 2048;
 
 }  // namespace
 
-int estimate_blocks_per_sm(int shading) {
-  return shading == SHADE_UNLIT ? heavy_blocks_t<kHtUnlit>(false) : heavy_blocks_t<kHtLit>(false);
+int estimate_blocks_per_sm(int shading, int grouped) {
+  if (shading == SHADE_UNLIT) return heavy_blocks_t<kHtUnlit, 4, false>();
+  return grouped ? heavy_blocks_t<kHtGroup, 16, true>() : heavy_blocks_t<kHtLit, 4, false>();
 }
 
 int heavy_batch_blocks_per_sm(int shading) {
-  return shading == SHADE_UNLIT ? heavy_blocks_t<kHtUnlit>(true) : heavy_blocks_t<kHtLit>(true);
+  return shading == SHADE_UNLIT ? heavy_batch_blocks_t<kHtUnlit>() : heavy_batch_blocks_t<kHtLit>();
 }
 
 cudaError_t launch_put_desc(const AssetDesc& d, AssetDesc* dst, cudaStream_t st) {
@@ -462,20 +462,20 @@ namespace {
 
 template <int HT>
 cudaError_t launch_heavy_batch_t(const BatchArgs& P, int grid, cudaStream_t st) {
-  const int bytes = (int)(heavy_batch_off<HT>() + sizeof(BatchSmem));
+  const int bytes = (int)(heavy_batch_off<HT, 4>() + sizeof(BatchSmem));
   cudaError_t e = cudaFuncSetAttribute(k_estimate_heavy_batch<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   k_estimate_heavy_batch<HT><<<grid, TILE_PX, bytes, st>>>(P);
   return cudaGetLastError();
 }
 
-template <int HT>
+template <int HT, int TSC, bool GR>
 cudaError_t launch_heavy_t(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                            int grid, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_estimate_heavy<HT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(Smem<HT>));
+  cudaError_t e = cudaFuncSetAttribute(k_estimate_heavy<HT, TSC, GR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(Smem<HT, TSC>));
   if (e != cudaSuccess) return e;
-  k_estimate_heavy<HT><<<grid, TILE_PX, sizeof(Smem<HT>), st>>>(S, ws, vl, a);
+  k_estimate_heavy<HT, TSC, GR><<<grid, TILE_PX, sizeof(Smem<HT, TSC>), st>>>(S, ws, vl, a);
   return cudaGetLastError();
 }
 
@@ -491,8 +491,9 @@ cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewLi
   if (e == cudaSuccess) e = launch_fast(S, ws, vl, a, grid_fast, st);
   if (e == cudaSuccess && ev_fast) e = cudaEventRecord(ev_fast[1], st);
   if (e != cudaSuccess) return e;
-  e = S.shading == SHADE_UNLIT ? launch_heavy_t<kHtUnlit>(S, ws, vl, a, grid_heavy, st)
-                               : launch_heavy_t<kHtLit>(S, ws, vl, a, grid_heavy, st);
+  if (S.shading == SHADE_UNLIT) e = launch_heavy_t<kHtUnlit, 4, false>(S, ws, vl, a, grid_heavy, st);
+  else if (S.grouped) e = launch_heavy_t<kHtGroup, 16, true>(S, ws, vl, a, grid_heavy, st);
+  else e = launch_heavy_t<kHtLit, 4, false>(S, ws, vl, a, grid_heavy, st);
   if (e == cudaSuccess && ev_fast) e = cudaEventRecord(ev_fast[2], st);
   if (e != cudaSuccess) return e;
   if (a.loss && a.pair_begin == 0) k_background_loss<<<dim3(n_tiles(S), vl.n), TILE_PX, 0, st>>>(S, ws, vl, a.loss);

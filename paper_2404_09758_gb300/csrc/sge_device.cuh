@@ -375,6 +375,32 @@ __device__ __forceinline__ bool cover(const Tri& t, int dx, int dy, long long e[
 __device__ __forceinline__ uint32_t vkey(int v) { return (uint32_t)v; }
 __device__ __forceinline__ uint32_t tkey(int k, int texel) { return ((uint32_t)(k + 1) << 28) | (uint32_t)texel; }
 
+// Every parameter channel of a contributor key: f(parameter index, its channel slot in a table
+// entry).  Vertex keys: x, y, z; texel keys: the texture's channels, or with GR (a group key of
+// for_each_contrib<true>) channel c of every read texture r, at slot 4 r + c.
+template <bool GR, typename F>
+__device__ __forceinline__ void for_each_channel(const SceneDev& S, uint32_t key, F&& f) {
+  const uint32_t kind = key >> 28, idx = key & 0x0FFFFFFFu;
+  if (kind == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f(3ll * idx + c, c);
+    return;
+  }
+  if constexpr (GR) {
+#pragma unroll
+    for (int r = 0; r < MAX_READ; ++r) {
+      if (r >= S.nread) break;
+      const TexDev& T = S.rtex[r];
+      const long long base = T.offset + (long long)idx * T.c;
+      for (int c = 0; c < T.c; ++c) f(base + c, 4 * r + c);
+    }
+  } else {
+    const TexDev& T = S.tex[kind - 1];
+    const long long base = T.offset + (long long)idx * T.c;
+    for (int c = 0; c < T.c; ++c) f(base + c, c);
+  }
+}
+
 __device__ __forceinline__ void key_params(const SceneDev& S, uint32_t key, long long& base, int& nch) {
   uint32_t kind = key >> 28, idx = key & 0x0FFFFFFFu;
   if (kind == 0) {
@@ -391,7 +417,7 @@ __device__ __forceinline__ void key_params(const SceneDev& S, uint32_t key, long
 // both sides (tris[0] = side +, tris[1] = side -, -1 = background) of the visible
 // triangle's three welded vertices and the bilinear 2x2 footprint of each read
 // texture.  foot[sd][r] is side sd's footprint of the r-th read texture.
-template <class F>
+template <bool GR = false, typename F>
 __device__ __forceinline__ void for_each_contrib(const SceneDev& S, const int tris[2],
                                                  const Foot (&foot)[2][MAX_READ], F&& f) {
   int vid[2][3];
@@ -408,7 +434,7 @@ __device__ __forceinline__ void for_each_contrib(const SceneDev& S, const int tr
     }
   }
 #pragma unroll
-  for (int r = 0; r < MAX_READ; ++r) {
+  for (int r = 0; r < (GR ? 1 : MAX_READ); ++r) {
     if (r >= S.nread) break;
     const int k = S.read_k[r];
     const int tw = S.tex[k].w;

@@ -161,7 +161,7 @@ cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& 
 // Perturbed, projected vertices of both sides for every (view slot, pair) of a block of pairs.
 cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                                cudaStream_t st);
-int estimate_blocks_per_sm(int shading);
+int estimate_blocks_per_sm(int shading, int grouped);
 int fast_blocks_per_sm(int shading);
 
 // Batched form of the two estimator kernels over BatchArgs' assets.
