@@ -42,7 +42,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # per warp / pixel pairs), and its DRAM traffic per launch, both from the ncu capture summarised
 # in profiles/k_estimate_fast_sphere8k_r512.md (same kernel source).
 ALU_INSTR_PER_PIXEL_PAIR = 1067.0
-DRAM_BYTES_PER_LAUNCH = 125.22e6
+DRAM_BYTES_PER_LAUNCH = 125.52e6
 
 
 def dist_env():
