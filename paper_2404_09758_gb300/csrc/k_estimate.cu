@@ -1,21 +1,24 @@
-// Fused, batched estimator: every estimate of one iteration (views x antithetic
-// pairs) in one persistent launch (Eq. 9, Algorithms 1-2, Section 4.3).
+// Fused, batched estimator for the tiles the fast kernel (k_fast.cu) cannot hold: more than
+// kLightBin live triangles (dense meshes, poles, silhouettes seen edge-on).  With the fast kernel
+// it runs every estimate of one iteration (views x antithetic pairs) in one persistent launch
+// (Eq. 9, Algorithms 1-2, Section 4.3).
 //
 // Work item = (view, 16x16 tile, run of pairs).  A CTA owns one item at a time,
 // one thread per pixel, and for every pair of its run:
-//   P+R  perturbs and sets up, in shared memory, both sides' versions of the
-//        triangles binned to the tile (signs recomputed from the hash; nothing
-//        perturbed is ever stored in global memory), then each thread finds its
-//        pixel's visible triangle on both sides (64-bit depth|id minimum);
+//   P+R  sets up, in shared memory and a chunk of 256 at a time, both sides' versions of the
+//        tile's live triangles from the vertex pass's projected perturbed vertices (nothing
+//        perturbed is stored per pixel), and each thread tests its pixel's candidates (up to
+//        kHeavyCand, listed by the pruning pass; more: every live triangle) for the visible
+//        triangle on both sides (64-bit depth|id minimum);
 //   G    shades both sides (UV buffer value, bilinear texels), forms
 //        f+ - f- = sum_c (I+_c - I-_c)(I+_c + I-_c - 2 I_c) and credits it to the
 //        union of both sides' contributing parameters.
-// Credits go to a shared-memory hash table keyed by vertex / texel.  Within a
-// pair all channels of a key share f+ - f- (only the sign s_i differs), so the
-// table accumulates A_key = sum_p (f+ - f-) and n_key per pair, and once per pair
-// folds s_i * A_key into per-channel sums.  At the end of the item each key
-// issues one global atomic per channel for the sum and the count.  A table that
-// fills up falls back to direct global atomics for the keys that do not fit.
+// Credits go to a shared-memory hash table keyed by vertex / texel (one key per texel for all
+// read textures when they share one size).  Within a pair all channels of a key share f+ - f-
+// (only the sign s_i differs), so the table accumulates A_key = sum_p (f+ - f-) and n_key per
+// pair, and once per pair folds s_i * A_key into per-channel sums.  At the end of the item each
+// key issues one global atomic per channel for the sum and the count.  A table that fills up
+// falls back to direct global atomics for the keys that do not fit.
 #include <cuda_runtime.h>
 
 #include "sge_device.cuh"

@@ -1,24 +1,27 @@
-// Batched estimator, fast path: tiles whose bin holds at most kLightBin triangles.
+// Batched estimator, fast path: tiles that keep at most kLightBin live triangles after pruning,
+// and the pruning pass itself.
+//
+// Once per call and (view, tile), k_bin_prune: the bin's triangles are set up unperturbed; a
+// triangle stays live if some pixel of the tile may see it under SOME perturbation of the call
+// (each edge function pushed out by the triangle's margin: the support of the box every snapped
+// perturbed vertex stays in) and it is not surely behind a triangle that surely covers the pixel
+// (farther than the largest vertex move from each of its edges, so every perturbed version still
+// covers it, and depth intervals apart).  Live triangles are compacted to the front of the bin;
+// each pixel's candidates among them (at most CMAX; more: test them all) are stored, so that a
+// pair tests a handful of triangles, not the bin.
 //
 // Work item = (view, 16x16 tile, run of antithetic pairs); one CTA thread per pixel.
-// Per item, once:
-//   the bin's triangles are set up unperturbed; every pixel keeps the (at most
-//   CMAX) triangles that can cover it under ANY perturbation of the call (each
-//   edge function pushed out by the triangle's margin: the support of the box
-//   every snapped perturbed vertex stays in), minus those surely behind a
-//   triangle that surely covers it (farther than the largest vertex move from
-//   each of its edges, so every perturbed version still covers it, and depth
-//   intervals apart); a pair then tests a handful of triangles, not the bin.
 // Per pair (Eq. 8 for one sign vector s, Algorithms 1-2):
 //   F+S the previous pair's credits are folded into per-channel sums with that
-//       pair's signs; the bin's triangles are set up on both sides (theta + s eps,
+//       pair's signs; the live triangles are set up on both sides (theta + s eps,
 //       theta - s eps) in shared memory from the projected perturbed vertices of
 //       the vertex pass (k_vertex.cu), with their 9 coordinate signs;
 //   R   each pixel finds its visible triangle on both sides among its candidates
 //       (smallest packed depth|id key);
 //   U   it computes both sides' UV and inserts the texels of their bilinear
-//       footprints into a shared-memory table; the first pixel to touch a texel in
-//       the pair draws the pair's signs of its channels;
+//       footprints into a shared-memory table (one key per texel for all read textures
+//       when they share one size); the first pixel to touch a texel in the pair draws
+//       the pair's signs of its channels;
 //   G   it samples its perturbed texels (signs from the table), shades both sides,
 //       forms f+ - f- and credits it: the visible triangle (all three vertices at
 //       once, or single corners where the sides disagree) and the union of the
