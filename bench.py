@@ -50,6 +50,20 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def job_throughput(seconds: float, units_per_rank: float, device=None):
+    """Whole-job rate of independent replicas: every rank processed units_per_rank in its own
+    `seconds`; the job took the slowest rank's time (max over ranks, one all-reduce on the
+    process group when there is one), and processed world x units_per_rank."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    if world > 1:
+        t = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return world * units_per_rank / seconds, seconds
+
+
 def make_scene():
     import synth
     return synth.config_batched(n_views=N_VIEWS, pairs=PAIRS, render=RENDER)
@@ -251,13 +265,8 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(ms) / 1000.0
-    if world > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
     px_per_step = N_VIEWS * PAIRS * RENDER * RENDER
-    value = world * px_per_step * args.steps / t_total
+    value, t_total = job_throughput(sum(ms) / 1000.0, px_per_step * args.steps, device=dev)
     assert g.status(st) == 0
 
     # dominant kernel: the library records CUDA events on `st` around each launch of the fast
