@@ -289,6 +289,14 @@ int sge_kernel_time(sge_scene *scene, float *total_ms, float *heavy_ms, int32_t 
 int sge_bin_stats(sge_scene *scene, sge_stream_t stream, int64_t *light_items, int64_t *heavy_items,
                   int64_t *bin_entries);
 
+/* The views of one iteration (Section 5 picks the view of each estimate at random): the first
+ * `count` entries of a Fisher-Yates shuffle of 0..n_views-1 whose i-th step swaps slot i with
+ * slot i + (r_i mod (n_views - i)), r_i the (i+1)-th SplitMix64 output from the key
+ * pair_key(seed, iter, 0xFFFFFFFF, 0xFFFFFFFF) (the same generator family as the signs; no
+ * estimate uses that key).  Host-only, deterministic; out: host [count] distinct view indices.
+ * Needs 1 <= count <= n_views and count <= SGE_MAX_VIEWS_PER_CALL. */
+int sge_draw_views(uint64_t seed, uint32_t iter, int32_t n_views, int32_t count, int32_t *out);
+
 /* Release the host object (never the borrowed device memory). */
 void sge_destroy_scene(sge_scene *scene);
 

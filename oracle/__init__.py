@@ -71,6 +71,7 @@ def lib():
             L.or_mix64.restype, L.or_mix64.argtypes = U64, [U64]
             L.or_pair_key.restype, L.or_pair_key.argtypes = U64, [U64, U32, U32, U32]
             L.or_sign.restype, L.or_sign.argtypes = I32, [U64, U64]
+            L.or_draw_views.restype, L.or_draw_views.argtypes = I32, [U64, U32, I32, I32, P]
             L.or_n_params.restype, L.or_n_params.argtypes = I64, [P]
             L.oracle_render.restype = I32
             L.oracle_render.argtypes = [P, I32, U64, U32, U32, I32, P, P, P]
@@ -162,6 +163,14 @@ def pair_key(seed: int, it: int, view: int, pair: int) -> int:
 
 def sign(key: int, i: int) -> int:
     return int(lib().or_sign(key, i))
+
+
+def draw_views(seed: int, it: int, n_views: int, count: int):
+    """The `count` distinct views of iteration `it` (a random view per estimate, Section 5)."""
+    out = np.empty(count, np.int32)
+    if lib().or_draw_views(seed, it, n_views, count, _ptr(out)):
+        raise ValueError("need 1 <= count <= n_views")
+    return [int(v) for v in out]
 
 
 def render(osc: OracleScene, view: int, seed: int = 0, it: int = 0, pair: int = 0, side: int = 0):

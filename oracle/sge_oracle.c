@@ -96,6 +96,29 @@ int or_sign(uint64_t key, uint64_t i)
     return (out >> 63) ? -1 : 1;
 }
 
+/* The views of one iteration (Section 5 draws the view of each estimate at random): a
+ * Fisher-Yates shuffle of 0..n-1 of which the first `count` entries are kept.  Step i swaps
+ * entry i with entry i + (r_i mod (n - i)), r_i the (i+1)-th generator output from the key
+ * (seed, iteration, view ~0, pair ~0).                                               */
+int or_draw_views(uint64_t seed, uint32_t iter, int32_t n, int32_t count, int32_t *out)
+{
+    if (n < 1 || count < 1 || count > n) return 1;
+    int32_t *a = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!a) return 2;
+    for (int32_t i = 0; i < n; ++i) a[i] = i;
+    uint64_t st = or_pair_key(seed, iter, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    for (int32_t i = 0; i < count; ++i) {
+        uint64_t r = or_splitmix_next(&st);
+        int32_t j = i + (int32_t)(r % (uint64_t)(n - i));
+        int32_t t = a[i];
+        a[i] = a[j];
+        a[j] = t;
+        out[i] = a[i];
+    }
+    free(a);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ parameters */
 static int64_t or_n_pos(const or_scene *s) { return 3 * (int64_t)s->n_vertices; }
 

@@ -19,7 +19,7 @@ from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_TEXTURES, MAX_VIEWS_PER_
                    STEP_SGD, STEP_SGD_MEAN, SGEError)
 from ._build import build
 
-__all__ = ["Scene", "Batch", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
+__all__ = ["Scene", "Batch", "draw_views", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
            "STEP_SGD_MEAN", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
 
 
@@ -269,6 +269,13 @@ class Scene:
         o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), int(t)
         _abi.check(_abi.load().sge_step(self._h, C.byref(o), _ptr(grad), _ptr(counts), int(n_pairs_total),
                                         _ptr(m), _ptr(v), _stream_ptr(stream)))
+
+
+def draw_views(seed: int, it: int, n_views: int, count: int) -> List[int]:
+    """Views of iteration `it` (Section 5: a random view per estimate), `count` distinct ones."""
+    out = (C.c_int32 * int(count))()
+    _abi.check(_abi.load().sge_draw_views(int(seed), int(it), int(n_views), int(count), out))
+    return [int(v) for v in out]
 
 
 class Batch:

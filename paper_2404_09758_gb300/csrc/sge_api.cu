@@ -656,6 +656,46 @@ int sge_bin_stats(sge_scene* s, sge_stream_t stream, int64_t* light_items, int64
   return SGE_OK;
 }
 
+int sge_draw_views(uint64_t seed, uint32_t iter, int32_t n_views, int32_t count, int32_t* out) {
+  if (!out) return fail(SGE_ERR_INVALID_ARG, "out is NULL");
+  if (n_views < 1 || count < 1 || count > n_views || count > SGE_MAX_VIEWS_PER_CALL)
+    return fail(SGE_ERR_INVALID_ARG, "need 1 <= count <= n_views and count <= %d", SGE_MAX_VIEWS_PER_CALL);
+  // the first `count` entries of a Fisher-Yates shuffle of 0..n_views-1 driven by the
+  // generator outputs of the key (seed, iter, ~0, ~0), a key no estimate uses
+  const uint64_t key = pair_key(seed, iter, 0xFFFFFFFFu, 0xFFFFFFFFu);
+  int32_t perm[SGE_MAX_VIEWS_PER_CALL];
+  const int32_t keep = count;
+  // a partial shuffle only touches the first `count` slots and the slots it swaps with:
+  // track those in a small map instead of materialising 0..n_views-1
+  int32_t from[2 * SGE_MAX_VIEWS_PER_CALL], to[2 * SGE_MAX_VIEWS_PER_CALL];
+  int m = 0;
+  auto get = [&](int32_t i) {
+    for (int q = 0; q < m; ++q)
+      if (from[q] == i) return to[q];
+    return i;
+  };
+  auto put = [&](int32_t i, int32_t v) {
+    for (int q = 0; q < m; ++q)
+      if (from[q] == i) {
+        to[q] = v;
+        return;
+      }
+    from[m] = i;
+    to[m] = v;
+    ++m;
+  };
+  for (int32_t i = 0; i < keep; ++i) {
+    const uint64_t r = mix64(key + (uint64_t)(i + 1) * kGamma);
+    const int32_t j = i + (int32_t)(r % (uint64_t)(n_views - i));
+    const int32_t vi = get(i), vj = get(j);
+    put(i, vj);
+    put(j, vi);
+    perm[i] = vj;
+  }
+  for (int32_t i = 0; i < keep; ++i) out[i] = perm[i];
+  return SGE_OK;
+}
+
 void sge_destroy_scene(sge_scene* s) {
   if (s) sge_kernel_timing(s, 0);
   delete s;

@@ -92,3 +92,13 @@ def test_descriptor_checks_run_on_the_host():
         assert (rc == _abi.OK) == ok, (shading, roles, L.sge_last_error())
         if not ok:
             assert rc == _abi.ERR_INVALID_ARG and b"role" in L.sge_last_error()
+
+
+def test_view_draw_equals_the_oracle():
+    """sge_draw_views (host code of the library) against the oracle's independent restatement."""
+    import oracle
+    from paper_2404_09758_gb300 import SGEError, draw_views
+    for seed, it, n, k in ((0, 0, 8, 8), (7, 3, 8, 2), (123456789, 42, 64, 64), (5, 1, 100, 10), (9, 9, 1, 1)):
+        assert draw_views(seed, it, n, k) == oracle.draw_views(seed, it, n, k)
+    with pytest.raises(SGEError):
+        draw_views(0, 0, 4, 5)

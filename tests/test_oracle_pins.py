@@ -426,3 +426,22 @@ def test_adam_step_matches_torch_adam():
         v = st["exp_avg_sq"].numpy().astype(np.float32)
         st["exp_avg"].copy_(torch.tensor(m.astype(np.float64)))
         st["exp_avg_sq"].copy_(torch.tensor(v.astype(np.float64)))
+
+
+def test_view_draw_is_a_uniform_choice_of_distinct_views():
+    """Section 5's random view per estimate: distinct views, each view equally likely (5 sigma
+    over 16,000 draws), a full draw is a permutation, and the draw is a function of (seed, iter)."""
+    import collections
+    for n, k in ((8, 8), (8, 3), (1, 1), (20, 5)):
+        v = oracle.draw_views(3, 7, n, k)
+        assert len(v) == k and len(set(v)) == k and all(0 <= x < n for x in v)
+    assert sorted(oracle.draw_views(11, 2, 8, 8)) == list(range(8))
+    assert oracle.draw_views(5, 9, 8, 4) == oracle.draw_views(5, 9, 8, 4)
+    assert oracle.draw_views(5, 9, 8, 4) != oracle.draw_views(5, 10, 8, 4)
+    n, draws = 8, 16000
+    c = collections.Counter(oracle.draw_views(1, it, n, 1)[0] for it in range(draws))
+    sd = (draws * (1 / n) * (1 - 1 / n)) ** 0.5
+    assert all(abs(c[v] - draws / n) < 5 * sd for v in range(n)), c
+    # second position: uniform over the views other than the first
+    c2 = collections.Counter(tuple(oracle.draw_views(2, it, 4, 2)) for it in range(12000))
+    assert len(c2) == 12 and all(abs(x - 1000) < 5 * (12000 * (1 / 12) * (11 / 12)) ** 0.5 for x in c2.values())
