@@ -177,6 +177,18 @@ int sge_estimate_grad_plain(sge_scene *scene, uint64_t seed, uint32_t iter, cons
                             int32_t n_views, int32_t pairs_per_view, float *grad_sums,
                             uint32_t *counts, float *loss_out, sge_stream_t stream);
 
+/* The full-image estimator the per-pixel form replaces (Eq. 4 with the whole-image error;
+ * Section 6.1 compares the two): for each of the n_views views in view_ids and each pair
+ * n < pairs_per_view, with s drawn from (seed, iter, view, n) exactly as sge_estimate_grad
+ * draws it, dF = f(theta + s eps) - f(theta - s eps) summed over the whole image, then EVERY
+ * parameter i gets grad_sums[i] += dF s_i and counts[i] += 1 (ACCUMULATE, as in
+ * sge_estimate_grad; the estimate is grad_sums[i] / (2 eps_i N)).  image_df (device
+ * [n_views][pairs_per_view] float32, required) receives each estimate's dF.  Runs the renders
+ * one estimate at a time (staged ID/UV buffers); n_views * pairs_per_view <= 4096. */
+int sge_estimate_grad_full_image(sge_scene *scene, uint64_t seed, uint32_t iter, const int32_t *view_ids,
+                                 int32_t n_views, int32_t pairs_per_view, float *grad_sums, uint32_t *counts,
+                                 float *image_df, sge_stream_t stream);
+
 /* Image error of the unperturbed scene, f(theta) = sum over pixels of
  * || I_p(theta) - I_p ||^2 (Table 1), per view: loss_out[j] (device [n_views]
  * float32) ACCUMULATES view view_ids[j]'s error.  The forward value of the

@@ -78,6 +78,8 @@ def lib():
             L.oracle_estimate.restype = I32
             L.oracle_estimate.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P, P, P]
             L.oracle_loss.restype, L.oracle_loss.argtypes = C.c_double, [P, I32]
+            L.oracle_estimate_full_image.restype = I32
+            L.oracle_estimate_full_image.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P, P, P]
             L.oracle_step.restype = None
             L.oracle_step.argtypes = [I32, I64, P, P, P, P, P, I64, C.c_double, C.c_double,
                                       C.c_double, I32, P, P, P, P, P]
@@ -203,6 +205,21 @@ def estimate(osc: OracleScene, seed: int, it: int, view_ids, pairs: int, per_pix
     if per_pixel:
         return S, Cn, loss, df, fm, cd
     return S, Cn, loss
+
+
+def estimate_full_image(osc: OracleScene, seed: int, it: int, view_ids, pairs: int):
+    """Eq. 4 with the whole-image error: sums S [d] float64, counts C [d] uint64, and per
+    estimate (view-major) dF, sum |f+ - f-|, sum max(f+, f-), sum cond (float64 arrays)."""
+    views = np.ascontiguousarray(view_ids, np.int32)
+    S = np.zeros(osc.n_params, np.float64)
+    Cn = np.zeros(osc.n_params, np.uint64)
+    ne = len(views) * pairs
+    dF, A, M, K = (np.zeros(ne) for _ in range(4))
+    rc = lib().oracle_estimate_full_image(osc.ref, seed, it, _ptr(views), len(views), pairs, _ptr(S), _ptr(Cn),
+                                          _ptr(dF), _ptr(A), _ptr(M), _ptr(K))
+    if rc:
+        raise ValueError(f"oracle_estimate_full_image failed ({rc})")
+    return S, Cn, dF, A, M, K
 
 
 def loss(osc: OracleScene, view: int) -> float:

@@ -641,6 +641,77 @@ int oracle_estimate(const or_scene *s, uint64_t seed, uint32_t iter, const int32
     return 0;
 }
 
+/* ------------------------------------------------------------------ public: full-image estimate
+ * The stochastic finite difference of Eq. 4 with the whole-image error f (the estimator the
+ * per-pixel formulation replaces; Section 6.1 compares the two).  For every listed view and
+ * pair n < pairs: s = sign vector of key (seed, iter, view, n); render theta + s eps and
+ * theta - s eps; dF = f(theta + s eps) - f(theta - s eps) = sum_p (f+_p - f-_p) (Table 1);
+ * then for EVERY parameter i: S_i += dF * s_i, C_i += 1.  The estimate is S_i / (2 eps_i N).
+ * Per estimate e = j * pairs + n also: dF[e], and for error bounds sum_p |f+_p - f-_p|,
+ * sum_p max(f+_p, f-_p), sum_p cond_p (cond as in oracle_estimate).                        */
+int oracle_estimate_full_image(const or_scene *s, uint64_t seed, uint32_t iter, const int32_t *view_ids,
+                               int n_views, int pairs, double *S, uint64_t *C, double *dF, double *sum_abs,
+                               double *sum_fmax, double *sum_cond)
+{
+    int W = s->width, H = s->height;
+    int64_t npx = (int64_t)W * H, d = or_n_params(s);
+    uint64_t *kp = malloc(sizeof(uint64_t) * npx), *km = malloc(sizeof(uint64_t) * npx);
+    if (!kp || !km) { free(kp); free(km); return 2; }
+    for (int j = 0; j < n_views; ++j) {
+        int view = view_ids[j];
+        if (view < 0 || view >= s->n_views) { free(kp); free(km); return 1; }
+        const float *tgt = s->targets + (int64_t)view * npx * 3;
+        for (int n = 0; n < pairs; ++n) {
+            uint64_t key = or_pair_key(seed, iter, (uint32_t)view, (uint32_t)n);
+            or_raster(s, view, key, +1, kp);
+            or_raster(s, view, key, -1, km);
+            double F = 0.0, A = 0.0, M = 0.0, K = 0.0;
+            for (int64_t py = 0; py < H; ++py)
+                for (int64_t px = 0; px < W; ++px) {
+                    int64_t p = py * W + px;
+                    double col[2][3];
+                    for (int sd = 0; sd < 2; ++sd) {
+                        uint64_t k = sd == 0 ? kp[p] : km[p];
+                        int side = sd == 0 ? +1 : -1;
+                        if (k == ~0ULL) {
+                            for (int c = 0; c < 3; ++c) col[sd][c] = s->background[c];
+                            continue;
+                        }
+                        int tri = (int)(k & 0xFFFFFFFFu);
+                        or_tri t;
+                        or_setup(s, view, key, side, tri, &t);
+                        or_uvs uv = or_uv(s, &t, tri, 256 * px + 128, 256 * py + 128);
+                        or_shade(s, view, &t, tri, &uv, key, side, col[sd]);
+                    }
+                    double fp = 0.0, fm = 0.0, cd = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        double T = tgt[3 * p + c];
+                        fp += (col[0][c] - T) * (col[0][c] - T);
+                        fm += (col[1][c] - T) * (col[1][c] - T);
+                        double a = col[0][c] - col[1][c], b = col[0][c] + col[1][c] - 2.0 * T;
+                        cd += (fabs(a) + fabs(b)) * (fabs(col[0][c]) + fabs(col[1][c]) + 2.0 * fabs(T));
+                    }
+                    F += fp - fm;
+                    A += fabs(fp - fm);
+                    M += fp > fm ? fp : fm;
+                    K += cd;
+                }
+            int64_t e = (int64_t)j * pairs + n;
+            if (dF) dF[e] = F;
+            if (sum_abs) sum_abs[e] = A;
+            if (sum_fmax) sum_fmax[e] = M;
+            if (sum_cond) sum_cond[e] = K;
+            for (int64_t i = 0; i < d; ++i) {
+                S[i] += F * or_sign(key, (uint64_t)i);
+                C[i] += 1;
+            }
+        }
+    }
+    free(kp);
+    free(km);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ public: full-image loss
  * f(theta) = sum_p || I_p(theta) - I_p ||^2 of the unperturbed scene (Table 1). */
 double oracle_loss(const or_scene *s, int view)

@@ -241,6 +241,19 @@ class Scene:
         _abi.check(_abi.load().sge_bin_stats(self._h, _stream_ptr(stream), C.byref(a), C.byref(b), C.byref(c)))
         return int(a.value), int(b.value), int(c.value)
 
+    def estimate_grad_full_image(self, seed: int, it: int, view_ids: Sequence[int], pairs_per_view: int, grad,
+                                 counts, image_df=None, stream=None):
+        """Eq. 4 with the whole-image error (the estimator Section 6.1 compares with): every
+        parameter gets dF s_i per estimate.  Returns image_df [views, pairs] (each estimate's dF)."""
+        torch = _torch()
+        if image_df is None:
+            image_df = torch.empty(len(view_ids), int(pairs_per_view), dtype=torch.float32, device=self.device)
+        arr, n = self._views(view_ids)
+        _abi.check(_abi.load().sge_estimate_grad_full_image(self._h, int(seed), int(it), arr, n, int(pairs_per_view),
+                                                            _ptr(grad), _ptr(counts), _ptr(image_df),
+                                                            _stream_ptr(stream)))
+        return image_df
+
     def loss(self, view_ids: Sequence[int], out=None, stream=None):
         """Image error f(theta) of the unperturbed scene per listed view (Table 1), [n] float32."""
         torch = _torch()

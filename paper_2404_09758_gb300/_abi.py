@@ -22,7 +22,7 @@ EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_
            "sge_render_idb", "sge_estimate_grad", "sge_estimate_grad_plain", "sge_step", "sge_status",
            "sge_destroy_scene", "sge_last_error", "sge_render_idb_static", "sge_loss", "sge_gradient",
            "sge_estimate_grad_batch", "sge_autotune_batch", "sge_kernel_timing", "sge_kernel_time",
-           "sge_bin_stats", "sge_draw_views")
+           "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image")
 
 
 class Texture(C.Structure):
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = False):
         L.sge_kernel_time.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(I32)]
         L.sge_bin_stats.argtypes = [P, P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]
         L.sge_draw_views.argtypes = [U64, U32, I32, I32, P]
+        L.sge_estimate_grad_full_image.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P]
         L.sge_destroy_scene.argtypes = [P]
         L.sge_destroy_scene.restype = None
         L.sge_last_error.argtypes = []

@@ -238,6 +238,24 @@ __global__ void k_scatter(SceneDev S, Workspace ws, uint64_t key, float* grad, u
   });
 }
 
+// Full-image estimator (Eq. 4), step G: the estimate's whole-image loss difference
+// sum_p (f+_p - f-_p), from the staged per-pixel differences, added to *out.
+__global__ void __launch_bounds__(256) k_reduce_image(const float* df, long long npx, float* out) {
+  __shared__ float red[8];
+  float v = 0.0f;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += (long long)gridDim.x * blockDim.x)
+    v += df[p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sum = 0.0f;
+    for (int i = 0; i < 8; ++i) sum += red[i];
+    atomicAdd(out, sum);
+  }
+}
+
 __global__ void k_validate(SceneDev S, uint32_t* status) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3ll * S.nt) return;
@@ -267,6 +285,16 @@ cudaError_t launch_plain_pair(const SceneDev& S, const Workspace& ws, int slot, 
   k_raster_pair<<<n_tiles(S), TILE_PX, 0, st>>>(S, ws, slot, view, key);
   k_shade_delta<<<blocks, 256, 0, st>>>(S, ws, view, key, a.loss, loss_scale, slot);
   k_scatter<<<blocks, 256, 0, st>>>(S, ws, key, a.grad, a.counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_delta(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key, float* out,
+                               cudaStream_t st) {
+  const long long npx = (long long)S.W * S.H;
+  const int blocks = (int)((npx + 255) / 256);
+  k_raster_pair<<<n_tiles(S), TILE_PX, 0, st>>>(S, ws, slot, view, key);
+  k_shade_delta<<<blocks, 256, 0, st>>>(S, ws, view, key, nullptr, 0.0f, slot);
+  k_reduce_image<<<blocks < 1024 ? blocks : 1024, 256, 0, st>>>(ws.dfbuf, npx, out);
   return cudaGetLastError();
 }
 

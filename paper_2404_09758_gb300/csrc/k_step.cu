@@ -3,7 +3,7 @@
 // are zeroed for the next iteration.  One thread per parameter; memory bound.
 #include <cuda_runtime.h>
 
-#include "sge_internal.h"
+#include "sge_device.cuh"
 
 namespace sge {
 
@@ -83,6 +83,28 @@ int grid_for(long long n) {
   return blocks < 1 ? 1 : (int)blocks;
 }
 
+// Full-image estimator (Eq. 4), accumulation: every parameter i gets sum_e dF_e s_i(e) over
+// the call's estimates e (signs from each estimate's key) and one count per estimate.  The
+// estimates' keys and differences are staged in shared memory once per CTA; one thread per
+// parameter (grid-stride).
+__global__ void k_full_image_grad(long long d, int n_est, int pairs, ViewList vl, uint64_t seed, uint32_t iter,
+                                  const float* dF, float* grad, uint32_t* counts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* keys = reinterpret_cast<uint64_t*>(smem_raw);
+  float* dfs = reinterpret_cast<float*>(keys + n_est);
+  for (int e = threadIdx.x; e < n_est; e += blockDim.x) {
+    keys[e] = pair_key(seed, iter, (uint32_t)vl.id[e / pairs], (uint32_t)(e % pairs));
+    dfs[e] = dF[e];
+  }
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (long long)gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (int e = 0; e < n_est; ++e) acc += sign_neg(keys[e], (uint64_t)i) ? -dfs[e] : dfs[e];
+    grad[i] += acc;
+    counts[i] += (uint32_t)n_est;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_gradient(const SceneDev& S, const float* grad, long long n_total, const float* scale, float* out,
@@ -119,6 +141,16 @@ cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32
   if (blocks < 1) blocks = 1;
   k_step<<<(unsigned)blocks, 256, 0, st>>>(G, o.kind, grad, counts, (float)(1.0 / (double)n_total), o.beta1,
                                            o.beta2, (float)c1, (float)c2, o.adam_eps, m, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full_image_grad(const SceneDev& S, const ViewList& vl, int pairs, uint64_t seed, uint32_t iter,
+                                   const float* dF, float* grad, uint32_t* counts, cudaStream_t st) {
+  const int n_est = vl.n * pairs;
+  const size_t smem = (size_t)n_est * (sizeof(uint64_t) + sizeof(float));
+  long long blocks = (S.n_params + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_full_image_grad<<<(unsigned)blocks, 256, smem, st>>>(S.n_params, n_est, pairs, vl, seed, iter, dF, grad, counts);
   return cudaGetLastError();
 }
 

@@ -366,6 +366,29 @@ int sge_estimate_grad_plain(sge_scene* s, uint64_t seed, uint32_t iter, const in
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad_plain");
 }
 
+int sge_estimate_grad_full_image(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids,
+                                 int32_t n_views, int32_t pairs_per_view, float* grad_sums, uint32_t* counts,
+                                 float* image_df, sge_stream_t stream) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  if (!grad_sums || !counts || !image_df) return fail(SGE_ERR_INVALID_ARG, "grad_sums, counts and image_df must be non-NULL");
+  if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
+  ViewList vl;
+  int rc = views_of(s, view_ids, n_views, vl);
+  if (rc) return rc;
+  if ((long long)n_views * pairs_per_view > 4096)
+    return fail(SGE_ERR_INVALID_ARG, "n_views * pairs_per_view = %lld above 4096", (long long)n_views * pairs_per_view);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(image_df, 0, sizeof(float) * (size_t)n_views * pairs_per_view, st);
+  if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
+  for (int j = 0; j < n_views && e == cudaSuccess; ++j)
+    for (int n = 0; n < pairs_per_view && e == cudaSuccess; ++n)
+      e = launch_image_delta(s->dev, s->ws, j, vl.id[j], pair_key(seed, iter, (uint32_t)vl.id[j], (uint32_t)n),
+                             image_df + (size_t)j * pairs_per_view + n, st);
+  if (e == cudaSuccess)
+    e = launch_full_image_grad(s->dev, vl, pairs_per_view, seed, iter, image_df, grad_sums, counts, st);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad_full_image");
+}
+
 int sge_step(sge_scene* s, const sge_opt* o, float* grad_sums, uint32_t* counts, int64_t n_pairs_total, float* adam_m,
              float* adam_v, sge_stream_t stream) {
   if (!s || !o) return fail(SGE_ERR_INVALID_ARG, "NULL argument");

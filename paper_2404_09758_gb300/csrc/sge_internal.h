@@ -181,6 +181,13 @@ cudaError_t launch_render(const SceneDev& S, const Workspace& ws, int slot, int 
 cudaError_t launch_plain_pair(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key,
                               const EstimateArgs& a, float loss_scale, cudaStream_t st);
 
+// Full-image estimator (Eq. 4): one estimate's whole-image loss difference added to *out (both
+// renders staged in the workspace), and the accumulation of every parameter's sum over a call.
+cudaError_t launch_image_delta(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key, float* out,
+                               cudaStream_t st);
+cudaError_t launch_full_image_grad(const SceneDev& S, const ViewList& vl, int pairs, uint64_t seed, uint32_t iter,
+                                   const float* dF, float* grad, uint32_t* counts, cudaStream_t st);
+
 // Image error of unperturbed renders (forward of the autograd form), added to loss[slot].
 cudaError_t launch_render_loss(const SceneDev& S, const Workspace& ws, int slot, int view, float* loss,
                                cudaStream_t st);

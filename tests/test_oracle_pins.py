@@ -445,3 +445,53 @@ def test_view_draw_is_a_uniform_choice_of_distinct_views():
     # second position: uniform over the views other than the first
     c2 = collections.Counter(tuple(oracle.draw_views(2, it, 4, 2)) for it in range(12000))
     assert len(c2) == 12 and all(abs(x - 1000) < 5 * (12000 * (1 / 12) * (11 / 12)) ** 0.5 for x in c2.values())
+
+
+# ------------------------------------------------------------- full-image estimator (Eq. 4)
+
+def test_full_image_difference_is_the_loss_of_two_explicit_scenes():
+    """dF of Eq. 4 is f(theta + s eps) - f(theta - s eps): rebuild both scenes explicitly from
+    the published signs and take the difference of their whole-image errors."""
+    sc, tgt = _quad_texture_scene(n=4, W=16)
+    sc = synth.with_params(sc, sc.positions + np.float32(0.0), [sc.textures[0].data])
+    osc = oracle.OracleScene(sc, tgt)
+    seed, it = 8, 3
+    S, Cn, dF, A, M, K = oracle.estimate_full_image(osc, seed, it, [0], 1)
+    key = oracle.pair_key(seed, it, 0, 0)
+    d = sc.n_params
+    s = np.array([oracle.sign(key, i) for i in range(d)], np.float64)
+    eps = np.concatenate([np.full(sc.n_pos_params, sc.eps_pos), np.full(d - sc.n_pos_params, sc.textures[0].eps)])
+    theta = np.concatenate([sc.positions.ravel(), sc.textures[0].data.ravel()]).astype(np.float32)
+
+    def f_of(sign):
+        th = (theta + (sign * s * eps).astype(np.float32)).astype(np.float32)
+        s2 = synth.with_params(sc, th[:sc.n_pos_params].reshape(-1, 3),
+                               [th[sc.n_pos_params:].reshape(sc.textures[0].data.shape)])
+        return oracle.loss(oracle.OracleScene(s2, tgt), 0)
+
+    want = f_of(+1) - f_of(-1)
+    assert want != 0.0 and abs(dF[0] - want) <= 1e-9 * max(1.0, abs(want))
+    # every parameter is credited: S = dF * s, one count each
+    assert np.allclose(S, dF[0] * s, rtol=0, atol=1e-12 * max(1.0, abs(dF[0])))
+    assert (Cn == 1).all()
+    assert A[0] >= abs(dF[0]) and M[0] > 0 and K[0] > 0
+
+
+def test_full_image_expectation_over_all_sign_vectors_is_the_gradient():
+    """Eq. 4 averaged over all 2^d sign vectors of a 2x2 RGB texture gives the exact gradient
+    (f is quadratic in the texels), like the per-pixel form."""
+    sc, tgt = _quad_texture_scene(n=2, W=8)
+    d_pos, d = sc.n_pos_params, sc.n_params
+    eps = sc.textures[0].eps
+    key = oracle.pair_key(5, 0, 0, 0)
+    s_hash = np.array([oracle.sign(key, i) for i in range(d)], np.float32)
+    n_tex = d - d_pos
+    total = np.zeros(n_tex)
+    for mask in range(1 << n_tex):
+        sigma = np.array([1.0 if (mask >> j) & 1 else -1.0 for j in range(n_tex)], np.float32)
+        eps_vec = np.zeros(d, np.float32)
+        eps_vec[d_pos:] = sigma * s_hash[d_pos:] * eps
+        S = oracle.estimate_full_image(oracle.OracleScene(sc, tgt, eps_vec=eps_vec), 5, 0, [0], 1)[0]
+        total += S[d_pos:] / (2.0 * eps_vec[d_pos:])
+    g = _exact_texel_gradient(sc, tgt)
+    assert np.allclose(total / (1 << n_tex), g, rtol=1e-9, atol=1e-9)
