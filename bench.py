@@ -541,15 +541,70 @@ def run_scale(args):
     print(json.dumps(line), flush=True)
 
 
+def run_full_image(args):
+    """The full-image estimator (Eq. 4 with the whole-image error) on the batched configuration's
+    workload (8 views x 64 pairs, 512^2): every estimate renders both sides (staged ID/UV
+    buffers), sums f+ - f- over the image, and every parameter is credited dF s_i.  The paper
+    shows it converging far slower than the per-pixel form (Section 6.1); it is timed here as
+    the comparison estimator, eagerly, one estimate after another."""
+    import torch
+
+    import synth
+    from paper_2404_09758_gb300 import Scene
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = make_scene()
+    ts = Scene.from_arrays(synth.target_scene(sc))
+    targets = ts.render_targets()
+    torch.cuda.synchronize()
+    del ts
+    g = Scene.from_arrays(sc, targets=targets)
+    grad, counts = g.new_grad_buffers()
+    views = list(range(N_VIEWS))
+    st = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(st):
+        for w in range(args.warmup):
+            g.estimate_grad_full_image(1, w, views, PAIRS, grad, counts, stream=st)
+    st.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(st):
+            for k in range(args.steps):
+                flush.fill_(k & 0xFF)
+                ev[k][0].record(st)
+                g.estimate_grad_full_image(1, 100 + k, views, PAIRS, grad, counts, stream=st)
+                ev[k][1].record(st)
+        torch.cuda.synchronize()
+    assert g.status(st) == 0
+    px_per_step = N_VIEWS * PAIRS * RENDER * RENDER
+    value, t_total = job_throughput(sum(a.elapsed_time(b) for a, b in ev) / 1000.0, px_per_step * args.steps)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + "_full_image_estimator", "views": N_VIEWS, "pairs_per_view": PAIRS,
+                       "l2": "flushed between timed steps (256 MB write)", "graph": "none (eager)"},
+            "param_gradients_per_s": g.n_params * N_VIEWS * PAIRS * args.steps / t_total,
+            # per estimate: raster of both sides, loss differences, image sum; per call: binning,
+            # the per-parameter accumulation
+            "gpu_launches": (3 * N_VIEWS * PAIRS + 4) * args.steps,
+            "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["batched", "uneven", "scale"], default="batched",
+    ap.add_argument("--workload", choices=["batched", "uneven", "scale", "full_image"], default="batched",
                     help="batched: the headline configuration; uneven: 32 assets in one batched call; "
-                         "scale: 1M triangles, GGX, 2048^2")
+                         "scale: 1M triangles, GGX, 2048^2; full_image: Eq. 4's whole-image estimator on "
+                         "the batched configuration")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -559,6 +614,8 @@ def main():
         run_uneven(args)
     elif args.workload == "scale":
         run_scale(args)
+    elif args.workload == "full_image":
+        run_full_image(args)
     else:
         run_ours(args)
 

@@ -495,3 +495,22 @@ def test_full_image_expectation_over_all_sign_vectors_is_the_gradient():
         total += S[d_pos:] / (2.0 * eps_vec[d_pos:])
     g = _exact_texel_gradient(sc, tgt)
     assert np.allclose(total / (1 << n_tex), g, rtol=1e-9, atol=1e-9)
+
+
+def test_per_pixel_estimate_has_less_variance_than_full_image():
+    """Section 3's motivation, measured: on a textured quad the per-pixel estimator (Eq. 8) of a
+    texel's gradient varies far less than the full-image one (Eq. 4), whose every texel carries
+    the whole image's difference; both are unbiased here, so their means agree."""
+    sc, tgt = _quad_texture_scene(n=4, W=16)
+    osc = oracle.OracleScene(sc, tgt)
+    d_pos, eps = sc.n_pos_params, sc.textures[0].eps
+    n = 1500
+    pp = np.zeros((n, sc.n_params - d_pos))
+    fi = np.zeros_like(pp)
+    for it in range(n):
+        pp[it] = oracle.estimate(osc, 13, it, [0], 1)[0][d_pos:] / (2 * eps)
+        fi[it] = oracle.estimate_full_image(osc, 13, it, [0], 1)[0][d_pos:] / (2 * eps)
+    var_pp, var_fi = pp.var(0), fi.var(0)
+    assert np.median(var_fi / var_pp) > 3.0, np.median(var_fi / var_pp)
+    se = np.sqrt((var_pp + var_fi) / n)
+    assert np.median(np.abs(pp.mean(0) - fi.mean(0)) / se) < 1.0
