@@ -50,7 +50,7 @@ typedef enum {
     SGE_ERR_CUDA = 2,          /* a CUDA runtime call failed                         */
     SGE_ERR_BIN_OVERFLOW = 3,  /* (device status) tile bins exceeded bin_capacity    */
     SGE_ERR_BAD_INDEX = 4,     /* (device status) an index buffer entry out of range */
-    SGE_ERR_UNSUPPORTED = 5,   /* a valid request this build does not implement      */
+    SGE_ERR_UNSUPPORTED = 5,   /* a valid request the library does not implement     */
     SGE_ERR_WORKSPACE = 6      /* workspace missing, too small or misaligned         */
 } sge_result;
 
