@@ -189,6 +189,19 @@ int sge_estimate_grad_full_image(sge_scene *scene, uint64_t seed, uint32_t iter,
                                  int32_t n_views, int32_t pairs_per_view, float *grad_sums, uint32_t *counts,
                                  float *image_df, sge_stream_t stream);
 
+/* Control-mesh optimisation through a subdivision (linear first; the paper tessellates a
+ * Catmull-Clark surface on the fly and credits each tessellated triangle to its control mesh,
+ * Section 6.3): the subdivided mesh's vertices are a fixed linear map of the control vertices,
+ * fine = R control, so the control vertices' gradient is R^T times the fine vertices' one, and
+ * R^T applied to the sums of sge_estimate_grad (the first 3 V_fine entries) gives sums whose
+ * Eq. 9 estimate (/ 2 eps N) is that of the control coordinates.  sge_refine computes, for
+ * every row r of a CSR matrix A (device row_ptr [n_rows + 1], col [nnz], w [nnz] float32),
+ * y[3r + k] = sum_j w_j x[3 col_j + k] for k = 0, 1, 2 (x, y device float32; accumulate != 0
+ * adds to y instead of overwriting it), summing each row in order.  Pass R to refine
+ * positions (fine = R control) and R^T's CSR to map sums (control += R^T fine). */
+int sge_refine(const int32_t *row_ptr, const int32_t *col, const float *w, int32_t n_rows, const float *x,
+               float *y, int32_t accumulate, sge_stream_t stream);
+
 /* Image error of the unperturbed scene, f(theta) = sum over pixels of
  * || I_p(theta) - I_p ||^2 (Table 1), per view: loss_out[j] (device [n_views]
  * float32) ACCUMULATES view view_ids[j]'s error.  The forward value of the

@@ -19,7 +19,7 @@ from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_TEXTURES, MAX_VIEWS_PER_
                    STEP_SGD, STEP_SGD_MEAN, SGEError)
 from ._build import build
 
-__all__ = ["Scene", "Batch", "draw_views", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
+__all__ = ["Scene", "Batch", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
            "STEP_SGD_MEAN", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
 
 
@@ -289,6 +289,20 @@ def draw_views(seed: int, it: int, n_views: int, count: int) -> List[int]:
     out = (C.c_int32 * int(count))()
     _abi.check(_abi.load().sge_draw_views(int(seed), int(it), int(n_views), int(count), out))
     return [int(v) for v in out]
+
+
+def refine(matrix, x, y=None, accumulate: bool = False, stream=None):
+    """y (+)= A x for xyz rows: A a CSR triple (row_ptr int32, col int32, w float32; CUDA tensors),
+    x [n_cols, 3] float32.  With A = R, the refine matrix of a subdivision, y = fine positions;
+    with A = R^T, y accumulates the control vertices' sums from the fine ones (chain rule)."""
+    torch = _torch()
+    row_ptr, col, w = matrix
+    n_rows = int(row_ptr.numel()) - 1
+    if y is None:
+        y = torch.zeros(n_rows, 3, dtype=torch.float32, device=x.device)
+    _abi.check(_abi.load().sge_refine(_ptr(row_ptr), _ptr(col), _ptr(w), n_rows, _ptr(x), _ptr(y),
+                                      1 if accumulate else 0, _stream_ptr(stream)))
+    return y
 
 
 class Batch:

@@ -22,7 +22,8 @@ EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_
            "sge_render_idb", "sge_estimate_grad", "sge_estimate_grad_plain", "sge_step", "sge_status",
            "sge_destroy_scene", "sge_last_error", "sge_render_idb_static", "sge_loss", "sge_gradient",
            "sge_estimate_grad_batch", "sge_autotune_batch", "sge_kernel_timing", "sge_kernel_time",
-           "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image")
+           "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image",
+           "sge_refine")
 
 
 class Texture(C.Structure):
@@ -108,6 +109,7 @@ def load(build_if_missing: bool = False):
         L.sge_bin_stats.argtypes = [P, P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64)]
         L.sge_draw_views.argtypes = [U64, U32, I32, I32, P]
         L.sge_estimate_grad_full_image.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P]
+        L.sge_refine.argtypes = [P, P, P, I32, P, P, I32, P]
         L.sge_destroy_scene.argtypes = [P]
         L.sge_destroy_scene.restype = None
         L.sge_last_error.argtypes = []

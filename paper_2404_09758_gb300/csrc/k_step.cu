@@ -105,6 +105,32 @@ __global__ void k_full_image_grad(long long d, int n_est, int pairs, ViewList vl
   }
 }
 
+// y[r] (+)= sum_j w_j x[col_j] for 3-vectors (xyz per row), rows of a CSR matrix in fixed order:
+// the refine matrix of a subdivision (fine = R control) or its transpose (control gradient =
+// R^T fine gradient).  One thread per row.
+__global__ void k_csr_vec3(const int32_t* ptr, const int32_t* col, const float* w, int n_rows, const float* x,
+                           float* y, int accumulate) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+  for (int j = ptr[r]; j < ptr[r + 1]; ++j) {
+    const float wj = w[j];
+    const long long c = 3ll * col[j];
+    a0 += wj * x[c];
+    a1 += wj * x[c + 1];
+    a2 += wj * x[c + 2];
+  }
+  if (accumulate) {
+    y[3ll * r] += a0;
+    y[3ll * r + 1] += a1;
+    y[3ll * r + 2] += a2;
+  } else {
+    y[3ll * r] = a0;
+    y[3ll * r + 1] = a1;
+    y[3ll * r + 2] = a2;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_gradient(const SceneDev& S, const float* grad, long long n_total, const float* scale, float* out,
@@ -151,6 +177,12 @@ cudaError_t launch_full_image_grad(const SceneDev& S, const ViewList& vl, int pa
   long long blocks = (S.n_params + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
   k_full_image_grad<<<(unsigned)blocks, 256, smem, st>>>(S.n_params, n_est, pairs, vl, seed, iter, dF, grad, counts);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_csr_vec3(const int32_t* ptr, const int32_t* col, const float* w, int n_rows, const float* x,
+                            float* y, int accumulate, cudaStream_t st) {
+  if (n_rows > 0) k_csr_vec3<<<(n_rows + 255) / 256, 256, 0, st>>>(ptr, col, w, n_rows, x, y, accumulate);
   return cudaGetLastError();
 }
 

@@ -389,6 +389,14 @@ int sge_estimate_grad_full_image(sge_scene* s, uint64_t seed, uint32_t iter, con
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad_full_image");
 }
 
+int sge_refine(const int32_t* row_ptr, const int32_t* col, const float* w, int32_t n_rows, const float* x, float* y,
+               int32_t accumulate, sge_stream_t stream) {
+  if (!row_ptr || !y || (n_rows > 0 && (!col || !w || !x))) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  if (n_rows < 0) return fail(SGE_ERR_INVALID_ARG, "n_rows must be >= 0");
+  cudaError_t e = launch_csr_vec3(row_ptr, col, w, n_rows, x, y, accumulate ? 1 : 0, (cudaStream_t)stream);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_refine");
+}
+
 int sge_step(sge_scene* s, const sge_opt* o, float* grad_sums, uint32_t* counts, int64_t n_pairs_total, float* adam_m,
              float* adam_v, sge_stream_t stream) {
   if (!s || !o) return fail(SGE_ERR_INVALID_ARG, "NULL argument");

@@ -188,6 +188,10 @@ cudaError_t launch_image_delta(const SceneDev& S, const Workspace& ws, int slot,
 cudaError_t launch_full_image_grad(const SceneDev& S, const ViewList& vl, int pairs, uint64_t seed, uint32_t iter,
                                    const float* dF, float* grad, uint32_t* counts, cudaStream_t st);
 
+// y (+)= A x for 3-vectors per row, A in CSR (row pointers, columns, weights; device).
+cudaError_t launch_csr_vec3(const int32_t* ptr, const int32_t* col, const float* w, int n_rows, const float* x,
+                            float* y, int accumulate, cudaStream_t st);
+
 // Image error of unperturbed renders (forward of the autograd form), added to loss[slot].
 cudaError_t launch_render_loss(const SceneDev& S, const Workspace& ws, int slot, int view, float* loss,
                                cudaStream_t st);

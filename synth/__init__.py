@@ -120,6 +120,38 @@ def subdivide_linear(mesh: Mesh, levels: int = 1) -> Mesh:
     return Mesh(pos.astype(np.float32), pidx, uvs.astype(np.float32), tidx)
 
 
+def linear_refine_matrix(mesh: Mesh, levels: int = 1):
+    """Refine matrix of subdivide_linear(mesh, levels): a scipy CSR matrix R (fine vertices x
+    control vertices) with the fine positions = R @ mesh.positions; a midpoint row is half of
+    each end of its edge, in the order subdivide_linear creates them."""
+    import scipy.sparse as sp
+    R = sp.identity(len(mesh.positions), format="csr", dtype=np.float64)
+    pidx = mesh.pos_idx
+    for _ in range(levels):
+        n = R.shape[0]
+        ends, cache, npi = [], {}, []
+
+        def mid(a, b):
+            if a == b:
+                return a
+            key = (a, b) if a < b else (b, a)
+            if key not in cache:
+                cache[key] = n + len(ends)
+                ends.append((a, b))
+            return cache[key]
+
+        for p0, p1, p2 in pidx.tolist():
+            m01, m12, m20 = mid(p0, p1), mid(p1, p2), mid(p2, p0)
+            npi += [[p0, m01, m20], [m01, p1, m12], [m20, m12, p2], [m01, m12, m20]]
+        k = len(ends)
+        cols = np.asarray(ends, np.int64).ravel()
+        M = sp.csr_matrix((np.full(2 * k, 0.5), (np.repeat(np.arange(k), 2), cols)), shape=(k, n))
+        R = sp.vstack([R, M @ R]).tocsr()
+        pidx = np.asarray(npi, np.int32)
+    R.sort_indices()
+    return R
+
+
 def radial_displace(positions: np.ndarray, seed: int, amplitude: float = 0.05,
                     n_terms: int = 4) -> np.ndarray:
     """Seeded low-frequency radial displacement: p <- p * (1 + a * g(p)), |g| <= 1."""

@@ -498,7 +498,7 @@ def test_full_image_expectation_over_all_sign_vectors_is_the_gradient():
 
 
 def test_per_pixel_estimate_has_less_variance_than_full_image():
-    """Section 3's motivation, measured: on a textured quad the per-pixel estimator (Eq. 8) of a
+    """Section 4.2's motivation, measured: on a textured quad the per-pixel estimator (Eq. 8) of a
     texel's gradient varies far less than the full-image one (Eq. 4), whose every texel carries
     the whole image's difference; both are unbiased here, so their means agree."""
     sc, tgt = _quad_texture_scene(n=4, W=16)
@@ -514,3 +514,16 @@ def test_per_pixel_estimate_has_less_variance_than_full_image():
     assert np.median(var_fi / var_pp) > 3.0, np.median(var_fi / var_pp)
     se = np.sqrt((var_pp + var_fi) / n)
     assert np.median(np.abs(pp.mean(0) - fi.mean(0)) / se) < 1.0
+
+
+def test_linear_refine_matrix_reproduces_the_subdivision():
+    """The refine matrix of midpoint subdivision maps control positions to the subdivided mesh's
+    positions (every row sums to 1: a subdivided vertex is an affine combination)."""
+    c = synth.uv_sphere(12, 8)
+    for levels in (1, 2):
+        f = synth.subdivide_linear(c, levels)
+        R = synth.linear_refine_matrix(c, levels)
+        assert R.shape == (len(f.positions), len(c.positions))
+        assert np.allclose(np.asarray(R.sum(1)).ravel(), 1.0)
+        got = (R @ c.positions.astype(np.float64)).astype(np.float32)
+        assert np.abs(got - f.positions).max() <= 2 * np.finfo(np.float32).eps
