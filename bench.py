@@ -595,16 +595,88 @@ def run_full_image(args):
         print(json.dumps(line), flush=True)
 
 
+def run_converge(args):
+    """Many-step optimisation of the autograd configuration (32,768-triangle displaced sphere,
+    1024^2 RGBA albedo + normal map, Lambert, 1024^2, 16 views x 16 pairs per iteration, Adam with
+    the paper's settings) for a fixed wall time: the image error of all views against time, like the
+    paper's teaser snapshots (130 s / 720 s on its own scene and GPU, context only)."""
+    import torch
+
+    import synth
+    from paper_2404_09758_gb300 import STEP_ADAM, Scene
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = synth.config_autograd()
+    views = list(range(sc.n_views))
+    pairs = sc.pairs_per_view
+    ts = Scene.from_arrays(synth.target_scene(sc), max_pairs_per_call=pairs)
+    targets = ts.render_targets()
+    torch.cuda.synchronize()
+    del ts
+    g = Scene.from_arrays(sc, targets=targets, max_pairs_per_call=pairs)
+    grad, counts = g.new_grad_buffers()
+    m = torch.zeros(g.n_params, device=dev)
+    v = torch.zeros(g.n_params, device=dev)
+    lr_tex = [t[1] for t in g.textures]
+    st = torch.cuda.Stream(device=dev)
+
+    def image_error():
+        with torch.cuda.stream(st):
+            e = g.loss(views, stream=st)
+        st.synchronize()
+        return float(e.sum().item())
+
+    def iteration(it, t):
+        g.estimate_grad(1, it, views, pairs, grad, counts, stream=st)
+        g.step(STEP_ADAM, grad, counts, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+
+    e0 = image_error()
+    # eager launches: an iteration is ~12 launches against a GPU time of tens of milliseconds, and
+    # every iteration needs its own sign keys and Adam step number
+    torch.cuda.synchronize()
+    curve = [(0.0, e0)]
+    t0 = time.perf_counter()
+    n_iter = 0
+    next_sample = 1.0
+    while True:
+        with torch.cuda.stream(st):
+            iteration(n_iter, n_iter + 1)
+        st.synchronize()  # no backlog: the clock reads finished work
+        n_iter += 1
+        el = time.perf_counter() - t0
+        if el >= next_sample or el >= args.seconds:
+            m0 = time.perf_counter()
+            curve.append((round(el, 3), image_error()))
+            t0 += time.perf_counter() - m0  # the measurement is not optimisation time
+            next_sample = el * 2.0 if el < 8.0 else el + 8.0
+            if el >= args.seconds:
+                break
+    line = {"metric": "image error against optimisation time (autograd configuration)", "value": curve[-1][1],
+            "unit": "sum of squared errors, all views", "n_gpus": 1, "steps": n_iter, "warmup": 0,
+            "ms_per_step": 1000.0 * curve[-1][0] / n_iter, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "subdiv32k_rgba1024_nrm1024_r1024_16views_x_16pairs_adam",
+                       "seconds": args.seconds, "graph": "none (eager; the error is measured between iterations)"},
+            "initial_error": e0, "curve": curve, "reduction": curve[-1][1] / e0,
+            # per iteration: 4 binning and pruning kernels, the vertex pass, the two estimators, the step
+            "gpu_launches": 8 * n_iter}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["batched", "uneven", "scale", "full_image"], default="batched",
+    ap.add_argument("--seconds", type=float, default=60.0, help="wall time of --workload converge")
+    ap.add_argument("--workload", choices=["batched", "uneven", "scale", "full_image", "converge"], default="batched",
                     help="batched: the headline configuration; uneven: 32 assets in one batched call; "
                          "scale: 1M triangles, GGX, 2048^2; full_image: Eq. 4's whole-image estimator on "
-                         "the batched configuration")
+                         "the batched configuration; converge: optimise the autograd configuration "
+                         "for --seconds and report the image error against time")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -616,6 +688,8 @@ def main():
         run_scale(args)
     elif args.workload == "full_image":
         run_full_image(args)
+    elif args.workload == "converge":
+        run_converge(args)
     else:
         run_ours(args)
 
