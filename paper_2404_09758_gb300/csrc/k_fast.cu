@@ -980,10 +980,11 @@ int fast_batch_blocks_per_sm(int shading) {
   return fast_batch_blocks_per_sm_t<SHADE_GGX>();
 }
 
-int fast_blocks_per_sm(int shading) {
+int fast_blocks_per_sm(int shading, int grouped) {
   if (shading == SHADE_UNLIT) return fast_blocks_per_sm_t<SHADE_UNLIT, false>();
-  if (shading == SHADE_LAMBERT) return fast_blocks_per_sm_t<SHADE_LAMBERT, false>();
-  return fast_blocks_per_sm_t<SHADE_GGX, false>();
+  if (shading == SHADE_LAMBERT)
+    return grouped ? fast_blocks_per_sm_t<SHADE_LAMBERT, true>() : fast_blocks_per_sm_t<SHADE_LAMBERT, false>();
+  return grouped ? fast_blocks_per_sm_t<SHADE_GGX, true>() : fast_blocks_per_sm_t<SHADE_GGX, false>();
 }
 
 }  // namespace sge

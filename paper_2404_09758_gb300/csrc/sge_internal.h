@@ -162,7 +162,7 @@ cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& 
 cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                                cudaStream_t st);
 int estimate_blocks_per_sm(int shading, int grouped);
-int fast_blocks_per_sm(int shading);
+int fast_blocks_per_sm(int shading, int grouped);
 
 // Batched form of the two estimator kernels over BatchArgs' assets.
 // Image error of background-only tiles (both sides show the background), added to loss[slot].
