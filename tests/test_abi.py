@@ -102,3 +102,53 @@ def test_view_draw_equals_the_oracle():
         assert draw_views(seed, it, n, k) == oracle.draw_views(seed, it, n, k)
     with pytest.raises(SGEError):
         draw_views(0, 0, 4, 5)
+
+
+def _valid_desc():
+    import ctypes as C
+    from paper_2404_09758_gb300 import _abi
+    d = _abi.SceneDesc()
+    fake = 0x1000  # never dereferenced by the host checks
+    d.positions, d.n_vertices, d.eps_pos = fake, 3, 1e-3
+    d.pos_idx, d.n_triangles, d.uvs, d.n_uvs, d.uv_idx = fake, 1, fake, 3, fake
+    d.mvp, d.cam_pos, d.n_views, d.width, d.height, d.near_w, d.targets = fake, fake, 2, 32, 24, 0.1, fake
+    d.shading, d.n_textures = 0, 1
+    t = d.textures[0]
+    t.texels, t.width, t.height, t.channels, t.eps, t.role = fake, 4, 4, 3, 1.0 / 255.0, 0
+    return d
+
+
+@pytest.mark.parametrize("field, value", [
+    ("n_vertices", 2), ("n_triangles", 0), ("n_views", 0), ("width", 0), ("height", 20000),
+    ("eps_pos", -1.0), ("eps_pos", float("nan")), ("near_w", 0.0), ("shading", 3), ("n_textures", 9),
+    ("positions", None), ("targets", None), ("tex_channels", 5), ("tex_role", 4), ("tex_eps", -1.0),
+    ("tex_texels", None)])
+def test_invalid_descriptions_are_rejected_on_the_host(field, value):
+    import ctypes as C
+    from paper_2404_09758_gb300 import _abi
+    L = _abi.load(build_if_missing=True)
+    d = _valid_desc()
+    n = C.c_size_t()
+    assert L.sge_workspace_size(C.byref(d), None, C.byref(n)) == _abi.OK and n.value > 0
+    if field.startswith("tex_"):
+        setattr(d.textures[0], field[4:], value)
+    else:
+        setattr(d, field, value)
+    assert L.sge_workspace_size(C.byref(d), None, C.byref(n)) == _abi.ERR_INVALID_ARG
+    assert L.sge_last_error()  # a message says which
+
+
+def test_workspace_grows_with_views_and_pairs():
+    import ctypes as C
+    from paper_2404_09758_gb300 import _abi
+    L = _abi.load(build_if_missing=True)
+    d = _valid_desc()
+    sizes = []
+    for views, pairs in ((1, 1), (2, 1), (2, 8)):
+        cfg = _abi.Config(views, 0, 0, 0, pairs)
+        n = C.c_size_t()
+        assert L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(n)) == _abi.OK
+        sizes.append(n.value)
+    assert sizes[0] < sizes[1] < sizes[2]
+    cfg = _abi.Config(0, 1 << 33, 0, 0, 0)  # bin capacity must stay below 2^32 entries
+    assert L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(C.c_size_t())) == _abi.ERR_INVALID_ARG
