@@ -599,16 +599,23 @@ def run_converge(args):
     """Many-step optimisation of the autograd configuration (32,768-triangle displaced sphere,
     1024^2 RGBA albedo + normal map, Lambert, 1024^2, 16 views x 16 pairs per iteration, Adam with
     the paper's settings) for a fixed wall time: the image error of all views against time, like the
-    paper's teaser snapshots (130 s / 720 s on its own scene and GPU, context only)."""
+    paper's teaser snapshots (130 s / 720 s on its own scene and GPU, context only).  With
+    --control catmull_clark the rendered surface is two Catmull-Clark levels of a 2,048-triangle
+    control sphere (47,616 triangles, the teaser's construction) and the parameters optimised are
+    the control vertices (refined every iteration; their sums through R^T) and the textures."""
     import torch
 
     import synth
-    from paper_2404_09758_gb300 import STEP_ADAM, Scene
+    from paper_2404_09758_gb300 import STEP_ADAM, ControlMesh, Scene
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = synth.config_autograd()
+    control = args.control == "catmull_clark"
+    if control:
+        sc, ctl, R, _ = synth.config_control()
+    else:
+        sc = synth.config_autograd()
     views = list(range(sc.n_views))
     pairs = sc.pairs_per_view
     ts = Scene.from_arrays(synth.target_scene(sc), max_pairs_per_call=pairs)
@@ -617,20 +624,36 @@ def run_converge(args):
     del ts
     g = Scene.from_arrays(sc, targets=targets, max_pairs_per_call=pairs)
     grad, counts = g.new_grad_buffers()
-    m = torch.zeros(g.n_params, device=dev)
-    v = torch.zeros(g.n_params, device=dev)
     lr_tex = [t[1] for t in g.textures]
     st = torch.cuda.Stream(device=dev)
+    if control:
+        cm = ControlMesh(g, ctl, R)
+        opt = cm.params  # the control vertices and the shared textures
+        grad_c, counts_c = cm.new_grad_buffers()
+    else:
+        opt = g
+    m = torch.zeros(opt.n_params, device=dev)
+    v = torch.zeros(opt.n_params, device=dev)
 
     def image_error():
         with torch.cuda.stream(st):
+            if control:
+                cm.refine(stream=st)
             e = g.loss(views, stream=st)
         st.synchronize()
         return float(e.sum().item())
 
     def iteration(it, t):
+        if not control:
+            g.estimate_grad(1, it, views, pairs, grad, counts, stream=st)
+            g.step(STEP_ADAM, grad, counts, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+            return
+        cm.refine(stream=st)
         g.estimate_grad(1, it, views, pairs, grad, counts, stream=st)
-        g.step(STEP_ADAM, grad, counts, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+        cm.control_sums(grad, grad_c, stream=st)
+        grad.zero_()
+        counts.zero_()
+        opt.step(STEP_ADAM, grad_c, counts_c, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
 
     e0 = image_error()
     # eager launches: an iteration is ~12 launches against a GPU time of tens of milliseconds, and
@@ -657,11 +680,13 @@ def run_converge(args):
             "unit": "sum of squared errors, all views", "n_gpus": 1, "steps": n_iter, "warmup": 0,
             "ms_per_step": 1000.0 * curve[-1][0] / n_iter, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "subdiv32k_rgba1024_nrm1024_r1024_16views_x_16pairs_adam",
+            "config": {"workload": sc.name + "_16views_x_16pairs_adam" + ("_control_mesh" if control else ""),
+                       "triangles": int(len(sc.pos_idx)), "params": int(opt.n_params),
                        "seconds": args.seconds, "graph": "none (eager; the error is measured between iterations)"},
             "initial_error": e0, "curve": curve, "reduction": curve[-1][1] / e0,
             # per iteration: 4 binning and pruning kernels, the vertex pass, the two estimators, the step
-            "gpu_launches": 8 * n_iter}
+            # (+ the two refine products of the control mesh)
+            "gpu_launches": (10 if control else 8) * n_iter}
     print(json.dumps(line), flush=True)
 
 
@@ -672,6 +697,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--seconds", type=float, default=60.0, help="wall time of --workload converge")
+    ap.add_argument("--control", choices=["none", "catmull_clark"], default="none",
+                    help="--workload converge: optimise a Catmull-Clark control mesh instead of the surface")
     ap.add_argument("--workload", choices=["batched", "uneven", "scale", "full_image", "converge"], default="batched",
                     help="batched: the headline configuration; uneven: 32 assets in one batched call; "
                          "scale: 1M triangles, GGX, 2048^2; full_image: Eq. 4's whole-image estimator on "

@@ -189,8 +189,8 @@ int sge_estimate_grad_full_image(sge_scene *scene, uint64_t seed, uint32_t iter,
                                  int32_t n_views, int32_t pairs_per_view, float *grad_sums, uint32_t *counts,
                                  float *image_df, sge_stream_t stream);
 
-/* Control-mesh optimisation through a subdivision (linear first; the paper tessellates a
- * Catmull-Clark surface on the fly and credits each tessellated triangle to its control mesh,
+/* Control-mesh optimisation through a subdivision (linear or Catmull-Clark; the paper tessellates
+ * a Catmull-Clark surface on the fly and credits each tessellated triangle to its control mesh,
  * Section 6.3): the subdivided mesh's vertices are a fixed linear map of the control vertices,
  * fine = R control, so the control vertices' gradient is R^T times the fine vertices' one, and
  * R^T applied to the sums of sge_estimate_grad (the first 3 V_fine entries) gives sums whose

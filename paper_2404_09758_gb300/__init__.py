@@ -19,7 +19,7 @@ from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_TEXTURES, MAX_VIEWS_PER_
                    STEP_SGD, STEP_SGD_MEAN, SGEError)
 from ._build import build
 
-__all__ = ["Scene", "Batch", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
+__all__ = ["Scene", "Batch", "ControlMesh", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
            "STEP_SGD_MEAN", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
 
 
@@ -303,6 +303,68 @@ def refine(matrix, x, y=None, accumulate: bool = False, stream=None):
     _abi.check(_abi.load().sge_refine(_ptr(row_ptr), _ptr(col), _ptr(w), n_rows, _ptr(x), _ptr(y),
                                       1 if accumulate else 0, _stream_ptr(stream)))
     return y
+
+
+def csr_tensors(matrix, device):
+    """A scipy sparse matrix as the CSR triple refine takes (row_ptr, col int32; w float32)."""
+    torch = _torch()
+    M = matrix.tocsr()
+    M.sort_indices()
+    return (torch.tensor(M.indptr.astype("int32"), device=device),
+            torch.tensor(M.indices.astype("int32"), device=device),
+            torch.tensor(M.data.astype("float32"), device=device))
+
+
+class ControlMesh:
+    """A control mesh behind a subdivided scene (Section 6.3: the rendered surface is the
+    control mesh's subdivision; the parameters optimised are the control vertices and the
+    textures).  R is the fixed refine matrix (scipy sparse, fine vertices x control vertices,
+    e.g. synth.subdivide_catmull_clark's): fine = R control, so the control coordinates' sums
+    are R^T times the fine vertices' sums.  `params` is a scene over the control vertices and
+    the fine scene's own texture tensors; its step updates both in place.
+
+        cm = ControlMesh(fine_scene, control, R)       # control: positions, pos_idx, uvs, uv_idx
+        cm.refine()                                    # fine positions = R control
+        fine_scene.estimate_grad(seed, it, views, pairs, g_fine, c_fine)
+        cm.control_sums(g_fine, g_ctl)                 # positions through R^T, texture sums copied
+        cm.params.step(STEP_ADAM, g_ctl, c_ctl, n_pairs, ...)
+    """
+
+    def __init__(self, fine: Scene, control, R):
+        if R.shape != (int(fine.positions.shape[0]), int(len(control.positions))):
+            raise ValueError(f"refine matrix {R.shape} does not map {len(control.positions)} control "
+                             f"vertices to the scene's {int(fine.positions.shape[0])}")
+        self.fine = fine
+        self.R = csr_tensors(R, fine.device)
+        self.RT = csr_tensors(R.T, fine.device)
+        d = fine._desc
+        self.params = Scene(control.positions, control.pos_idx, control.uvs, control.uv_idx,
+                            [(t, eps, role) for t, eps, role in fine.textures], d.eps_pos, fine.mvp,
+                            fine.cam_pos, fine.width, fine.height, targets=fine.targets, near=d.near_w,
+                            shading=d.shading, light_dir=tuple(d.light_dir), light_rgb=tuple(d.light_rgb),
+                            ambient=d.ambient, background=tuple(d.background), device=fine.device)
+        self.positions = self.params.positions
+        self.n_fine = 3 * int(fine.positions.shape[0])
+        self.n_control = 3 * int(self.positions.shape[0])
+        if self.params.n_params - self.n_control != fine.n_params - self.n_fine:
+            raise RuntimeError("control and fine scenes disagree on the texture parameters")
+
+    def new_grad_buffers(self):
+        return self.params.new_grad_buffers()
+
+    def refine(self, stream=None) -> None:
+        """The fine scene's positions from the control positions (sge_refine with R)."""
+        refine(self.R, self.positions, self.fine.positions, stream=stream)
+
+    def control_sums(self, grad_fine, grad_control, stream=None) -> None:
+        """grad_control = the control parameters' sums: R^T on the position block, the texture
+        block copied (the textures are the same parameters in both scenes)."""
+        torch = _torch()
+        refine(self.RT, grad_fine[:self.n_fine].view(-1, 3), grad_control[:self.n_control].view(-1, 3),
+               stream=stream)
+        s = torch.cuda.current_stream(self.fine.device) if stream is None else stream
+        with torch.cuda.stream(s):
+            grad_control[self.n_control:].copy_(grad_fine[self.n_fine:], non_blocking=True)
 
 
 class Batch:

@@ -152,6 +152,138 @@ def linear_refine_matrix(mesh: Mesh, levels: int = 1):
     return R
 
 
+def catmull_clark_faces(n_vertices: int, faces, levels: int = 1):
+    """Catmull-Clark subdivision (Catmull & Clark 1978) of a closed polygon mesh, as a matrix.
+
+    faces: polygons (sequences of vertex indices, counter-clockwise seen from outside); every
+    edge must be shared by exactly two faces.  Returns (R, quads): R is a scipy CSR matrix
+    (fine vertices x control vertices) with the subdivided positions = R @ control positions,
+    and quads the subdivided faces, [F, 4] int32.  Each level maps
+      face point   = mean of the face's corners,
+      edge point   = (both ends + the two adjacent face points) / 4,
+      vertex point = (Q + 2 M + (n - 3) P) / n,
+    with n the vertex's valence, Q the mean of its adjacent face points and M the mean of its
+    incident edges' midpoints.  Fine vertices are numbered vertex points, then edge points (in
+    order of first appearance), then face points; each face of k corners becomes k quads
+    (corner, edge point, face point, edge point)."""
+    import scipy.sparse as sp
+    R = sp.identity(n_vertices, format="csr", dtype=np.float64)
+    faces = [tuple(int(v) for v in f) for f in faces]
+    for _ in range(levels):
+        n = R.shape[0]
+        edge_id, edge_ends, edge_faces = {}, [], []
+        for fi, f in enumerate(faces):
+            k = len(f)
+            for c in range(k):
+                a, b = f[c], f[(c + 1) % k]
+                key = (a, b) if a < b else (b, a)
+                if key not in edge_id:
+                    edge_id[key] = len(edge_ends)
+                    edge_ends.append(key)
+                    edge_faces.append([])
+                edge_faces[edge_id[key]].append(fi)
+        if any(len(fs) != 2 for fs in edge_faces):
+            raise ValueError("Catmull-Clark subdivision here takes closed manifold meshes only")
+        ne, nf = len(edge_ends), len(faces)
+        rows, cols, vals = [], [], []
+
+        def put(r, c, w):
+            rows.append(r)
+            cols.append(c)
+            vals.append(w)
+
+        # face points: rows n + ne + fi
+        for fi, f in enumerate(faces):
+            for v in f:
+                put(n + ne + fi, v, 1.0 / len(f))
+
+        def put_face_point(r, fi, w):
+            f = faces[fi]
+            for v in f:
+                put(r, v, w / len(f))
+
+        # edge points
+        for e, (a, b) in enumerate(edge_ends):
+            put(n + e, a, 0.25)
+            put(n + e, b, 0.25)
+            for fi in edge_faces[e]:
+                put_face_point(n + e, fi, 0.25)
+        # vertex points: Q / n + 2 M / n + (n - 3) / n P, with M = mean of (P + other end) / 2
+        inc_edges = [[] for _ in range(n)]
+        for e, (a, b) in enumerate(edge_ends):
+            inc_edges[a].append(e)
+            inc_edges[b].append(e)
+        inc_faces = [[] for _ in range(n)]
+        for fi, f in enumerate(faces):
+            for v in f:
+                inc_faces[v].append(fi)
+        for v in range(n):
+            val = len(inc_edges[v])
+            if val == 0:
+                put(v, v, 1.0)  # a vertex no face uses stays where it is
+                continue
+            for fi in inc_faces[v]:
+                put_face_point(v, fi, 1.0 / (len(inc_faces[v]) * val))
+            for e in inc_edges[v]:
+                a, b = edge_ends[e]
+                put(v, a, 1.0 / (val * val))
+                put(v, b, 1.0 / (val * val))
+            put(v, v, (val - 3.0) / val)
+        M = sp.csr_matrix((vals, (rows, cols)), shape=(n + ne + nf, n))  # duplicates are summed
+        R = (M @ R).tocsr()
+        quads = []
+        for fi, f in enumerate(faces):
+            k = len(f)
+            for c in range(k):
+                a, b, p = f[c], f[(c + 1) % k], f[c - 1]
+                e_next = edge_id[(a, b) if a < b else (b, a)]
+                e_prev = edge_id[(p, a) if p < a else (a, p)]
+                quads.append((a, n + e_next, n + ne + fi, n + e_prev))
+        faces = quads
+    R.sum_duplicates()
+    R.sort_indices()
+    return R, np.asarray(faces, np.int32).reshape(-1, 4)
+
+
+def subdivide_catmull_clark(mesh: Mesh, levels: int = 1):
+    """Catmull-Clark subdivision of a closed triangle mesh (zero-area triangles, such as a UV
+    sphere's pole slivers, are dropped from the control mesh first), returned as a triangle mesh
+    and its refine matrix: (fine Mesh, R) with fine.positions = R @ mesh.positions (rounded to
+    float32).  Each fine quad (a, b, c, d) is split into (a, b, c) and (a, c, d).  UVs are
+    subdivided linearly per face (face point UV = mean of the face's corner UVs, edge point UV
+    = midpoint of the edge's UVs on that face), so texture seams stay seams."""
+    keep = ((mesh.pos_idx[:, 0] != mesh.pos_idx[:, 1]) & (mesh.pos_idx[:, 1] != mesh.pos_idx[:, 2])
+            & (mesh.pos_idx[:, 2] != mesh.pos_idx[:, 0]))
+    faces = mesh.pos_idx[keep].tolist()
+    uv_faces = mesh.uv_idx[keep].tolist()
+    R, quads = catmull_clark_faces(len(mesh.positions), faces, levels)
+    # the same face order and corner order as catmull_clark_faces, on the UV indices
+    uvs = [tuple(u) for u in mesh.uvs.astype(np.float64)]
+    for _ in range(levels):
+        mids, new_faces = {}, []
+
+        def mid(a, b):
+            key = (a, b) if a < b else (b, a)
+            if key not in mids:
+                mids[key] = len(uvs)
+                uvs.append(tuple(0.5 * (np.asarray(uvs[a]) + np.asarray(uvs[b]))))
+            return mids[key]
+
+        for f in uv_faces:
+            k = len(f)
+            centre = len(uvs)
+            uvs.append(tuple(np.mean([uvs[t] for t in f], axis=0)))
+            for c in range(k):
+                a, b, p = f[c], f[(c + 1) % k], f[c - 1]
+                new_faces.append((a, mid(a, b), centre, mid(p, a)))
+        uv_faces = new_faces
+    uq = np.asarray(uv_faces, np.int32).reshape(-1, 4)
+    tri = lambda q: np.stack([q[:, [0, 1, 2]], q[:, [0, 2, 3]]], axis=1).reshape(-1, 3)
+    pos = (R @ mesh.positions.astype(np.float64)).astype(np.float32)
+    fine = Mesh(pos, tri(quads).astype(np.int32), np.asarray(uvs, np.float32), tri(uq).astype(np.int32))
+    return fine, R
+
+
 def radial_displace(positions: np.ndarray, seed: int, amplitude: float = 0.05,
                     n_terms: int = 4) -> np.ndarray:
     """Seeded low-frequency radial displacement: p <- p * (1 + a * g(p)), |g| <= 1."""
@@ -369,6 +501,24 @@ def config_autograd(n_views: int = 16, pairs: int = 16, render: int = 1024,
                  light_dir=tuple(float(x) for x in ld), ambient=0.1,
                  target_positions=tgt_pos, target_textures=[tgt_alb, tgt_nrm],
                  pairs_per_view=pairs)
+
+
+def config_control(n_views: int = 16, pairs: int = 16, render: int = 1024, tex: int = 1024):
+    """The autograd configuration as the paper's teaser builds it (Section 6.3): a 2,048-triangle
+    control sphere (1,984 after its pole slivers are dropped) under two Catmull-Clark levels
+    (47,616 triangles), the control vertices displaced; RGBA albedo + tangent-space normal map;
+    Lambert with one directional light.  Returns (scene, control Mesh, R, target control
+    positions), the scene's positions R @ the control positions."""
+    ctl = uv_sphere(32, 32)
+    fine, R = subdivide_catmull_clark(ctl, 2)
+    ctl0 = radial_displace(ctl.positions, seed=0, amplitude=0.05)
+    tgt_ctl = radial_displace(ctl.positions, seed=1, amplitude=0.08)
+    lift = lambda p: (R @ p.astype(np.float64)).astype(np.float32)
+    base = config_autograd(n_views, pairs, render, tex)
+    sc = dataclasses.replace(base, name=f"catmullclark48k_rgba{tex}_nrm{tex}_r{render}", positions=lift(ctl0),
+                             pos_idx=fine.pos_idx, uvs=fine.uvs, uv_idx=fine.uv_idx,
+                             target_positions=lift(tgt_ctl))
+    return sc, dataclasses.replace(ctl, positions=ctl0), R, tgt_ctl
 
 
 def config_uneven(n_assets: int = 32, n_views: int = 4, pairs: int = 8, render: int = 512,
