@@ -75,6 +75,9 @@ def lib():
             L.or_n_params.restype, L.or_n_params.argtypes = I64, [P]
             L.oracle_render.restype = I32
             L.oracle_render.argtypes = [P, I32, U64, U32, U32, I32, P, P, P]
+            L.oracle_render_deep.restype = I32
+            L.oracle_render_deep.argtypes = [P, I32, U64, U32, U32, I32, P, P]
+            L.oracle_layers.restype, L.oracle_layers.argtypes = I32, []
             L.oracle_estimate.restype = I32
             L.oracle_estimate.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P, P, P]
             L.oracle_loss.restype, L.oracle_loss.argtypes = C.c_double, [P, I32]
@@ -185,6 +188,19 @@ def render(osc: OracleScene, view: int, seed: int = 0, it: int = 0, pair: int = 
     if rc:
         raise ValueError(f"oracle_render failed ({rc})")
     return keys, uv, rgb
+
+
+def render_deep(osc: OracleScene, view: int, seed: int = 0, it: int = 0, pair: int = 0, side: int = 0,
+                with_rgb: bool = True):
+    """Deep ID buffer [LAYERS,H,W] uint64 (ascending keys, ~0 = empty; Section 4.4, transparent
+    geometry) and, for a transparent scene, its front-to-back composite [H,W,3] float64."""
+    H, W = osc.height, osc.width
+    deep = np.empty((lib().oracle_layers(), H, W), np.uint64)
+    rgb = np.empty((H, W, 3), np.float64) if with_rgb else None
+    rc = lib().oracle_render_deep(osc.ref, view, seed, it, pair, side, _ptr(deep), _ptr(rgb) if with_rgb else None)
+    if rc:
+        raise ValueError(f"oracle_render_deep failed ({rc})")
+    return deep, rgb
 
 
 def estimate(osc: OracleScene, seed: int, it: int, view_ids, pairs: int, per_pixel: bool = False):

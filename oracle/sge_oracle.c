@@ -27,7 +27,8 @@
 #define OR_MAX_TEX 8
 
 enum { OR_ROLE_ALBEDO = 0, OR_ROLE_NORMAL = 1, OR_ROLE_ROUGHNESS = 2, OR_ROLE_METALLIC = 3 };
-enum { OR_UNLIT = 0, OR_LAMBERT = 1, OR_GGX = 2 };
+enum { OR_UNLIT = 0, OR_LAMBERT = 1, OR_GGX = 2, OR_TRANSPARENT = 3 };
+#define OR_LAYERS 4 /* fragments a pixel's deep ID buffer keeps (transparent geometry) */
 enum { OR_FOOT_BILINEAR = 0, OR_FOOT_NEAREST = 1 };
 
 /* Everything describing one scene; mirrors the ctypes Structure in __init__.py. */
@@ -267,6 +268,27 @@ static int64_t or_floordiv(int64_t a, int64_t b)
     return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
 }
 
+/* Pixels whose centres (256 px + 128 in fixed point) lie in the triangle's bounding box,
+ * clipped to the image: [pxa, pxb] x [pya, pyb].                                */
+static void or_pixel_box(const or_tri *t, int W, int H, int64_t *pxa, int64_t *pxb, int64_t *pya, int64_t *pyb)
+{
+    int32_t x0 = t->X[0], x1 = t->X[0], y0 = t->Y[0], y1 = t->Y[0];
+    for (int k = 1; k < 3; ++k) {
+        if (t->X[k] < x0) x0 = t->X[k];
+        if (t->X[k] > x1) x1 = t->X[k];
+        if (t->Y[k] < y0) y0 = t->Y[k];
+        if (t->Y[k] > y1) y1 = t->Y[k];
+    }
+    *pxa = -or_floordiv(-((int64_t)x0 - 128), 256);
+    *pxb = or_floordiv((int64_t)x1 - 128, 256);
+    *pya = -or_floordiv(-((int64_t)y0 - 128), 256);
+    *pyb = or_floordiv((int64_t)y1 - 128, 256);
+    if (*pxa < 0) *pxa = 0;
+    if (*pya < 0) *pya = 0;
+    if (*pxb > W - 1) *pxb = W - 1;
+    if (*pyb > H - 1) *pyb = H - 1;
+}
+
 /* ------------------------------------------------------------------ rasterizer R
  * Rasterize one (perturbed) scene into a depth|ID buffer (Section 4.4, opaque
  * geometry): for every triangle and every pixel centre of its bounding box,
@@ -279,26 +301,48 @@ static void or_raster(const or_scene *s, int view, uint64_t key, int side, uint6
         or_tri t;
         or_setup(s, view, key, side, tri, &t);
         if (!t.ok) continue;
-        int32_t x0 = t.X[0], x1 = t.X[0], y0 = t.Y[0], y1 = t.Y[0];
-        for (int k = 1; k < 3; ++k) {
-            if (t.X[k] < x0) x0 = t.X[k];
-            if (t.X[k] > x1) x1 = t.X[k];
-            if (t.Y[k] < y0) y0 = t.Y[k];
-            if (t.Y[k] > y1) y1 = t.Y[k];
-        }
-        /* pixel px has its centre at 256 px + 128 */
-        int64_t pxa = -or_floordiv(-((int64_t)x0 - 128), 256), pxb = or_floordiv((int64_t)x1 - 128, 256);
-        int64_t pya = -or_floordiv(-((int64_t)y0 - 128), 256), pyb = or_floordiv((int64_t)y1 - 128, 256);
-        if (pxa < 0) pxa = 0;
-        if (pya < 0) pya = 0;
-        if (pxb > W - 1) pxb = W - 1;
-        if (pyb > H - 1) pyb = H - 1;
+        int64_t pxa, pxb, pya, pyb;
+        or_pixel_box(&t, W, H, &pxa, &pxb, &pya, &pyb);
         for (int64_t py = pya; py <= pyb; ++py)
             for (int64_t px = pxa; px <= pxb; ++px) {
                 int64_t e[3];
                 if (!or_inside(&t, 256 * px + 128, 256 * py + 128, e)) continue;
                 uint64_t k = or_key(&t, e, tri);
                 if (k < keys[py * W + px]) keys[py * W + px] = k;
+            }
+    }
+}
+
+/* ------------------------------------------------------------------ deep rasterizer (transparent geometry)
+ * Section 4.4, transparent geometry: the raster pass outputs a deep ID buffer, the
+ * front-to-back list of the triangles a pixel sees.  Here every pixel keeps the
+ * OR_LAYERS smallest keys (depth bits, triangle id) among the triangles covering its
+ * centre, in ascending order; unused slots hold ~0.  deep is [OR_LAYERS][H][W].   */
+static void or_raster_deep(const or_scene *s, int view, uint64_t key, int side, uint64_t *deep)
+{
+    int W = s->width, H = s->height;
+    int64_t npx = (int64_t)W * H;
+    for (int64_t i = 0; i < OR_LAYERS * npx; ++i) deep[i] = ~0ULL;
+    for (int tri = 0; tri < s->n_triangles; ++tri) {
+        or_tri t;
+        or_setup(s, view, key, side, tri, &t);
+        if (!t.ok) continue;
+        int64_t pxa, pxb, pya, pyb;
+        or_pixel_box(&t, W, H, &pxa, &pxb, &pya, &pyb);
+        for (int64_t py = pya; py <= pyb; ++py)
+            for (int64_t px = pxa; px <= pxb; ++px) {
+                int64_t e[3];
+                if (!or_inside(&t, 256 * px + 128, 256 * py + 128, e)) continue;
+                /* insert into the pixel's ascending list; the largest key falls off the end */
+                uint64_t k = or_key(&t, e, tri);
+                for (int j = 0; j < OR_LAYERS; ++j) {
+                    uint64_t *slot = deep + j * npx + py * W + px;
+                    if (k < *slot) {
+                        uint64_t tmp = *slot;
+                        *slot = k;
+                        k = tmp;
+                    }
+                }
             }
     }
 }
@@ -389,7 +433,7 @@ static int or_reads(const or_scene *s, int k)
 {
     int r = s->tex_role[k];
     if (or_find_role(s, r) != k) return 0; /* only the first texture of a role is read */
-    if (s->shading == OR_UNLIT) return r == OR_ROLE_ALBEDO;
+    if (s->shading == OR_UNLIT || s->shading == OR_TRANSPARENT) return r == OR_ROLE_ALBEDO;
     if (s->shading == OR_LAMBERT) return r == OR_ROLE_ALBEDO || r == OR_ROLE_NORMAL;
     return 1;
 }
@@ -494,16 +538,95 @@ static void or_shade(const or_scene *s, int view, const or_tri *t, int tri, cons
     }
 }
 
+/* ------------------------------------------------------------------ transparent compositing
+ * Section 4.4, transparent geometry: front-to-back rendering of the pixel's deep list.
+ * Listed fragment j is unlit, with colour rgb_j and opacity a_j = clamp(alpha, 0, 1)
+ * from the RGBA albedo sampled (bilinear) at its UV; with transmittance T_0 = 1,
+ *   C = sum_j T_j a_j rgb_j + T_n background,   T_{j+1} = T_j (1 - a_j).
+ * Fragments beyond the list are not drawn.  Returns the number n of listed
+ * fragments; tris[j] and uvs[j] are fragment j's triangle and UV.               */
+static int or_composite(const or_scene *s, int view, uint64_t key, int side, const uint64_t *deep, int64_t npx,
+                        int64_t px, int64_t py, double rgb[3], int tris[OR_LAYERS], or_uvs uvs[OR_LAYERS])
+{
+    int ka = or_find_role(s, OR_ROLE_ALBEDO);
+    int64_t p = py * s->width + px;
+    double T = 1.0;
+    int n = 0;
+    for (int c = 0; c < 3; ++c) rgb[c] = 0.0;
+    for (int j = 0; j < OR_LAYERS && ka >= 0; ++j) {
+        uint64_t k = deep[j * npx + p];
+        if (k == ~0ULL) break;
+        int tri = (int)(k & 0xFFFFFFFFu);
+        or_tri t;
+        or_setup(s, view, key, side, tri, &t);
+        uvs[j] = or_uv(s, &t, tri, 256 * px + 128, 256 * py + 128);
+        or_foot f;
+        or_bilinear(uvs[j].u, uvs[j].v, s->tex_w[ka], s->tex_h[ka], &f);
+        double a[4];
+        or_sample(s, ka, &f, key, side, a);
+        double al = a[3] < 0.0 ? 0.0 : (a[3] > 1.0 ? 1.0 : a[3]);
+        for (int c = 0; c < 3; ++c) rgb[c] += T * al * a[c];
+        T *= 1.0 - al;
+        tris[j] = tri;
+        n++;
+    }
+    for (int c = 0; c < 3; ++c) rgb[c] += T * s->background[c];
+    return n;
+}
+
+/* ------------------------------------------------------------------ public: deep render
+ * The deep ID buffer of one render (see or_raster_deep), [OR_LAYERS][H][W], and with
+ * rgb != NULL (transparent scenes only) its front-to-back composite [H][W][3].    */
+int oracle_render_deep(const or_scene *s, int view, uint64_t seed, uint32_t iter, uint32_t pair, int side,
+                       uint64_t *deep, double *rgb)
+{
+    if (view < 0 || view >= s->n_views || side < -1 || side > 1) return 1;
+    if (rgb && s->shading != OR_TRANSPARENT) return 1;
+    uint64_t key = or_pair_key(seed, iter, (uint32_t)view, pair);
+    int64_t npx = (int64_t)s->width * s->height;
+    or_raster_deep(s, view, key, side, deep);
+    if (rgb)
+        for (int64_t py = 0; py < s->height; ++py)
+            for (int64_t px = 0; px < s->width; ++px) {
+                int tris[OR_LAYERS];
+                or_uvs uvs[OR_LAYERS];
+                or_composite(s, view, key, side, deep, npx, px, py, rgb + 3 * (py * s->width + px), tris, uvs);
+            }
+    return 0;
+}
+
+int oracle_layers(void) { return OR_LAYERS; }
+
 /* ------------------------------------------------------------------ public: render
  * One render of the scene theta + side * s * eps (side -1, 0 or +1) for the
  * estimate keyed by (seed, iter, view, pair): depth|ID keys, UV buffer (0 on
- * background) and colour (the background colour on background).              */
+ * background) and colour (the background colour on background).  A transparent
+ * scene gives its front fragment's key and UV and the composite colour.      */
 int oracle_render(const or_scene *s, int view, uint64_t seed, uint32_t iter, uint32_t pair, int side,
                   uint64_t *keys, float *uv, double *rgb)
 {
     if (view < 0 || view >= s->n_views || side < -1 || side > 1) return 1;
     uint64_t key = or_pair_key(seed, iter, (uint32_t)view, pair);
     int W = s->width, H = s->height;
+    if (s->shading == OR_TRANSPARENT) {
+        int64_t npx = (int64_t)W * H;
+        uint64_t *deep = malloc(sizeof(uint64_t) * OR_LAYERS * npx);
+        if (!deep) return 2;
+        or_raster_deep(s, view, key, side, deep);
+        for (int64_t py = 0; py < H; ++py)
+            for (int64_t px = 0; px < W; ++px) {
+                int64_t p = py * W + px;
+                int tris[OR_LAYERS];
+                or_uvs uvs[OR_LAYERS];
+                double col[3];
+                int n = or_composite(s, view, key, side, deep, npx, px, py, col, tris, uvs);
+                keys[p] = deep[p];
+                if (uv) { uv[2 * p] = n ? uvs[0].u : 0.0f; uv[2 * p + 1] = n ? uvs[0].v : 0.0f; }
+                if (rgb) for (int c = 0; c < 3; ++c) rgb[3 * p + c] = col[c];
+            }
+        free(deep);
+        return 0;
+    }
     or_raster(s, view, key, side, keys);
     for (int64_t py = 0; py < H; ++py)
         for (int64_t px = 0; px < W; ++px) {
@@ -529,7 +652,9 @@ int oracle_render(const or_scene *s, int view, uint64_t seed, uint32_t iter, uin
  * estimate renders two scenes; the pixel credits the union over both sides of
  * (a) the three welded vertices of the visible triangle, x, y and z each, and
  * (b) the texels of the footprint of every texture the shading reads, all
- * channels.  Each parameter appears once per pixel.                           */
+ * channels.  Each parameter appears once per pixel.  In a transparent scene the
+ * pixel credits this for every fragment of each side's deep list (Section 4.4: G
+ * walks the list and treats each listed triangle as the opaque case does).     */
 #define OR_MAX_CONTRIB 1024
 
 typedef struct { int n; int64_t idx[OR_MAX_CONTRIB]; int group[OR_MAX_CONTRIB]; } or_set;
@@ -571,14 +696,19 @@ static void or_contributors(const or_scene *s, int tri, const or_uvs *uv, or_set
  * loss[j] = sum over pixels of the mean over pairs of (f+ + f-)/2.
  * Optional per-pixel outputs, each [n_views][pairs][H][W]: delta_f = f+ - f-,
  * fmax = max(f+, f-), cond = sum_c (|a_c| + |b_c|)(|I+_c| + |I-_c| + 2|I_c|) with
- * a = I+ - I-, b = I+ + I- - 2 I (the size of the terms in f+ - f-).           */
+ * a = I+ - I-, b = I+ + I- - 2 I (the size of the terms in f+ - f-).
+ * Transparent scenes render each side through its deep list (or_raster_deep,
+ * or_composite).                                                                */
 int oracle_estimate(const or_scene *s, uint64_t seed, uint32_t iter, const int32_t *view_ids,
                     int n_views, int pairs, double *S, uint64_t *C, double *loss,
                     double *delta_f, double *fmax, double *cond)
 {
     int W = s->width, H = s->height;
     int64_t npx = (int64_t)W * H;
-    uint64_t *kp = malloc(sizeof(uint64_t) * npx), *km = malloc(sizeof(uint64_t) * npx);
+    /* transparent scenes keep a deep list per pixel (Section 4.4) and credit every listed fragment */
+    int deep = s->shading == OR_TRANSPARENT;
+    int64_t nbuf = deep ? OR_LAYERS * npx : npx;
+    uint64_t *kp = malloc(sizeof(uint64_t) * nbuf), *km = malloc(sizeof(uint64_t) * nbuf);
     or_set *K = malloc(sizeof(or_set));
     if (!kp || !km || !K) { free(kp); free(km); free(K); return 2; }
     for (int j = 0; j < n_views; ++j) {
@@ -588,28 +718,38 @@ int oracle_estimate(const or_scene *s, uint64_t seed, uint32_t iter, const int32
         if (loss) loss[j] = 0.0;
         for (int n = 0; n < pairs; ++n) {
             uint64_t key = or_pair_key(seed, iter, (uint32_t)view, (uint32_t)n);
-            or_raster(s, view, key, +1, kp);
-            or_raster(s, view, key, -1, km);
+            if (deep) {
+                or_raster_deep(s, view, key, +1, kp);
+                or_raster_deep(s, view, key, -1, km);
+            } else {
+                or_raster(s, view, key, +1, kp);
+                or_raster(s, view, key, -1, km);
+            }
             for (int64_t py = 0; py < H; ++py)
                 for (int64_t px = 0; px < W; ++px) {
                     int64_t p = py * W + px;
                     double col[2][3];
-                    or_uvs uvp[2];
-                    int tris[2];
+                    or_uvs uvl[2][OR_LAYERS];
+                    int tris[2][OR_LAYERS], nl[2];
                     K->n = 0;
                     for (int sd = 0; sd < 2; ++sd) {
-                        uint64_t k = sd == 0 ? kp[p] : km[p];
+                        const uint64_t *buf = sd == 0 ? kp : km;
                         int side = sd == 0 ? +1 : -1;
-                        tris[sd] = -1;
-                        if (k == ~0ULL) {
+                        if (deep) {
+                            nl[sd] = or_composite(s, view, key, side, buf, npx, px, py, col[sd], tris[sd], uvl[sd]);
+                            continue;
+                        }
+                        nl[sd] = 0;
+                        if (buf[p] == ~0ULL) {
                             for (int c = 0; c < 3; ++c) col[sd][c] = s->background[c];
                             continue;
                         }
-                        tris[sd] = (int)(k & 0xFFFFFFFFu);
+                        nl[sd] = 1;
+                        tris[sd][0] = (int)(buf[p] & 0xFFFFFFFFu);
                         or_tri t;
-                        or_setup(s, view, key, side, tris[sd], &t);
-                        uvp[sd] = or_uv(s, &t, tris[sd], 256 * px + 128, 256 * py + 128);
-                        or_shade(s, view, &t, tris[sd], &uvp[sd], key, side, col[sd]);
+                        or_setup(s, view, key, side, tris[sd][0], &t);
+                        uvl[sd][0] = or_uv(s, &t, tris[sd][0], 256 * px + 128, 256 * py + 128);
+                        or_shade(s, view, &t, tris[sd][0], &uvl[sd][0], key, side, col[sd]);
                     }
                     double fp = 0.0, fm = 0.0, cd = 0.0;
                     for (int c = 0; c < 3; ++c) {
@@ -626,7 +766,7 @@ int oracle_estimate(const or_scene *s, uint64_t seed, uint32_t iter, const int32
                     if (cond) cond[o] = cd;
                     if (loss) loss[j] += 0.5 * (fp + fm) / pairs;
                     for (int sd = 0; sd < 2; ++sd)
-                        if (tris[sd] >= 0) or_contributors(s, tris[sd], &uvp[sd], K);
+                        for (int j = 0; j < nl[sd]; ++j) or_contributors(s, tris[sd][j], &uvl[sd][j], K);
                     for (int q = 0; q < K->n; ++q) {
                         int64_t i = K->idx[q];
                         S[i] += df * or_sign(key, (uint64_t)i);
@@ -655,6 +795,7 @@ int oracle_estimate_full_image(const or_scene *s, uint64_t seed, uint32_t iter, 
 {
     int W = s->width, H = s->height;
     int64_t npx = (int64_t)W * H, d = or_n_params(s);
+    if (s->shading == OR_TRANSPARENT) return 3; /* the whole-image form is written for opaque scenes */
     uint64_t *kp = malloc(sizeof(uint64_t) * npx), *km = malloc(sizeof(uint64_t) * npx);
     if (!kp || !km) { free(kp); free(km); return 2; }
     for (int j = 0; j < n_views; ++j) {

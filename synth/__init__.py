@@ -28,6 +28,7 @@ ROLE_METALLIC = 3
 SHADE_UNLIT = 0
 SHADE_LAMBERT = 1
 SHADE_GGX = 2
+SHADE_TRANSPARENT = 3  # unlit RGBA fragments composited front to back (deep ID buffer)
 
 
 # --------------------------------------------------------------------------- meshes
@@ -519,6 +520,46 @@ def config_control(n_views: int = 16, pairs: int = 16, render: int = 1024, tex: 
                              pos_idx=fine.pos_idx, uvs=fine.uvs, uv_idx=fine.uv_idx,
                              target_positions=lift(tgt_ctl))
     return sc, dataclasses.replace(ctl, positions=ctl0), R, tgt_ctl
+
+
+def merge_meshes(meshes: List[Mesh], offsets) -> Mesh:
+    """One mesh from several, mesh k translated by offsets[k]; indices renumbered."""
+    pos, pidx, uvs, tidx = [], [], [], []
+    nv = nt = 0
+    for m, off in zip(meshes, offsets):
+        pos.append(m.positions + np.asarray(off, np.float32))
+        pidx.append(m.pos_idx + nv)
+        uvs.append(m.uvs)
+        tidx.append(m.uv_idx + nt)
+        nv += len(m.positions)
+        nt += len(m.uvs)
+    return Mesh(np.concatenate(pos).astype(np.float32), np.concatenate(pidx).astype(np.int32),
+                np.concatenate(uvs).astype(np.float32), np.concatenate(tidx).astype(np.int32))
+
+
+def rgba_texture(width: int, height: int, seed: int, alpha_lo: float = 0.25, alpha_hi: float = 0.75) -> np.ndarray:
+    """Smooth random RGBA texture: sinusoid colours, opacity remapped into [alpha_lo, alpha_hi]."""
+    t = sinusoid_texture(width, height, 4, seed)
+    t[..., 3] = alpha_lo + (alpha_hi - alpha_lo) * t[..., 3]
+    return t.astype(np.float32)
+
+
+def config_transparent(n_views: int = 8, pairs: int = 16, render: int = 512, tex: int = 512,
+                       n_lon: int = 32, n_lat: int = 32) -> Scene:
+    """Transparent geometry (Section 4.4): three overlapping semi-transparent UV spheres
+    (radius 0.6, 3 x 2,048 triangles) in a row, so a pixel sees up to six fragments (each
+    sphere's front and back), more than the deep ID buffer keeps; one RGBA albedo (opacity in
+    [0.25, 0.75]), composited front to back over a gray background.  Target: Gaussian vertex
+    noise (sigma 0.02) and another RGBA texture."""
+    sph = uv_sphere(n_lon, n_lat, radius=0.6)
+    mesh = merge_meshes([sph, sph, sph], [(-0.45, 0.0, -0.3), (0.0, 0.05, 0.0), (0.45, -0.05, 0.3)])
+    tgt_pos = gaussian_displace(mesh.positions, 0.02, 1)
+    mvp, cam = _views(random_eyes(n_views, seed=2), render, render)
+    return Scene(f"transparent3x{2 * n_lon * n_lat // 1000}k_rgba{tex}_r{render}", mesh.positions, mesh.pos_idx,
+                 mesh.uvs, mesh.uv_idx, [Texture(rgba_texture(tex, tex, seed=0), 1.0 / 255.0, ROLE_ALBEDO)],
+                 1e-3, mvp, cam, render, render, shading=SHADE_TRANSPARENT, background=(0.3, 0.3, 0.3),
+                 target_positions=tgt_pos, target_textures=[rgba_texture(tex, tex, seed=1)],
+                 pairs_per_view=pairs)
 
 
 def config_uneven(n_assets: int = 32, n_views: int = 4, pairs: int = 8, render: int = 512,
