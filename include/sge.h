@@ -56,8 +56,19 @@ typedef enum {
 
 /* Texture roles: what the shading model reads a texture as. */
 enum { SGE_ROLE_ALBEDO = 0, SGE_ROLE_NORMAL = 1, SGE_ROLE_ROUGHNESS = 2, SGE_ROLE_METALLIC = 3 };
-/* Shading models: unlit albedo; Lambert + normal map; GGX (Cook-Torrance) + 4 maps. */
-enum { SGE_SHADE_UNLIT = 0, SGE_SHADE_LAMBERT = 1, SGE_SHADE_GGX = 2 };
+/* Shading models: unlit albedo; Lambert + normal map; GGX (Cook-Torrance) + 4 maps;
+ * transparent geometry (Section 4.4): unlit RGBA fragments composited front to back.
+ * A transparent scene's raster pass keeps a deep ID buffer: for every pixel the
+ * SGE_MAX_LAYERS covering fragments with the smallest (depth bits << 32 | triangle id)
+ * keys, ascending; farther fragments are not drawn.  Fragment j has colour rgb_j and
+ * opacity a_j = clamp(alpha_j, 0, 1) from the bilinear RGBA albedo (4 channels required)
+ * and the pixel is C = sum_j T_j a_j rgb_j + T_n background, T_0 = 1, T_{j+1} = T_j (1 - a_j).
+ * Its contributor set is every listed fragment's three vertices and albedo footprint, on
+ * both sides.  Transparent scenes take sge_estimate_grad, sge_loss, sge_render_deep,
+ * sge_gradient and sge_step; the other estimate and render calls return
+ * SGE_ERR_UNSUPPORTED for them. */
+enum { SGE_SHADE_UNLIT = 0, SGE_SHADE_LAMBERT = 1, SGE_SHADE_GGX = 2, SGE_SHADE_TRANSPARENT = 3 };
+#define SGE_MAX_LAYERS 4 /* fragments per pixel of a transparent scene's deep ID buffer */
 /* Descent steps (Section 5).  MEAN divides each sum by its count instead of 2 eps N. */
 enum { SGE_STEP_SGD = 0, SGE_STEP_ADAM = 1, SGE_STEP_SGD_MEAN = 2 };
 
@@ -72,7 +83,8 @@ typedef struct {
     int32_t role;           /* SGE_ROLE_*; only the first texture of each role is read    */
 } sge_texture;
 
-/* Scene: an opaque triangle mesh with textures seen from n_views cameras. */
+/* Scene: a triangle mesh (opaque, or transparent with SGE_SHADE_TRANSPARENT) with textures
+ * seen from n_views cameras. */
 typedef struct {
     float *positions;       /* device, [n_vertices][3] float32 (parameters)               */
     int32_t n_vertices;     /* >= 3, < 2^28                                                */
@@ -92,7 +104,8 @@ typedef struct {
     const float *targets;   /* device, [n_views][height][width][3] target images I        */
     float background[3];    /* colour of uncovered pixels                                 */
     int32_t shading;        /* SGE_SHADE_*; the textures must include the roles it reads:
-                               unlit albedo; Lambert albedo, normal; GGX all four        */
+                               unlit albedo; Lambert albedo, normal; GGX all four;
+                               transparent a 4-channel (RGBA) albedo                     */
     float light_dir[3];     /* unit vector towards the light, world space                 */
     float light_rgb[3];
     float ambient;
@@ -149,6 +162,16 @@ int sge_validate(sge_scene *scene, sge_stream_t stream);
  *   rgb      [height][width][3] float32 shaded colour, background colour where uncovered. */
 int sge_render_idb(sge_scene *scene, int32_t view, uint64_t seed, uint32_t iter, uint32_t pair,
                    int32_t side, uint64_t *depth_id, float *uv, float *rgb, sge_stream_t stream);
+
+/* Transparent geometry (Section 4.4): one render's deep ID buffer and its front-to-back
+ * composite, for a scene of shading SGE_SHADE_TRANSPARENT (else SGE_ERR_UNSUPPORTED).
+ * The render is theta + side * s * eps (side -1, 0 or +1) with s drawn for
+ * (seed, iter, view, pair) as sge_estimate_grad draws it.  deep_ids (device
+ * [SGE_MAX_LAYERS][height][width] uint64, or NULL) receives each pixel's ascending
+ * (depth bits << 32 | triangle id) keys, ~0 in unused slots; rgb (device
+ * [height][width][3] float32, or NULL) the composite colour. */
+int sge_render_deep(sge_scene *scene, int32_t view, uint64_t seed, uint32_t iter, uint32_t pair, int32_t side,
+                    uint64_t *deep_ids, float *rgb, sge_stream_t stream);
 
 /* All estimates of one iteration (Eq. 9): for each of the n_views views in view_ids
  * (host array, distinct indices < desc->n_views, n_views <= max_views_per_call) and

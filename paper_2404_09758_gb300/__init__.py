@@ -15,8 +15,9 @@ import ctypes as C
 from typing import List, Optional, Sequence
 
 from . import _abi
-from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_TEXTURES, MAX_VIEWS_PER_CALL, OK, STEP_ADAM,
-                   STEP_SGD, STEP_SGD_MEAN, SGEError)
+from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_LAYERS, MAX_TEXTURES, MAX_VIEWS_PER_CALL, OK,
+                   SHADE_GGX, SHADE_LAMBERT, SHADE_TRANSPARENT, SHADE_UNLIT, STEP_ADAM, STEP_SGD, STEP_SGD_MEAN,
+                   SGEError)
 from ._build import build
 
 __all__ = ["Scene", "Batch", "ControlMesh", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
@@ -194,12 +195,27 @@ class Scene:
                                               _ptr(keys), _ptr(uv), _ptr(rgb), _stream_ptr(stream)))
         return keys, uv, rgb
 
+    def render_deep(self, view: int, seed: int = 0, it: int = 0, pair: int = 0, side: int = 0,
+                    deep=None, rgb=None, stream=None):
+        """One render of a transparent scene (Section 4.4): deep ID buffer [MAX_LAYERS,H,W] int64
+        (bit patterns of the ascending uint64 keys, -1 = empty) and the composite [H,W,3]."""
+        torch = _torch()
+        H, W = self.height, self.width
+        deep = torch.empty(_abi.MAX_LAYERS, H, W, dtype=torch.int64, device=self.device) if deep is None else deep
+        rgb = torch.empty(H, W, 3, dtype=torch.float32, device=self.device) if rgb is None else rgb
+        _abi.check(_abi.load().sge_render_deep(self._h, int(view), int(seed), int(it), int(pair), int(side),
+                                               _ptr(deep), _ptr(rgb), _stream_ptr(stream)))
+        return deep, rgb
+
     def render_targets(self, stream=None):
         """Unperturbed renders of every view, [n_views,H,W,3] (e.g. of a target scene)."""
         torch = _torch()
         out = torch.empty(self.n_views, self.height, self.width, 3, dtype=torch.float32, device=self.device)
         for v in range(self.n_views):
-            self.render_idb(v, side=0, rgb=out[v], stream=stream)
+            if self._desc.shading == SHADE_TRANSPARENT:
+                self.render_deep(v, side=0, rgb=out[v], stream=stream)
+            else:
+                self.render_idb(v, side=0, rgb=out[v], stream=stream)
         return out
 
     @staticmethod

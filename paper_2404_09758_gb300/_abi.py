@@ -14,16 +14,18 @@ MAX_TEXTURES = 8
 MAX_VIEWS_PER_CALL = 64
 MAX_BATCH = 64
 MAX_BATCH_VIEWS = 8
+MAX_LAYERS = 4  # fragments per pixel of a transparent scene's deep ID buffer
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_BIN_OVERFLOW, ERR_BAD_INDEX, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
 STEP_SGD, STEP_ADAM, STEP_SGD_MEAN = 0, 1, 2
+SHADE_UNLIT, SHADE_LAMBERT, SHADE_GGX, SHADE_TRANSPARENT = 0, 1, 2, 3
 
 EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_targets", "sge_validate",
            "sge_render_idb", "sge_estimate_grad", "sge_estimate_grad_plain", "sge_step", "sge_status",
            "sge_destroy_scene", "sge_last_error", "sge_render_idb_static", "sge_loss", "sge_gradient",
            "sge_estimate_grad_batch", "sge_autotune_batch", "sge_kernel_timing", "sge_kernel_time",
            "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image",
-           "sge_refine")
+           "sge_refine", "sge_render_deep")
 
 
 class Texture(C.Structure):
@@ -95,6 +97,7 @@ def load(build_if_missing: bool = False):
         L.sge_set_targets.argtypes = [P, P]
         L.sge_validate.argtypes = [P, P]
         L.sge_render_idb.argtypes = [P, I32, U64, U32, U32, I32, P, P, P, P]
+        L.sge_render_deep.argtypes = [P, I32, U64, U32, U32, I32, P, P, P]
         L.sge_estimate_grad.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P, P]
         L.sge_estimate_grad_plain.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P]
         L.sge_step.argtypes = [P, P, P, P, I64, P, P, P]

@@ -1,0 +1,256 @@
+// Transparent geometry (Section 4.4): the raster pass keeps a deep ID buffer (each pixel's
+// SGE_MAX_LAYERS nearest fragments, ascending (depth bits, triangle id) keys), the shading
+// composites the listed RGBA fragments front to back over the background, and G walks the list,
+// crediting every listed fragment's vertices and albedo footprint as the opaque case credits
+// its one visible triangle.
+//
+// One CTA per (16 x 16 tile, estimate).  The tile's binned triangles are set up for both sides
+// in shared memory a chunk at a time; each pixel keeps both sides' lists in registers, then
+// shades, forms f+ - f- and credits the union of its fragments' parameters with global
+// atomics.  Bins come from the conservative binning without pruning: a fragment behind another
+// is still listed.
+#include <cuda_runtime.h>
+
+#include "sge_device.cuh"
+
+namespace sge {
+
+namespace {
+
+constexpr int K = SGE_MAX_LAYERS;
+constexpr int DCHUNK = 128;              // binned triangles staged per pass
+constexpr int MAX_KEYS = 2 * K * 7;      // contributor keys of a pixel: 3 vertices + 4 texels per fragment
+constexpr int kDeepEstimates = 16384;    // estimates (grid rows) of one launch
+
+template <int NS>
+struct DeepSmem {
+  Tri t[NS][DCHUNK];
+  int tri[DCHUNK];
+  float m[16];
+  float red[TILE_PX / 32];
+};
+
+// Insert key k into the ascending list L; the largest key falls off the end.
+__device__ __forceinline__ void deep_insert(unsigned long long (&L)[K], unsigned long long k) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    const unsigned long long lo = k < L[j] ? k : L[j];
+    k = k < L[j] ? L[j] : k;
+    L[j] = lo;
+  }
+}
+
+// Deep lists of one pixel of the tile for NS sides (sides[s] = +1, -1 or 0).
+template <int NS>
+__device__ __forceinline__ void deep_raster(const SceneDev& S, const Workspace& ws, DeepSmem<NS>& sm, int slot,
+                                            int tile, uint64_t key, const int (&sides)[NS],
+                                            unsigned long long (&L)[NS][K], long long rx, long long ry, int dx,
+                                            int dy) {
+  const int ntl = n_tiles(S);
+  const uint32_t beg = ws.tile_off[slot * ntl + tile];
+  int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - beg);
+  // after a bin overflow (reported in the status word) the tile's list was not stored
+  if ((long long)beg + nb > ws.bin_capacity) nb = 0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s)
+#pragma unroll
+    for (int j = 0; j < K; ++j) L[s][j] = ~0ull;
+  for (int c0 = 0; c0 < nb; c0 += DCHUNK) {
+    const int cnt = min(DCHUNK, nb - c0);
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const int tri = (int)ws.bins[beg + c0 + threadIdx.x];
+      sm.tri[threadIdx.x] = tri;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) setup_from_scene(S, sm.m, tri, key, sides[s], rx, ry, sm.t[s][threadIdx.x]);
+    }
+    __syncthreads();
+    for (int j = 0; j < cnt; ++j) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const Tri& t = sm.t[s][j];
+        if (!t.ok) continue;
+        long long e[3];
+        if (!cover(t, dx, dy, e)) continue;
+        float l[3];
+        lambdas(e, t.inv_area, l);
+        deep_insert(L[s], ((unsigned long long)ordered_bits(interp_depth(l, t.z)) << 32) | (uint32_t)sm.tri[j]);
+      }
+    }
+  }
+}
+
+// Front-to-back composite of one side's list at one pixel: T = 1; per listed fragment
+// C += T a rgb, T *= 1 - a with a = clamp(alpha, 0, 1); C += T background.  tris[j] and
+// foot[j] receive each fragment's triangle (-1 past the list) and albedo footprint.
+__device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float* m, uint64_t key, int side,
+                                                 const unsigned long long (&L)[K], long long rx, long long ry,
+                                                 int dx, int dy, int (&tris)[K], Foot (&foot)[K]) {
+  const TexDev& A = S.rtex[0];  // the RGBA albedo, the one texture this model reads
+  float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    tris[j] = -1;
+    if (L[j] == ~0ull) continue;
+    const int tri = (int)(L[j] & 0xFFFFFFFFu);
+    Tri t;
+    setup_from_scene(S, m, tri, key, side, rx, ry, t);
+    long long e[3];
+    cover(t, dx, dy, e);
+    float l[3];
+    lambdas(e, t.inv_area, l);
+    PerspW pw = persp(l, t.iw);
+    const int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
+    const float u = persp_interp(pw, __ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t2));
+    const float v = persp_interp(pw, __ldg(S.uvs + 2 * t0 + 1), __ldg(S.uvs + 2 * t1 + 1), __ldg(S.uvs + 2 * t2 + 1));
+    foot[j] = footprint(u, v, A.w, A.h);
+    float a[4];
+    sample_tex(A, foot[j], key, side, a);
+    const float al = fminf(fmaxf(a[3], 0.0f), 1.0f);
+    const float w = T * al;
+    c0 += w * a[0];
+    c1 += w * a[1];
+    c2 += w * a[2];
+    T *= 1.0f - al;
+    tris[j] = tri;
+  }
+  return f3(c0 + T * S.bg[0], c1 + T * S.bg[1], c2 + T * S.bg[2]);
+}
+
+// Sum of v over the CTA, added to *out by thread 0.
+__device__ __forceinline__ void cta_add(float v, float* red, float* out) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float sum = 0.0f;
+    for (int i = 0; i < TILE_PX / 32; ++i) sum += red[i];
+    if (sum != 0.0f) atomicAdd(out, sum);
+  }
+}
+
+// One estimate per grid row: blockIdx.y = slot * pair_count + (pair - pair_begin).
+__global__ void __launch_bounds__(TILE_PX) k_estimate_deep(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a,
+                                                           int row0) {
+  __shared__ DeepSmem<2> sm;
+  const int tile = blockIdx.x;
+  const int row = row0 + (int)blockIdx.y;
+  const int slot = row / a.pair_count, pair = a.pair_begin + row % a.pair_count;
+  const int view = vl.id[slot];
+  const uint64_t key = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)pair);
+  const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+  const int dx = threadIdx.x % TILE, dy = threadIdx.x / TILE;
+  const int px = tx * TILE + dx, py = ty * TILE + dy;
+  const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
+  if (threadIdx.x < 16) sm.m[threadIdx.x] = S.mvp[16 * view + threadIdx.x];
+  __syncthreads();
+  unsigned long long L[2][K];
+  const int sides[2] = {1, -1};
+  deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, rx, ry, dx, dy);
+  float lv = 0.0f;
+  if (px < S.W && py < S.H) {
+    const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
+    int tris[2][K];
+    Foot foot[2][K];
+    const float3 cp = deep_composite(S, sm.m, key, 1, L[0], rx, ry, dx, dy, tris[0], foot[0]);
+    const float3 cm = deep_composite(S, sm.m, key, -1, L[1], rx, ry, dx, dy, tris[1], foot[1]);
+    const float* tp = S.targets + ((long long)view * npx + p) * 3;
+    float fp, fm;
+    const float df = loss_diff(cp, cm, f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2)), fp, fm);
+    lv = 0.5f * (fp + fm);
+    if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
+    // the contributor set: every listed fragment's welded vertices and footprint texels, both sides
+    const TexDev& A = S.rtex[0];
+    uint32_t ks[MAX_KEYS];
+    int nk = 0;
+    auto add = [&](uint32_t k) {
+      for (int q = 0; q < nk; ++q)
+        if (ks[q] == k) return;
+      ks[nk++] = k;
+    };
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        const int tri = tris[s][j];
+        if (tri < 0) continue;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) add(vkey(__ldg(S.pidx + 3 * tri + v)));
+        const Foot& f = foot[s][j];
+        add(tkey(A.index, f.y0 * A.w + f.x0));
+        add(tkey(A.index, f.y0 * A.w + f.x1));
+        add(tkey(A.index, f.y1 * A.w + f.x0));
+        add(tkey(A.index, f.y1 * A.w + f.x1));
+      }
+    for (int q = 0; q < nk; ++q) {
+      long long base;
+      int nch;
+      key_params(S, ks[q], base, nch);
+      for (int c = 0; c < nch; ++c) {
+        atomicAdd(a.grad + base + c, sign_neg(key, (uint64_t)(base + c)) ? -df : df);
+        atomicAdd(a.counts + base + c, 1u);
+      }
+    }
+  }
+  if (a.loss) cta_add(lv / (float)a.pairs, sm.red, a.loss + slot);
+}
+
+// One render's deep lists and composite (side -1, 0 or +1); with loss, the image error of the
+// render against the view's target is added to loss[slot].
+__global__ void __launch_bounds__(TILE_PX) k_render_deep(SceneDev S, Workspace ws, int slot, int view, uint64_t key,
+                                                         int side, unsigned long long* deep, float* rgb, float* loss) {
+  __shared__ DeepSmem<1> sm;
+  const int tile = blockIdx.x;
+  const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
+  const int dx = threadIdx.x % TILE, dy = threadIdx.x / TILE;
+  const int px = tx * TILE + dx, py = ty * TILE + dy;
+  const long long rx = 256ll * (tx * TILE) + 128, ry = 256ll * (ty * TILE) + 128;
+  if (threadIdx.x < 16) sm.m[threadIdx.x] = S.mvp[16 * view + threadIdx.x];
+  __syncthreads();
+  unsigned long long L[1][K];
+  const int sides[1] = {side};
+  deep_raster<1>(S, ws, sm, slot, tile, key, sides, L, rx, ry, dx, dy);
+  float f = 0.0f;
+  if (px < S.W && py < S.H) {
+    const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
+    if (deep) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) deep[j * npx + p] = L[0][j];
+    }
+    if (rgb || loss) {
+      int tris[K];
+      Foot foot[K];
+      const float3 c = deep_composite(S, sm.m, key, side, L[0], rx, ry, dx, dy, tris, foot);
+      if (rgb) rgb[3 * p] = c.x, rgb[3 * p + 1] = c.y, rgb[3 * p + 2] = c.z;
+      if (loss) {
+        const float* tp = S.targets + ((long long)view * npx + p) * 3;
+        const float d0 = c.x - __ldg(tp), d1 = c.y - __ldg(tp + 1), d2 = c.z - __ldg(tp + 2);
+        f = d0 * d0 + d1 * d1 + d2 * d2;
+      }
+    }
+  }
+  if (loss) cta_add(f, sm.red, loss + slot);
+}
+
+}  // namespace
+
+cudaError_t launch_deep_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
+                                 cudaStream_t st) {
+  const int rows = vl.n * a.pair_count;
+  for (int r0 = 0; r0 < rows; r0 += kDeepEstimates) {
+    const int nr = rows - r0 < kDeepEstimates ? rows - r0 : kDeepEstimates;
+    k_estimate_deep<<<dim3(n_tiles(S), nr), TILE_PX, 0, st>>>(S, ws, vl, a, r0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_render_deep(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key, int side,
+                               unsigned long long* deep, float* rgb, float* loss, cudaStream_t st) {
+  k_render_deep<<<n_tiles(S), TILE_PX, 0, st>>>(S, ws, slot, view, key, side, deep, rgb, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace sge

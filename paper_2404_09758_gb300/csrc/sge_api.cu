@@ -65,7 +65,8 @@ int check_desc(const sge_scene_desc* d) {
     return fail(SGE_ERR_INVALID_ARG, "render size %dx%d out of [1, 16384]", d->width, d->height);
   if (!(d->eps_pos >= 0.0f) || !std::isfinite(d->eps_pos)) return fail(SGE_ERR_INVALID_ARG, "eps_pos must be finite and >= 0");
   if (!(d->near_w > 0.0f)) return fail(SGE_ERR_INVALID_ARG, "near_w must be > 0");
-  if (d->shading < SGE_SHADE_UNLIT || d->shading > SGE_SHADE_GGX) return fail(SGE_ERR_INVALID_ARG, "bad shading %d", d->shading);
+  if (d->shading < SGE_SHADE_UNLIT || d->shading > SGE_SHADE_TRANSPARENT)
+    return fail(SGE_ERR_INVALID_ARG, "bad shading %d", d->shading);
   if (d->shading == SGE_SHADE_GGX && !d->cam_pos) return fail(SGE_ERR_INVALID_ARG, "GGX shading needs cam_pos");
   if (d->n_textures < 0 || d->n_textures > SGE_MAX_TEXTURES) return fail(SGE_ERR_INVALID_ARG, "n_textures %d out of [0, %d]", d->n_textures, SGE_MAX_TEXTURES);
   for (int k = 0; k < d->n_textures; ++k) {
@@ -78,7 +79,9 @@ int check_desc(const sge_scene_desc* d) {
     if (!(t.eps >= 0.0f) || !std::isfinite(t.eps)) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be finite and >= 0", k);
   }
   // the shading model samples one texture of each role it reads: all must be present
-  const int need = d->shading == SGE_SHADE_UNLIT ? 1 : (d->shading == SGE_SHADE_LAMBERT ? 2 : 4);
+  const int need = (d->shading == SGE_SHADE_UNLIT || d->shading == SGE_SHADE_TRANSPARENT)
+                       ? 1
+                       : (d->shading == SGE_SHADE_LAMBERT ? 2 : 4);
   static const int roles[4] = {SGE_ROLE_ALBEDO, SGE_ROLE_NORMAL, SGE_ROLE_ROUGHNESS, SGE_ROLE_METALLIC};
   static const char* names[4] = {"albedo", "normal", "roughness", "metallic"};
   for (int r = 0; r < need; ++r) {
@@ -86,7 +89,21 @@ int check_desc(const sge_scene_desc* d) {
     for (int k = 0; k < d->n_textures; ++k) found = found || d->textures[k].role == roles[r];
     if (!found) return fail(SGE_ERR_INVALID_ARG, "shading model %d needs a texture of role %s", d->shading, names[r]);
   }
+  if (d->shading == SGE_SHADE_TRANSPARENT) {
+    for (int k = 0; k < d->n_textures; ++k)
+      if (d->textures[k].role == SGE_ROLE_ALBEDO) {  // the first albedo is the one read
+        if (d->textures[k].channels != 4)
+          return fail(SGE_ERR_INVALID_ARG, "transparent shading needs an RGBA (4-channel) albedo, texture %d has %d",
+                      k, d->textures[k].channels);
+        break;
+      }
+  }
   return SGE_OK;
+}
+
+int unsupported_transparent(const char* call) {
+  return fail(SGE_ERR_UNSUPPORTED, "%s: transparent scenes run through sge_estimate_grad, sge_loss and "
+              "sge_render_deep", call);
 }
 
 int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
@@ -306,6 +323,7 @@ int sge_render_idb(sge_scene* s, int32_t view, uint64_t seed, uint32_t iter, uin
                    uint64_t* depth_id, float* uv, float* rgb, sge_stream_t stream) {
   if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
   if (side < -1 || side > 1) return fail(SGE_ERR_INVALID_ARG, "side %d not in {-1, 0, 1}", side);
+  if (s->dev.shading == SHADE_TRANSPARENT) return unsupported_transparent("sge_render_idb");
   ViewList vl;
   int rc = views_of(s, &view, 1, vl);
   if (rc) return rc;
@@ -315,6 +333,23 @@ int sge_render_idb(sge_scene* s, int32_t view, uint64_t seed, uint32_t iter, uin
     e = launch_render(s->dev, s->ws, 0, view, pair_key(seed, iter, (uint32_t)view, pair), side,
                       reinterpret_cast<unsigned long long*>(depth_id), reinterpret_cast<float2*>(uv), rgb, st);
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_render_idb");
+}
+
+int sge_render_deep(sge_scene* s, int32_t view, uint64_t seed, uint32_t iter, uint32_t pair, int32_t side,
+                    uint64_t* deep_ids, float* rgb, sge_stream_t stream) {
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  if (side < -1 || side > 1) return fail(SGE_ERR_INVALID_ARG, "side %d not in {-1, 0, 1}", side);
+  if (s->dev.shading != SHADE_TRANSPARENT)
+    return fail(SGE_ERR_UNSUPPORTED, "sge_render_deep: the scene is not transparent (shading %d)", s->dev.shading);
+  ViewList vl;
+  int rc = views_of(s, &view, 1, vl);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_binning(s->dev, s->ws, vl, st);  // no pruning: hidden fragments are listed
+  if (e == cudaSuccess)
+    e = launch_render_deep(s->dev, s->ws, 0, view, pair_key(seed, iter, (uint32_t)view, pair), side,
+                           reinterpret_cast<unsigned long long*>(deep_ids), rgb, nullptr, st);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_render_deep");
 }
 
 int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids, int32_t n_views,
@@ -332,6 +367,12 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
   cudaError_t e = cudaSuccess;
   if (delta_f_out)
     e = cudaMemsetAsync(delta_f_out, 0, sizeof(float) * (size_t)n_views * pairs_per_view * s->dev.W * s->dev.H, st);
+  if (s->dev.shading == SHADE_TRANSPARENT) {
+    // deep lists need every binned triangle (no pruning); one launch covers every pair
+    if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
+    if (e == cudaSuccess) e = launch_deep_estimate(s->dev, s->ws, vl, a, st);
+    return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
+  }
   if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st, true);
   // pairs run in blocks of at most max_pairs_per_call (the projected-vertex buffer holds one block)
   for (int p0 = 0; p0 < pairs_per_view && e == cudaSuccess; p0 += s->ws.max_pairs) {
@@ -356,6 +397,7 @@ int sge_estimate_grad_plain(sge_scene* s, uint64_t seed, uint32_t iter, const in
   ViewList vl;
   int rc = views_of(s, view_ids, n_views, vl);
   if (rc) return rc;
+  if (s->dev.shading == SHADE_TRANSPARENT) return unsupported_transparent("sge_estimate_grad_plain");
   cudaStream_t st = (cudaStream_t)stream;
   EstimateArgs a{seed, iter, pairs_per_view, 1, 0, pairs_per_view, grad_sums, counts, loss_out, nullptr};
   cudaError_t e = launch_binning(s->dev, s->ws, vl, st);
@@ -377,6 +419,7 @@ int sge_estimate_grad_full_image(sge_scene* s, uint64_t seed, uint32_t iter, con
   if (rc) return rc;
   if ((long long)n_views * pairs_per_view > 4096)
     return fail(SGE_ERR_INVALID_ARG, "n_views * pairs_per_view = %lld above 4096", (long long)n_views * pairs_per_view);
+  if (s->dev.shading == SHADE_TRANSPARENT) return unsupported_transparent("sge_estimate_grad_full_image");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(image_df, 0, sizeof(float) * (size_t)n_views * pairs_per_view, st);
   if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
@@ -423,7 +466,10 @@ int sge_loss(sge_scene* s, const int32_t* view_ids, int32_t n_views, float* loss
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = launch_binning(s->dev, s->ws, vl, st);
-  for (int j = 0; j < n_views && e == cudaSuccess; ++j) e = launch_render_loss(s->dev, s->ws, j, vl.id[j], loss_out, st);
+  for (int j = 0; j < n_views && e == cudaSuccess; ++j)
+    e = s->dev.shading == SHADE_TRANSPARENT
+            ? launch_render_deep(s->dev, s->ws, j, vl.id[j], 0, 0, nullptr, nullptr, loss_out, st)
+            : launch_render_loss(s->dev, s->ws, j, vl.id[j], loss_out, st);
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_loss");
 }
 
@@ -453,6 +499,7 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
   for (int i = 0; i < n; ++i) {
     const sge_batch_entry& E = entries[i];
     if (!E.scene) return fail(SGE_ERR_INVALID_ARG, "entries[%d].scene is NULL", i);
+    if (E.scene->dev.shading == SHADE_TRANSPARENT) return unsupported_transparent("sge_estimate_grad_batch");
     if (!E.grad_sums || !E.counts) return fail(SGE_ERR_INVALID_ARG, "entries[%d]: grad_sums and counts must be non-NULL", i);
     if (E.n_views > SGE_MAX_BATCH_VIEWS)
       return fail(SGE_ERR_INVALID_ARG, "entries[%d].n_views %d above %d", i, E.n_views, SGE_MAX_BATCH_VIEWS);

@@ -20,6 +20,7 @@ constexpr int kNotDrawn = (int)0x80000000;  // projected X of a vertex its trian
 constexpr int ROLE_ALBEDO = SGE_ROLE_ALBEDO, ROLE_NORMAL = SGE_ROLE_NORMAL;
 constexpr int ROLE_ROUGHNESS = SGE_ROLE_ROUGHNESS, ROLE_METALLIC = SGE_ROLE_METALLIC;
 constexpr int SHADE_UNLIT = SGE_SHADE_UNLIT, SHADE_LAMBERT = SGE_SHADE_LAMBERT, SHADE_GGX = SGE_SHADE_GGX;
+constexpr int SHADE_TRANSPARENT = SGE_SHADE_TRANSPARENT;
 
 struct TexDev {
   const float* ptr;
@@ -191,6 +192,14 @@ cudaError_t launch_full_image_grad(const SceneDev& S, const ViewList& vl, int pa
 // y (+)= A x for 3-vectors per row, A in CSR (row pointers, columns, weights; device).
 cudaError_t launch_csr_vec3(const int32_t* ptr, const int32_t* col, const float* w, int n_rows, const float* x,
                             float* y, int accumulate, cudaStream_t st);
+
+// Transparent geometry (Section 4.4), after launch_binning without pruning: every estimate of a
+// block of pairs (deep lists, front-to-back composite, f+ - f-, credits of every listed fragment),
+// and one render's deep ID buffer / composite / image error (added to loss[slot]).
+cudaError_t launch_deep_estimate(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
+                                 cudaStream_t st);
+cudaError_t launch_render_deep(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key, int side,
+                               unsigned long long* deep, float* rgb, float* loss, cudaStream_t st);
 
 // Image error of unperturbed renders (forward of the autograd form), added to loss[slot].
 cudaError_t launch_render_loss(const SceneDev& S, const Workspace& ws, int slot, int view, float* loss,

@@ -11,6 +11,8 @@ Tolerances (derived from the arithmetic of each side):
     k = 8 for unlit and Lambert shading (a bilinear sum and a dot product);
     k = 512 for GGX, whose distribution term divides by (n.h^2 (alpha^2 - 1) + 1)^2
     and so amplifies rounding by up to 1/alpha^2, on top of three normalisations;
+    k = 32 for transparent geometry: up to four bilinear fragments, each weighted by a
+    running product of (1 - alpha) factors, summed front to back;
   - colours of one render: |diff| <= k u (1 + |I|) with the same k;
   - gradient sums: relative L2 error <= 1e-4 per parameter group against the
     oracle's float64 sums.
@@ -69,7 +71,7 @@ def run_both(sc, targets, seed, it, views, pairs, plain=False, footprint=0, gpu_
 
 def color_k(sc):
     import synth
-    return 512.0 if sc.shading == synth.SHADE_GGX else 8.0
+    return {synth.SHADE_GGX: 512.0, synth.SHADE_TRANSPARENT: 32.0}.get(sc.shading, 8.0)
 
 
 def assert_parity(sc, r, grad_tol=1e-4):

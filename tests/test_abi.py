@@ -92,6 +92,15 @@ def test_descriptor_checks_run_on_the_host():
         assert (rc == _abi.OK) == ok, (shading, roles, L.sge_last_error())
         if not ok:
             assert rc == _abi.ERR_INVALID_ARG and b"role" in L.sge_last_error()
+    # transparent geometry reads one albedo, which must carry an opacity channel (RGBA)
+    d.shading, d.n_textures = 3, 1
+    d.textures[0].role = 0
+    for channels, ok in ((4, True), (3, False), (1, False)):
+        d.textures[0].channels = channels
+        rc = L.sge_workspace_size(C.byref(d), None, C.byref(nbytes))
+        assert (rc == _abi.OK) == ok, (channels, L.sge_last_error())
+        if not ok:
+            assert rc == _abi.ERR_INVALID_ARG and b"RGBA" in L.sge_last_error()
 
 
 def test_view_draw_equals_the_oracle():
@@ -120,7 +129,7 @@ def _valid_desc():
 
 @pytest.mark.parametrize("field, value", [
     ("n_vertices", 2), ("n_triangles", 0), ("n_views", 0), ("width", 0), ("height", 20000),
-    ("eps_pos", -1.0), ("eps_pos", float("nan")), ("near_w", 0.0), ("shading", 3), ("n_textures", 9),
+    ("eps_pos", -1.0), ("eps_pos", float("nan")), ("near_w", 0.0), ("shading", 4), ("n_textures", 9),
     ("positions", None), ("targets", None), ("tex_channels", 5), ("tex_role", 4), ("tex_eps", -1.0),
     ("tex_texels", None)])
 def test_invalid_descriptions_are_rejected_on_the_host(field, value):
