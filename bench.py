@@ -653,6 +653,60 @@ def run_transparent(args):
         print(json.dumps(line), flush=True)
 
 
+def run_soup(args):
+    """Section 6.1's experiment: triangle soups of 1,024, 10,240 and 102,400 triangles (12
+    parameters each: three vertices and an RGB colour; 12,288 to 1,228,800 parameters) fitted to a smooth 512^2
+    image with Adam (lr = eps), 8 antithetic pairs per iteration, once with the per-pixel
+    estimator (Eq. 8) and once with the full-image one (Eq. 4).  Reports the image error left
+    after each number of iterations, and the time per iteration."""
+    import torch
+
+    import synth
+    from paper_2404_09758_gb300 import STEP_ADAM, Scene
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    iters, pairs, render = 200, 8, 512
+    marks = (0, 25, 50, 100, 200)
+    out, ms = {}, {}
+    for n in (1024, 10240, 102400):
+        sc, tg = synth.triangle_soup(n, render, seed=0)
+        for kind in ("per_pixel", "full_image"):
+            g = Scene.from_arrays(sc, targets=tg)
+            grad, counts = g.new_grad_buffers()
+            m = torch.zeros(g.n_params, device=dev)
+            v = torch.zeros(g.n_params, device=dev)
+            curve, t_opt = {}, 0.0
+            for it in range(iters + 1):
+                if it in marks:
+                    curve[it] = float(g.loss([0]).item())
+                if it == iters:
+                    break
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if kind == "per_pixel":
+                    g.estimate_grad(1, it, [0], pairs, grad, counts)
+                else:
+                    g.estimate_grad_full_image(1, it, [0], pairs, grad, counts)
+                g.step(STEP_ADAM, grad, counts, pairs, sc.eps_pos, [sc.textures[0].eps], m=m, v=v, t=it + 1)
+                torch.cuda.synchronize()
+                t_opt += time.perf_counter() - t0
+            assert g.status() == 0
+            out[f"{n}_{kind}"] = {str(k): round(c / curve[0], 4) for k, c in curve.items()}
+            ms[f"{n}_{kind}"] = round(1000.0 * t_opt / iters, 3)
+            del g, grad, counts, m, v
+    line = {"metric": "image error left after Adam iterations, per-pixel (Eq. 8) vs full-image (Eq. 4) estimator",
+            "value": out["102400_per_pixel"][str(iters)], "unit": "fraction of the initial image error",
+            "n_gpus": 1, "steps": iters, "warmup": 0, "ms_per_step": ms["102400_per_pixel"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"triangle_soups_1k_10k_100k_r{render}_{pairs}pairs_adam", "iterations": iters,
+                       "params_per_triangle": 12, "graph": "none (eager)"},
+            "error_left": out, "ms_per_iteration": ms}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_converge(args):
     """Many-step optimisation of the autograd configuration (32,768-triangle displaced sphere,
     1024^2 RGBA albedo + normal map, Lambert, 1024^2, 16 views x 16 pairs per iteration, Adam with
@@ -757,13 +811,15 @@ def main():
     ap.add_argument("--seconds", type=float, default=60.0, help="wall time of --workload converge")
     ap.add_argument("--control", choices=["none", "catmull_clark"], default="none",
                     help="--workload converge: optimise a Catmull-Clark control mesh instead of the surface")
-    ap.add_argument("--workload", choices=["batched", "uneven", "scale", "full_image", "converge", "transparent"],
+    ap.add_argument("--workload", choices=["batched", "uneven", "scale", "full_image", "converge", "transparent",
+                                           "soup"],
                     default="batched",
                     help="batched: the headline configuration; uneven: 32 assets in one batched call; "
                          "scale: 1M triangles, GGX, 2048^2; full_image: Eq. 4's whole-image estimator on "
                          "the batched configuration; converge: optimise the autograd configuration "
                          "for --seconds and report the image error against time; transparent: deep ID "
-                         "buffers of three overlapping semi-transparent spheres")
+                         "buffers of three overlapping semi-transparent spheres; soup: Section 6.1's "
+                         "per-pixel vs full-image comparison on triangle soups")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -779,6 +835,8 @@ def main():
         run_converge(args)
     elif args.workload == "transparent":
         run_transparent(args)
+    elif args.workload == "soup":
+        run_soup(args)
     else:
         run_ours(args)
 

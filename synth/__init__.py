@@ -562,6 +562,31 @@ def config_transparent(n_views: int = 8, pairs: int = 16, render: int = 512, tex
                  pairs_per_view=pairs)
 
 
+def triangle_soup(n: int, render: int = 512, seed: int = 0):
+    """Section 6.1's experiment: n independent triangles with 12 parameters each (three vertices,
+    one RGB colour) fitted to an image.  Identity camera (clip = world: x, y in [-1, 1] span the
+    image, z in (0, 1) orders the triangles).  Colour i is texel i of an n x 1 RGB texture, named
+    by the triangle's three UVs (the texel's centre).  Initial state: triangles of circumradius
+    3 / sqrt(n) world units at uniform positions and orientations (the soup covers the image
+    about three times over), colours uniform in [0.25, 0.75]; eps_pos is one pixel, the colour
+    eps 2/255.  Returns (scene, target image [1, render, render, 3]): a smooth random image."""
+    rng = np.random.default_rng(seed)
+    c = np.concatenate([rng.uniform(-1.0, 1.0, size=(n, 2)), rng.uniform(0.2, 0.8, size=(n, 1))], axis=1)
+    R = 3.0 / math.sqrt(n)
+    ang = rng.uniform(0.0, 2.0 * math.pi, size=(n, 1)) + np.array([0.0, 2.0, 4.0]) * math.pi / 3.0
+    pos = np.repeat(c[:, None, :], 3, axis=1)
+    pos[..., 0] += R * np.cos(ang)
+    pos[..., 1] += R * np.sin(ang)
+    pidx = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    uv = np.stack([np.repeat((np.arange(n) + 0.5) / n, 3), np.full(3 * n, 0.5)], axis=1)
+    tex = rng.uniform(0.25, 0.75, size=(1, n, 3)).astype(np.float32)
+    target = sinusoid_texture(render, render, 3, seed + 1)[None]
+    sc = Scene(f"soup{n}_r{render}", pos.reshape(-1, 3).astype(np.float32), pidx, uv.astype(np.float32),
+               pidx.copy(), [Texture(tex, 2.0 / 255.0, ROLE_ALBEDO)], 2.0 / render,
+               np.eye(4, dtype=np.float32)[None], np.array([[0.0, 0.0, 3.0]], np.float32), render, render)
+    return sc, target.astype(np.float32)
+
+
 def config_uneven(n_assets: int = 32, n_views: int = 4, pairs: int = 8, render: int = 512,
                   tri_lo: int = 1000, tri_hi: int = 200_000,
                   tex_choices=(256, 512, 1024, 2048)) -> List[Scene]:
