@@ -672,8 +672,11 @@ def run_soup(args):
     out, ms = {}, {}
     for n in (1024, 10240, 102400):
         sc, tg = synth.triangle_soup(n, render, seed=0)
+        # a 1,024-triangle soup's triangles span up to 5 x 5 tiles: more bin entries than the
+        # default capacity (6 per triangle + 8 per tile) assumes
+        cap = 32 * n + 16 * ((render + 15) // 16) ** 2
         for kind in ("per_pixel", "full_image"):
-            g = Scene.from_arrays(sc, targets=tg)
+            g = Scene.from_arrays(sc, targets=tg, bin_capacity=cap)
             grad, counts = g.new_grad_buffers()
             m = torch.zeros(g.n_params, device=dev)
             v = torch.zeros(g.n_params, device=dev)
