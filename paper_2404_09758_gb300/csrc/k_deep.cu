@@ -81,16 +81,16 @@ __device__ __forceinline__ void deep_raster(const SceneDev& S, const Workspace& 
 }
 
 // Front-to-back composite of one side's list at one pixel: T = 1; per listed fragment
-// C += T a rgb, T *= 1 - a with a = clamp(alpha, 0, 1); C += T background.  tris[j] and
-// foot[j] receive each fragment's triangle (-1 past the list) and albedo footprint.
+// C += T a rgb, T *= 1 - a with a = clamp(alpha, 0, 1); C += T background.  on_fragment(tri,
+// foot) is called for each listed fragment with its triangle and albedo footprint.
+template <typename F>
 __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float* m, uint64_t key, int side,
                                                  const unsigned long long (&L)[K], long long rx, long long ry,
-                                                 int dx, int dy, int (&tris)[K], Foot (&foot)[K]) {
+                                                 int dx, int dy, F&& on_fragment) {
   const TexDev& A = S.rtex[0];  // the RGBA albedo, the one texture this model reads
   float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    tris[j] = -1;
     if (L[j] == ~0ull) continue;
     const int tri = (int)(L[j] & 0xFFFFFFFFu);
     Tri t;
@@ -103,16 +103,16 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     const int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
     const float u = persp_interp(pw, __ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t2));
     const float v = persp_interp(pw, __ldg(S.uvs + 2 * t0 + 1), __ldg(S.uvs + 2 * t1 + 1), __ldg(S.uvs + 2 * t2 + 1));
-    foot[j] = footprint(u, v, A.w, A.h);
+    const Foot f = footprint(u, v, A.w, A.h);
     float a[4];
-    sample_tex(A, foot[j], key, side, a);
+    sample_tex(A, f, key, side, a);
     const float al = fminf(fmaxf(a[3], 0.0f), 1.0f);
     const float w = T * al;
     c0 += w * a[0];
     c1 += w * a[1];
     c2 += w * a[2];
     T *= 1.0f - al;
-    tris[j] = tri;
+    on_fragment(tri, f);
   }
   return f3(c0 + T * S.bg[0], c1 + T * S.bg[1], c2 + T * S.bg[2]);
 }
@@ -131,7 +131,7 @@ __device__ __forceinline__ void cta_add(float v, float* red, float* out) {
 }
 
 // One estimate per grid row: blockIdx.y = slot * pair_count + (pair - pair_begin).
-__global__ void __launch_bounds__(TILE_PX) k_estimate_deep(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a,
+__global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a,
                                                            int row0) {
   __shared__ DeepSmem<2> sm;
   const int tile = blockIdx.x;
@@ -151,16 +151,8 @@ __global__ void __launch_bounds__(TILE_PX) k_estimate_deep(SceneDev S, Workspace
   float lv = 0.0f;
   if (px < S.W && py < S.H) {
     const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
-    int tris[2][K];
-    Foot foot[2][K];
-    const float3 cp = deep_composite(S, sm.m, key, 1, L[0], rx, ry, dx, dy, tris[0], foot[0]);
-    const float3 cm = deep_composite(S, sm.m, key, -1, L[1], rx, ry, dx, dy, tris[1], foot[1]);
-    const float* tp = S.targets + ((long long)view * npx + p) * 3;
-    float fp, fm;
-    const float df = loss_diff(cp, cm, f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2)), fp, fm);
-    lv = 0.5f * (fp + fm);
-    if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
-    // the contributor set: every listed fragment's welded vertices and footprint texels, both sides
+    // the contributor set, gathered while compositing: every listed fragment's welded vertices
+    // and footprint texels, both sides, each key once
     const TexDev& A = S.rtex[0];
     uint32_t ks[MAX_KEYS];
     int nk = 0;
@@ -169,20 +161,21 @@ __global__ void __launch_bounds__(TILE_PX) k_estimate_deep(SceneDev S, Workspace
         if (ks[q] == k) return;
       ks[nk++] = k;
     };
+    auto credit_keys = [&](int tri, const Foot& f) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const int tri = tris[s][j];
-        if (tri < 0) continue;
-#pragma unroll
-        for (int v = 0; v < 3; ++v) add(vkey(__ldg(S.pidx + 3 * tri + v)));
-        const Foot& f = foot[s][j];
-        add(tkey(A.index, f.y0 * A.w + f.x0));
-        add(tkey(A.index, f.y0 * A.w + f.x1));
-        add(tkey(A.index, f.y1 * A.w + f.x0));
-        add(tkey(A.index, f.y1 * A.w + f.x1));
-      }
+      for (int v = 0; v < 3; ++v) add(vkey(__ldg(S.pidx + 3 * tri + v)));
+      add(tkey(A.index, f.y0 * A.w + f.x0));
+      add(tkey(A.index, f.y0 * A.w + f.x1));
+      add(tkey(A.index, f.y1 * A.w + f.x0));
+      add(tkey(A.index, f.y1 * A.w + f.x1));
+    };
+    const float3 cp = deep_composite(S, sm.m, key, 1, L[0], rx, ry, dx, dy, credit_keys);
+    const float3 cm = deep_composite(S, sm.m, key, -1, L[1], rx, ry, dx, dy, credit_keys);
+    const float* tp = S.targets + ((long long)view * npx + p) * 3;
+    float fp, fm;
+    const float df = loss_diff(cp, cm, f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2)), fp, fm);
+    lv = 0.5f * (fp + fm);
+    if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
     for (int q = 0; q < nk; ++q) {
       long long base;
       int nch;
@@ -219,9 +212,7 @@ __global__ void __launch_bounds__(TILE_PX) k_render_deep(SceneDev S, Workspace w
       for (int j = 0; j < K; ++j) deep[j * npx + p] = L[0][j];
     }
     if (rgb || loss) {
-      int tris[K];
-      Foot foot[K];
-      const float3 c = deep_composite(S, sm.m, key, side, L[0], rx, ry, dx, dy, tris, foot);
+      const float3 c = deep_composite(S, sm.m, key, side, L[0], rx, ry, dx, dy, [](int, const Foot&) {});
       if (rgb) rgb[3 * p] = c.x, rgb[3 * p + 1] = c.y, rgb[3 * p + 2] = c.z;
       if (loss) {
         const float* tp = S.targets + ((long long)view * npx + p) * 3;
