@@ -303,13 +303,13 @@ int sge_status(sge_scene *scene, sge_stream_t stream, int32_t *device_status);
  * be NULL).  Its scratch is a fixed array in the library's device memory,
  * SGE_STATIC_SCRATCH limits below, held on every GPU that loads the library until
  * the process exits; requests beyond the limits return SGE_ERR_INVALID_ARG and
- * launch nothing.  The first call on a device (that device current) looks up the
+ * launch nothing, and transparent scenes SGE_ERR_UNSUPPORTED.  The first call on a device (that device current) looks up the
  * array's address; make it before any stream capture.  All calls share the
  * array: calls that overlap on the GPU (other streams or threads) race; order
  * them on one stream.  device_status (device int32, or NULL) receives SGE_OK or
  * SGE_ERR_BIN_OVERFLOW (tiles whose lists did not fit render as background).
- * Allocates nothing and calls no allocating library routine.  Errors are
- * reported by return code only. */
+ * Allocates nothing and calls no allocating library routine.  Errors return their
+ * code and leave a message for sge_last_error, as the other calls do. */
 #define SGE_STATIC_MAX_TRIANGLES 131072
 #define SGE_STATIC_MAX_PIXELS (2048 * 2048)
 #define SGE_STATIC_BIN_ENTRIES (1 << 21)

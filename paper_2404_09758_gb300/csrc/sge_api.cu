@@ -42,6 +42,14 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(SGE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+}  // namespace
+
+namespace sge {
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace sge
+
+namespace {
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {

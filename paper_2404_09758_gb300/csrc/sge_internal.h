@@ -213,4 +213,7 @@ cudaError_t launch_validate(const SceneDev& S, uint32_t* status, cudaStream_t st
 
 __host__ __device__ inline int n_tiles(const SceneDev& S) { return S.tiles_x * S.tiles_y; }
 
+// The calling thread's message for sge_last_error (host).
+void set_last_error(const char* msg);
+
 }  // namespace sge

@@ -51,8 +51,11 @@ constexpr int kMaxDevices = 64;
 std::mutex g_lock;
 void* g_addr[kMaxDevices] = {};
 
-// Errors are reported by return code only (this entry point keeps no message state).
-int fail(int code, const char*) { return code; }
+// Errors return their code and leave their message for sge_last_error.
+int fail(int code, const char* msg) {
+  set_last_error(msg);
+  return code;
+}
 
 // Device address of the scratch on the current device (looked up once per device).
 int scratch_address(void** out) {
@@ -88,6 +91,8 @@ extern "C" int sge_render_idb_static(const sge_scene_desc* d, int32_t view, uint
     return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: render larger than SGE_STATIC_MAX_PIXELS");
   if (view < 0 || view >= d->n_views) return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: bad view");
   if (side < -1 || side > 1) return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: side not in {-1, 0, 1}");
+  if (d->shading == SGE_SHADE_TRANSPARENT)
+    return fail(SGE_ERR_UNSUPPORTED, "sge_render_idb_static: transparent scenes render through sge_render_deep");
   if (d->shading < SGE_SHADE_UNLIT || d->shading > SGE_SHADE_GGX || (d->shading == SGE_SHADE_GGX && !d->cam_pos))
     return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: bad shading");
   if (d->n_textures < 0 || d->n_textures > SGE_MAX_TEXTURES)

@@ -161,3 +161,16 @@ def test_workspace_grows_with_views_and_pairs():
     assert sizes[0] < sizes[1] < sizes[2]
     cfg = _abi.Config(0, 1 << 33, 0, 0, 0)  # bin capacity must stay below 2^32 entries
     assert L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(C.c_size_t())) == _abi.ERR_INVALID_ARG
+
+
+def test_static_render_refuses_transparent_scenes_on_the_host():
+    """The allocation-free render is written for one visible triangle a pixel: a transparent
+    description is refused as unsupported before any device call."""
+    import ctypes as C
+    from paper_2404_09758_gb300 import _abi
+    L = _abi.load(build_if_missing=True)
+    d = _valid_desc()
+    d.shading = 3
+    d.textures[0].channels = 4
+    rc = L.sge_render_idb_static(C.byref(d), 0, 0, 0, 0, 0, None, None, None, None, None)
+    assert rc == _abi.ERR_UNSUPPORTED and b"sge_render_deep" in L.sge_last_error()
