@@ -30,22 +30,29 @@ struct DeepSmem {
   float red[TILE_PX / 32];
 };
 
-// Insert key k into the ascending list L; the largest key falls off the end.
-__device__ __forceinline__ void deep_insert(unsigned long long (&L)[K], unsigned long long k) {
+// Insert key k (staged at shared-memory slot q) into the ascending list L (slots P); the
+// largest key falls off the end.
+__device__ __forceinline__ void deep_insert(unsigned long long (&L)[K], int (&P)[K], unsigned long long k, int q) {
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    const unsigned long long lo = k < L[j] ? k : L[j];
-    k = k < L[j] ? L[j] : k;
+    const bool lt = k < L[j];
+    const unsigned long long lo = lt ? k : L[j];
+    const int qlo = lt ? q : P[j];
+    k = lt ? L[j] : k;
+    q = lt ? P[j] : q;
     L[j] = lo;
+    P[j] = qlo;
   }
 }
 
-// Deep lists of one pixel of the tile for NS sides (sides[s] = +1, -1 or 0).
+// Deep lists of one pixel of the tile for NS sides (sides[s] = +1, -1 or 0), with each entry's
+// slot in the staged chunk.  Returns whether the whole bin fit one chunk: then sm.t[s][P[s][j]]
+// still holds the set-up of entry j when the raster is done.
 template <int NS>
-__device__ __forceinline__ void deep_raster(const SceneDev& S, const Workspace& ws, DeepSmem<NS>& sm, int slot,
+__device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& ws, DeepSmem<NS>& sm, int slot,
                                             int tile, uint64_t key, const int (&sides)[NS],
-                                            unsigned long long (&L)[NS][K], long long rx, long long ry, int dx,
-                                            int dy) {
+                                            unsigned long long (&L)[NS][K], int (&P)[NS][K], long long rx,
+                                            long long ry, int dx, int dy) {
   const int ntl = n_tiles(S);
   const uint32_t beg = ws.tile_off[slot * ntl + tile];
   int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - beg);
@@ -54,7 +61,7 @@ __device__ __forceinline__ void deep_raster(const SceneDev& S, const Workspace& 
 #pragma unroll
   for (int s = 0; s < NS; ++s)
 #pragma unroll
-    for (int j = 0; j < K; ++j) L[s][j] = ~0ull;
+    for (int j = 0; j < K; ++j) L[s][j] = ~0ull, P[s][j] = 0;
   for (int c0 = 0; c0 < nb; c0 += DCHUNK) {
     const int cnt = min(DCHUNK, nb - c0);
     __syncthreads();
@@ -74,27 +81,33 @@ __device__ __forceinline__ void deep_raster(const SceneDev& S, const Workspace& 
         if (!cover(t, dx, dy, e)) continue;
         float l[3];
         lambdas(e, t.inv_area, l);
-        deep_insert(L[s], ((unsigned long long)ordered_bits(interp_depth(l, t.z)) << 32) | (uint32_t)sm.tri[j]);
+        deep_insert(L[s], P[s], ((unsigned long long)ordered_bits(interp_depth(l, t.z)) << 32) | (uint32_t)sm.tri[j],
+                    j);
       }
     }
   }
+  return nb <= DCHUNK;
 }
 
 // Front-to-back composite of one side's list at one pixel: T = 1; per listed fragment
 // C += T a rgb, T *= 1 - a with a = clamp(alpha, 0, 1); C += T background.  on_fragment(tri,
 // foot) is called for each listed fragment with its triangle and albedo footprint.
+// staged: the side's set-ups in shared memory (slots P) when the bin fit one chunk, else NULL
+// (each fragment is set up again; the same arithmetic gives the same set-up).
 template <typename F>
 __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float* m, uint64_t key, int side,
-                                                 const unsigned long long (&L)[K], long long rx, long long ry,
-                                                 int dx, int dy, F&& on_fragment) {
+                                                 const unsigned long long (&L)[K], const int (&P)[K],
+                                                 const Tri* staged, long long rx, long long ry, int dx, int dy,
+                                                 F&& on_fragment) {
   const TexDev& A = S.rtex[0];  // the RGBA albedo, the one texture this model reads
   float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
     if (L[j] == ~0ull) continue;
     const int tri = (int)(L[j] & 0xFFFFFFFFu);
-    Tri t;
-    setup_from_scene(S, m, tri, key, side, rx, ry, t);
+    Tri own;
+    if (!staged) setup_from_scene(S, m, tri, key, side, rx, ry, own);
+    const Tri& t = staged ? staged[P[j]] : own;
     long long e[3];
     cover(t, dx, dy, e);
     float l[3];
@@ -146,8 +159,9 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
   if (threadIdx.x < 16) sm.m[threadIdx.x] = S.mvp[16 * view + threadIdx.x];
   __syncthreads();
   unsigned long long L[2][K];
+  int P[2][K];
   const int sides[2] = {1, -1};
-  deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, rx, ry, dx, dy);
+  const bool resident = deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy);
   float lv = 0.0f;
   if (px < S.W && py < S.H) {
     const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
@@ -169,8 +183,10 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
       add(tkey(A.index, f.y1 * A.w + f.x0));
       add(tkey(A.index, f.y1 * A.w + f.x1));
     };
-    const float3 cp = deep_composite(S, sm.m, key, 1, L[0], rx, ry, dx, dy, credit_keys);
-    const float3 cm = deep_composite(S, sm.m, key, -1, L[1], rx, ry, dx, dy, credit_keys);
+    const float3 cp = deep_composite(S, sm.m, key, 1, L[0], P[0], resident ? sm.t[0] : nullptr, rx, ry, dx, dy,
+                                     credit_keys);
+    const float3 cm = deep_composite(S, sm.m, key, -1, L[1], P[1], resident ? sm.t[1] : nullptr, rx, ry, dx, dy,
+                                     credit_keys);
     const float* tp = S.targets + ((long long)view * npx + p) * 3;
     float fp, fm;
     const float df = loss_diff(cp, cm, f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2)), fp, fm);
@@ -202,8 +218,9 @@ __global__ void __launch_bounds__(TILE_PX) k_render_deep(SceneDev S, Workspace w
   if (threadIdx.x < 16) sm.m[threadIdx.x] = S.mvp[16 * view + threadIdx.x];
   __syncthreads();
   unsigned long long L[1][K];
+  int P[1][K];
   const int sides[1] = {side};
-  deep_raster<1>(S, ws, sm, slot, tile, key, sides, L, rx, ry, dx, dy);
+  const bool resident = deep_raster<1>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy);
   float f = 0.0f;
   if (px < S.W && py < S.H) {
     const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
@@ -212,7 +229,8 @@ __global__ void __launch_bounds__(TILE_PX) k_render_deep(SceneDev S, Workspace w
       for (int j = 0; j < K; ++j) deep[j * npx + p] = L[0][j];
     }
     if (rgb || loss) {
-      const float3 c = deep_composite(S, sm.m, key, side, L[0], rx, ry, dx, dy, [](int, const Foot&) {});
+      const float3 c = deep_composite(S, sm.m, key, side, L[0], P[0], resident ? sm.t[0] : nullptr, rx, ry, dx, dy,
+                                      [](int, const Foot&) {});
       if (rgb) rgb[3 * p] = c.x, rgb[3 * p + 1] = c.y, rgb[3 * p + 2] = c.z;
       if (loss) {
         const float* tp = S.targets + ((long long)view * npx + p) * 3;
