@@ -5,10 +5,10 @@
 // its one visible triangle.
 //
 // One CTA per (16 x 16 tile, estimate).  The tile's binned triangles are set up for both sides
-// in shared memory a chunk at a time; each pixel keeps both sides' lists in registers, then
-// shades, forms f+ - f- and credits the union of its fragments' parameters with global
-// atomics.  Bins come from the conservative binning without pruning: a fragment behind another
-// is still listed.
+// in shared memory a chunk at a time; each pixel keeps both sides' lists in registers (with each
+// entry's chunk slot, so that a bin of one chunk is not set up again to shade), then shades,
+// forms f+ - f- and credits the union of its fragments' parameters with global atomics.  Bins
+// come from the conservative binning without pruning: a fragment behind another is still listed.
 #include <cuda_runtime.h>
 
 #include "sge_device.cuh"
