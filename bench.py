@@ -36,13 +36,34 @@ UNIT = "pixel-pairs/s"
 WORKLOAD = "sphere8k_tex512_r512_8views_x_64pairs"
 N_VIEWS, PAIRS, RENDER = 8, 64, 512
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# Roofline of the dominant kernel (k_estimate_fast): it is bound by instruction issue on the
-# SMs' integer/FP lanes, not by HBM or tensor cores.  Per-unit figure: thread instructions the
-# kernel executes per antithetic pixel pair of the workload (smsp__inst_executed x active threads
-# per warp / pixel pairs), and its DRAM traffic per launch, both from the ncu capture summarised
-# in profiles/k_estimate_fast_sphere8k_r512.md (same kernel source).
-ALU_INSTR_PER_PIXEL_PAIR = 1067.0
-DRAM_BYTES_PER_LAUNCH = 125.52e6
+# Roofline of the dominant kernel (k_estimate_fast): nothing on the path is a dense contraction
+# and it moves about a byte of DRAM per pixel pair, so its roofline is the SMs' lane rate
+# (152 SMs x 128 FP32/INT32 lanes x clock).  The work is counted from the method, not from the
+# kernel: method_ops() below.  The kernel's own executed instructions per pixel pair (ncu
+# smsp__inst_executed x active lanes of the same build) give the issue efficiency beside it.
+# Arithmetic of one covered side of a pixel pair (Section 4.3 R, Algorithm 2 G), in 32-bit
+# operations: the visible triangle's coverage test (3 edge functions of 2 multiply-adds, 3
+# compares), barycentrics (3 conversions, 3 multiplies) and depth (3 multiplies, 2 adds): 20;
+# perspective-correct UV (3 + 6 multiplies, 2 + 4 adds, 2 divides): 17; the bilinear footprint
+# (per axis a multiply, 2 subtracts, floor, conversion; wrap and clamp): 14; per read texture the
+# 4 bilinear weights (6) and per texel channel the perturbed value and its weighted add (2).
+OPS_VISIBLE, OPS_UV, OPS_FOOT, OPS_WEIGHTS, OPS_PER_TEXEL_CHANNEL = 20, 17, 14, 6, 2
+OPS_SHADE = {0: 0, 1: 55, 2: 125}  # unlit; Lambert with a normal map; GGX + Lambert (per side)
+OPS_LOSS_DIFF = 12  # per pixel pair: sum_c (I+ - I-)(I+ + I- - 2I)
+OPS_CREDIT = 2      # per contribution: one add to the parameter's sum, one to its count
+# ncu capture of this kernel build (profiles/k_estimate_fast_sphere8k_r512.md): executed thread
+# instructions per pixel pair and DRAM bytes per launch; None until captured for this build
+NCU_INSTR_PER_PIXEL_PAIR = None
+NCU_DRAM_BYTES_PER_LAUNCH = None
+
+
+def method_ops(shading: int, read_channels, covered_sides: float, covered_pairs: float, contributions: float):
+    """32-bit operations the method performs in one estimate call, from quantities the run
+    counts: covered_sides (pixel pairs x sides showing a triangle), covered_pairs (pixel pairs with
+    a triangle on either side), contributions (sum over pixel pairs of |K(p)|, from the counts)."""
+    per_side = OPS_VISIBLE + OPS_UV + OPS_FOOT + OPS_SHADE[shading] + \
+        sum(OPS_WEIGHTS + 4 * c * OPS_PER_TEXEL_CHANNEL for c in read_channels)
+    return covered_sides * per_side + covered_pairs * OPS_LOSS_DIFF + contributions * OPS_CREDIT
 
 
 def dist_env():
@@ -196,7 +217,7 @@ def run_ours(args):
     import torch.distributed as dist
 
     import synth
-    from paper_2404_09758_gb300 import STEP_ADAM, Scene
+    from paper_2404_09758_gb300 import STEP_ADAM, IterState, Scene
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -221,10 +242,14 @@ def run_ours(args):
     st = torch.cuda.Stream(device=dev)
 
     def iteration(it, t):
+        # `it` and `t` are host values (eager warm-up) or one IterState in device memory that the
+        # captured graph reads and advances, so that every replay is the next iteration
         loss.zero_()
         g.estimate_grad(1, it, views, PAIRS, grad, counts, loss=loss, stream=st)
         # Adam with the paper's settings: beta1 0.9, beta2 0.999, learning rate = eps (Section 5)
         g.step(STEP_ADAM, grad, counts, n_total, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+        if isinstance(it, IterState):
+            it.advance(1, 1, stream=st)
 
     # contributions of one iteration (parameter gradients credited), counted exactly
     with torch.cuda.stream(st):
@@ -235,15 +260,25 @@ def run_ours(args):
     grad.zero_()
     counts.zero_()
     assert g.status(st) == 0
+    # pixels each view covers (unperturbed render): the method's work per pair and side
+    covered_px = 0
+    for vw in views:
+        k, _, _ = g.render_idb(vw, side=0, stream=st)
+        st.synchronize()  # the render runs on st; the count below on the current stream
+        covered_px += int((k != -1).sum().item())
+    ops_per_step = method_ops(sc.shading, [int(t.data.shape[2]) for t in sc.textures[:1]],
+                              2.0 * PAIRS * covered_px, float(PAIRS * covered_px), float(contributions))
 
-    # warm up eagerly, then capture one iteration in a CUDA graph (iteration counter and
-    # Adam step live in host-side arguments, so the graph replays one fixed iteration index)
+    # warm up eagerly, then capture one iteration in a CUDA graph; the iteration index and
+    # Adam's step number live in device memory (continuing the warm-up's sequence) and the
+    # graph's last node advances them
     for w in range(max(args.warmup, 1)):
         iteration(w, w + 1)
     st.synchronize()
+    state = IterState(max(args.warmup, 1), max(args.warmup, 1) + 1, device=dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=st):
-        iteration(1000, 1)
+        iteration(state, state)
     st.synchronize()
     for _ in range(args.warmup):
         graph.replay()
@@ -332,20 +367,31 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     # peak: every SM issues one instruction per lane per cycle on its 128 FP32/INT32 lanes
     peak = n_sm * 128 * sm_clock_mhz * 1e6 / 1e12
-    # the timed launches together covered every pixel pair of args.steps iterations
-    achieved = ALU_INSTR_PER_PIXEL_PAIR * px_per_step * args.steps / (fast_total_ms / 1000.0) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
-                "frac": achieved / peak, "traffic": DRAM_BYTES_PER_LAUNCH,
+    # the method's operations of args.steps iterations over the fast kernel's time (the one launch
+    # per call runs every estimate of the call)
+    achieved = ops_per_step * args.steps / (fast_total_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T ops/s",
+                "frac": achieved / peak,
+                "traffic": NCU_DRAM_BYTES_PER_LAUNCH,
+                "work": f"{ops_per_step / px_per_step:.1f} method operations per pixel pair (method_ops: "
+                        f"{covered_px / (N_VIEWS * RENDER * RENDER):.3f} of the pixels covered, "
+                        f"{contributions / px_per_step:.2f} contributions per pixel pair)",
                 "kernel": f"k_estimate_fast<unlit>, {fast_ms:.3f} ms per launch (CUDA events around "
                           f"its {fast_launches} launches on the launching stream)",
                 "peak_source": f"{n_sm} SMs x 128 lanes x {sm_clock_mhz:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)"}
+    if NCU_INSTR_PER_PIXEL_PAIR is not None:
+        # executed thread instructions (ncu, this build) at the kernel's measured time: how busy the
+        # lanes are, wasted work included
+        roofline["issue_efficiency"] = NCU_INSTR_PER_PIXEL_PAIR * px_per_step / (fast_ms / 1000.0) / 1e12 / peak
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "views": N_VIEWS, "pairs_per_view": PAIRS,
                        "render": f"{RENDER}x{RENDER}", "triangles": int(sc.pos_idx.shape[0]),
                        "params": int(g.n_params), "l2": "flushed between timed steps (256 MB write)",
-                       "graph": "estimate + Adam step captured in one CUDA graph",
+                       "graph": "estimate + Adam step + iteration advance captured in one CUDA graph; "
+                                "every replay is the next iteration (device-resident iteration index "
+                                "and Adam step)",
                        "parallelism": f"replicas x{world}"},
             "param_gradients_per_s": world * contributions * args.steps / t_total,
             "touched_params_per_s": world * touched * args.steps / t_total,
@@ -358,11 +404,26 @@ def run_ours(args):
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             # per iteration: 3 binning kernels, the pruning pass, the vertex pass, the fast and the
-            # heavy-bin estimator, the background-loss kernel and the step kernel
-            "gpu_launches": 9 * args.steps,
+            # heavy-bin estimator, the background-loss kernel, the step kernel and the advance
+            "gpu_launches": 10 * args.steps,
             "clocks": clocks}
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
+        if not args.no_sub:
+            # the uneven-batch and scale configurations, a few graph replays each (their own
+            # workloads give the full lines): ms per iteration and pixel pairs per second
+            del graph, g, grad, counts, m, v, flush
+            torch.cuda.empty_cache()
+            sub = {}
+            for name, fn, k in (("uneven32_r512_4views_x_8pairs", measure_uneven, 3),
+                                ("gridsphere1m_4x2048_ggx_r2048_16views_x_16pairs", measure_scale, 2)):
+                r = fn(k, 3)
+                sub[name] = {"ms_per_iteration": r["ms_per_step"], "pixel_pairs_per_s": r["value"],
+                             "param_gradients_per_s": r["param_gradients_per_s"], "steps": k,
+                             "clocks": r["clocks"]}
+                torch.cuda.empty_cache()
+            line["sub_results"] = sub
+            line["atomic_ceiling"] = {"unit": "fp32 red.global.add per s", **measure_atomics()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -370,6 +431,10 @@ def run_ours(args):
 
 
 def run_uneven(args):
+    print(json.dumps(measure_uneven(args.steps, args.warmup)), flush=True)
+
+
+def measure_uneven(steps: int, warmup: int):
     """Uneven batch: 32 seeded assets (1K..200K triangles, 256^2..2048^2 RGB textures), each
     at 512^2 from 4 views with 8 antithetic pairs, all estimates in one persistent launch per
     estimator kernel (autotuned launch shape), then an Adam step per asset; the iteration is
@@ -377,7 +442,7 @@ def run_uneven(args):
     import torch
 
     import synth
-    from paper_2404_09758_gb300 import STEP_ADAM, Batch, Scene
+    from paper_2404_09758_gb300 import STEP_ADAM, Batch, IterState, Scene
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -414,21 +479,24 @@ def run_uneven(args):
         for a in assets:
             a["g"].step(STEP_ADAM, a["grad"], a["counts"], views_n * pairs, a["sc"].eps_pos,
                         [tt[1] for tt in a["g"].textures], m=a["m"], v=a["v"], t=t, stream=st)
+        if isinstance(it, IterState):
+            it.advance(1, 1, stream=st)
 
-    for w in range(args.warmup):
+    for w in range(warmup):
         iteration(w, w + 1)
     st.synchronize()
+    state = IterState(warmup, warmup + 1, device=dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=st):
-        iteration(1000, 1)
+        iteration(state, state)
     st.synchronize()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             with torch.cuda.stream(st):
                 flush.fill_(k & 0xFF)
                 ev[k][0].record(st)
@@ -437,35 +505,40 @@ def run_uneven(args):
         torch.cuda.synchronize()
     t_total = sum(a.elapsed_time(c) for a, c in ev) / 1000.0
     px_per_step = len(assets) * views_n * pairs * render * render
-    value = px_per_step * args.steps / t_total
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps, "higher_is_better": True,
+    value = px_per_step * steps / t_total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1000.0 * t_total / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "uneven32_r512_4views_x_8pairs", "assets": len(assets),
                        "triangles": [int(a["sc"].pos_idx.shape[0]) for a in assets],
                        "texture_sizes": [int(a["sc"].textures[0].data.shape[0]) for a in assets],
                        "l2": "flushed between timed steps (256 MB write)",
-                       "graph": "batched estimate + per-asset Adam steps captured in one CUDA graph",
+                       "graph": "batched estimate + per-asset Adam steps + iteration advance captured in one "
+                                "CUDA graph (every replay is the next iteration)",
                        "tuning": {"pairs_per_item": b.tuning.pairs_per_item,
                                   "blocks_per_sm": b.tuning.blocks_per_sm, "light_bin": b.tuning.light_bin,
                                   "autotune_ms": tune_ms}},
-            "param_gradients_per_s": sum(contributions) * args.steps / t_total,
+            "param_gradients_per_s": sum(contributions) * steps / t_total,
             "contributions_per_asset": contributions,
             # per asset: 3 binning kernels, background loss, vertex pass, Adam step; per call: the
-            # batched pruning pass, the fast and the heavy-bin estimator
-            "gpu_launches": (6 * len(assets) + 3) * args.steps,
+            # batched pruning pass, the fast and the heavy-bin estimator, the advance
+            "gpu_launches": (6 * len(assets) + 4) * steps,
             "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_scale(args):
+    print(json.dumps(measure_scale(args.steps, args.warmup)), flush=True)
+
+
+def measure_scale(steps: int, warmup: int):
     """Scale configuration: 1,048,576-triangle displaced grid sphere, four 2048^2 RGB maps,
     GGX with one light, 2048^2 render, 16 views x 16 antithetic pairs per iteration, the
     iteration (estimate + Adam step) captured in a CUDA graph.  A second configuration."""
     import torch
 
     import synth
-    from paper_2404_09758_gb300 import STEP_ADAM, Scene
+    from paper_2404_09758_gb300 import STEP_ADAM, IterState, Scene
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -496,20 +569,23 @@ def run_scale(args):
         loss.zero_()
         g.estimate_grad(1, it, views, pairs, grad, counts, loss=loss, stream=st)
         g.step(STEP_ADAM, grad, counts, nv * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+        if isinstance(it, IterState):
+            it.advance(1, 1, stream=st)
 
-    for w in range(args.warmup):
+    for w in range(warmup):
         iteration(w, w + 1)
     st.synchronize()
+    state = IterState(warmup, warmup + 1, device=dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=st):
-        iteration(1000, 1)
+        iteration(state, state)
     st.synchronize()
     graph.replay()
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
+        for k in range(steps):
             with torch.cuda.stream(st):
                 flush.fill_(k & 0xFF)
                 ev[k][0].record(st)
@@ -525,19 +601,59 @@ def run_scale(args):
     g.kernel_timing(False)
     assert g.status(st) == 0
     px_per_step = nv * pairs * sc.width * sc.height
-    line = {"metric": METRIC, "value": px_per_step * args.steps / t_total, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_total / args.steps,
+    line = {"metric": METRIC, "value": px_per_step * steps / t_total, "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1000.0 * t_total / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "gridsphere1m_4x2048_ggx_r2048_16views_x_16pairs", "views": nv,
                        "pairs_per_view": pairs, "render": f"{sc.width}x{sc.height}",
                        "triangles": int(sc.pos_idx.shape[0]), "params": int(g.n_params),
                        "l2": "inputs larger than L2; 256 MB flush between timed steps",
-                       "graph": "estimate + Adam step captured in one CUDA graph"},
-            "param_gradients_per_s": contributions * args.steps / t_total,
+                       "graph": "estimate + Adam step + iteration advance captured in one CUDA graph "
+                                "(every replay is the next iteration)"},
+            "param_gradients_per_s": contributions * steps / t_total,
             "contributions_per_step": contributions,
             "fast_kernel_ms": fast_ms / max(fast_n, 1),
-            "gpu_launches": 9 * args.steps,
+            "gpu_launches": 10 * steps,
             "clocks": clk.summary()}
+    return line
+
+
+def measure_atomics(repeats: int = 5):
+    """Ceiling of global float atomics on this GPU (the per-contribution AtomicAdd of Algorithm 2):
+    sge_atomic_bench's fire-and-forget fp32 reductions, one address per thread and 1-of-K hot
+    addresses, timed with CUDA events (best of `repeats`).  Reductions per second."""
+    import torch
+    from paper_2404_09758_gb300 import _abi
+    L = _abi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n_threads, per = 152 * 2048 * 8, 32
+    buf = torch.zeros(n_threads, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    out = {}
+    for name, n_addr in (("distinct", n_threads), ("hot_1_of_32768", 32768), ("hot_1_of_1024", 1024),
+                         ("hot_1_of_32", 32), ("hot_1", 1)):
+        best = None
+        for r in range(repeats + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _abi.check(L.sge_atomic_bench(buf.data_ptr(), n_addr, n_threads, per, st.cuda_stream))
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if r > 0:
+                best = ms if best is None else min(best, ms)
+        out[name] = n_threads * per / (best / 1000.0)
+    return out
+
+
+def run_atomics(args):
+    import torch
+    torch.cuda.set_device(dist_env()[2])
+    rates = measure_atomics()
+    line = {"metric": "global fp32 atomic reductions per second (ceiling of Algorithm 2's AtomicAdd)",
+            "value": rates["distinct"], "unit": "reductions/s", "n_gpus": 1, "steps": 5, "warmup": 1,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": "red_global_add_f32_2.5M_threads_x32"}, "rates": rates}
     print(json.dumps(line), flush=True)
 
 
@@ -721,7 +837,7 @@ def run_converge(args):
     import torch
 
     import synth
-    from paper_2404_09758_gb300 import STEP_ADAM, ControlMesh, Scene
+    from paper_2404_09758_gb300 import STEP_ADAM, ControlMesh, IterState, Scene
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -758,29 +874,51 @@ def run_converge(args):
         st.synchronize()
         return float(e.sum().item())
 
-    def iteration(it, t):
+    # one iteration, captured once: the iteration index and Adam's step number live in device
+    # memory (state), read by the estimate and the step and advanced by the graph's last node
+    state = IterState(0, 1, device=dev)
+
+    def iteration():
         if not control:
-            g.estimate_grad(1, it, views, pairs, grad, counts, stream=st)
-            g.step(STEP_ADAM, grad, counts, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
-            return
-        cm.refine(stream=st)
-        g.estimate_grad(1, it, views, pairs, grad, counts, stream=st)
-        cm.control_sums(grad, grad_c, stream=st)
-        grad.zero_()
-        counts.zero_()
-        opt.step(STEP_ADAM, grad_c, counts_c, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=t, stream=st)
+            g.estimate_grad(1, state, views, pairs, grad, counts, stream=st)
+            g.step(STEP_ADAM, grad, counts, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=state, stream=st)
+        else:
+            cm.refine(stream=st)
+            g.estimate_grad(1, state, views, pairs, grad, counts, stream=st)
+            cm.control_sums(grad, grad_c, stream=st)
+            grad.zero_()
+            counts.zero_()
+            opt.step(STEP_ADAM, grad_c, counts_c, len(views) * pairs, sc.eps_pos, lr_tex, m=m, v=v, t=state,
+                     stream=st)
+        state.advance(1, 1, stream=st)
 
     e0 = image_error()
-    # eager launches: an iteration is ~12 launches against a GPU time of tens of milliseconds, and
-    # every iteration needs its own sign keys and Adam step number
+    # capture on a scratch copy of the optimised state (m, v, parameters are restored after the
+    # capture's warm-up launch), then replay: iteration k of the loop is replay k
+    saved = [p.detach().clone() for p in opt.param_groups()]
+    with torch.cuda.stream(st):
+        iteration()
+    st.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        iteration()
+    st.synchronize()
+    for p, q in zip(opt.param_groups(), saved):
+        p.copy_(q)
+    if control:
+        cm.refine(stream=st)
+    m.zero_()
+    v.zero_()
+    grad.zero_()
+    counts.zero_()
+    state.tensor.copy_(torch.tensor([0, 1], dtype=torch.int32))
     torch.cuda.synchronize()
     curve = [(0.0, e0)]
     t0 = time.perf_counter()
     n_iter = 0
     next_sample = 1.0
     while True:
-        with torch.cuda.stream(st):
-            iteration(n_iter, n_iter + 1)
+        graph.replay()
         st.synchronize()  # no backlog: the clock reads finished work
         n_iter += 1
         el = time.perf_counter() - t0
@@ -797,11 +935,13 @@ def run_converge(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": sc.name + "_16views_x_16pairs_adam" + ("_control_mesh" if control else ""),
                        "triangles": int(len(sc.pos_idx)), "params": int(opt.n_params),
-                       "seconds": args.seconds, "graph": "none (eager; the error is measured between iterations)"},
+                       "seconds": args.seconds,
+                       "graph": "one iteration captured in a CUDA graph and replayed (device-resident iteration "
+                                "index and Adam step); the error is measured between replays"},
             "initial_error": e0, "curve": curve, "reduction": curve[-1][1] / e0,
-            # per iteration: 4 binning and pruning kernels, the vertex pass, the two estimators, the step
-            # (+ the two refine products of the control mesh)
-            "gpu_launches": (10 if control else 8) * n_iter}
+            # per iteration: 4 binning and pruning kernels, the vertex pass, the two estimators, the
+            # background loss, the step, the advance (+ the two refine products of the control mesh)
+            "gpu_launches": (12 if control else 10) * n_iter}
     print(json.dumps(line), flush=True)
 
 
@@ -811,18 +951,21 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default workload only: skip the uneven-batch and scale sub-results")
     ap.add_argument("--seconds", type=float, default=60.0, help="wall time of --workload converge")
     ap.add_argument("--control", choices=["none", "catmull_clark"], default="none",
                     help="--workload converge: optimise a Catmull-Clark control mesh instead of the surface")
     ap.add_argument("--workload", choices=["batched", "uneven", "scale", "full_image", "converge", "transparent",
-                                           "soup"],
+                                           "soup", "atomics"],
                     default="batched",
                     help="batched: the headline configuration; uneven: 32 assets in one batched call; "
                          "scale: 1M triangles, GGX, 2048^2; full_image: Eq. 4's whole-image estimator on "
                          "the batched configuration; converge: optimise the autograd configuration "
                          "for --seconds and report the image error against time; transparent: deep ID "
                          "buffers of three overlapping semi-transparent spheres; soup: Section 6.1's "
-                         "per-pixel vs full-image comparison on triangle soups")
+                         "per-pixel vs full-image comparison on triangle soups; atomics: the ceiling of "
+                         "global fp32 atomic reductions")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -840,6 +983,8 @@ def main():
         run_transparent(args)
     elif args.workload == "soup":
         run_soup(args)
+    elif args.workload == "atomics":
+        run_atomics(args)
     else:
         run_ours(args)
 

@@ -115,10 +115,19 @@ typedef struct {
 typedef struct {
     int32_t max_views_per_call; /* views per estimate call the workspace is sized for (default n_views, <= 64) */
     int64_t bin_capacity;       /* triangle-tile bin entries over those views (default (6 n_triangles + 8 tiles) * views) */
-    int32_t pairs_per_item;     /* antithetic pairs one CTA runs per (view, tile) item (default 16, <= 64) */
+    int32_t pairs_per_item;     /* antithetic pairs one CTA runs per (view, tile) item (default 8, <= 64) */
     int32_t blocks_per_sm;      /* persistent CTAs per SM (default: as many as fit) */
     int32_t max_pairs_per_call; /* pairs per view projected at once (default 64); more run in blocks */
+    int32_t footprint;          /* texels a pixel credits (SGE_FOOT_*; default bilinear)           */
 } sge_config;
+
+/* Texels a pixel credits for each texture the shading reads (Algorithm 2's contributor set).
+ * Rendering samples bilinearly either way.  SGE_FOOT_BILINEAR credits the 2x2 bilinear
+ * footprint, which makes Eq. 8 unbiased for textures the image depends on linearly;
+ * SGE_FOOT_NEAREST credits the single texel whose square holds the sample point,
+ * (floor(u W) wrapped, floor(v H) clamped), as Section 4.4 ("Textures") describes. */
+#define SGE_FOOT_BILINEAR 0
+#define SGE_FOOT_NEAREST 1
 
 typedef struct {
     int32_t kind;                       /* SGE_STEP_*                                   */
@@ -246,6 +255,35 @@ int sge_gradient(sge_scene *scene, const float *grad_sums, int64_t n_pairs_total
 int sge_step(sge_scene *scene, const sge_opt *opt, float *grad_sums, uint32_t *counts,
              int64_t n_pairs_total, float *adam_m, float *adam_v, sge_stream_t stream);
 
+/* Optimizer loop captured once in a CUDA graph.  Section 5 draws fresh signs for every
+ * estimate (Eq. 9 averages independent ones) and runs one Adam step per iteration, so a
+ * replayed graph must not bake the iteration index or Adam's step number into its launch
+ * arguments.  These forms read both from a small state object in device memory when their
+ * kernels run, and sge_iter_advance moves it on: capture estimate -> step -> advance once,
+ * then every replay is the next iteration.  The state is caller-owned device memory
+ * (8 bytes, 4-byte aligned); initialise it (e.g. {iter0, 1}) before the first replay. */
+typedef struct {
+    uint32_t iter;   /* iteration index whose sign vectors the next estimate draws          */
+    int32_t t;       /* Adam step number of the next step, >= 1                             */
+} sge_iter_state;
+
+/* sge_estimate_grad with the iteration index read from state->iter (device) by the kernels
+ * at run time; every other argument, output and error is that of sge_estimate_grad, and the
+ * result equals sge_estimate_grad(..., state->iter, ...) at that moment. */
+int sge_estimate_grad_state(sge_scene *scene, uint64_t seed, const sge_iter_state *state, const int32_t *view_ids,
+                            int32_t n_views, int32_t pairs_per_view, float *grad_sums, uint32_t *counts,
+                            float *loss_out, float *delta_f_out, sge_stream_t stream);
+
+/* sge_step with Adam's step number read from state->t (device) at run time (opt->t is
+ * ignored); the bias corrections 1 - beta^t are formed on the device in float32.  SGD and
+ * the per-pixel mean do not read the state. */
+int sge_step_state(sge_scene *scene, const sge_opt *opt, const sge_iter_state *state, float *grad_sums,
+                   uint32_t *counts, int64_t n_pairs_total, float *adam_m, float *adam_v, sge_stream_t stream);
+
+/* One device thread adds d_iter to state->iter and d_t to state->t, stream-ordered after the
+ * work enqueued before it (an iteration's last node in a captured loop). */
+int sge_iter_advance(sge_iter_state *state, int32_t d_iter, int32_t d_t, sge_stream_t stream);
+
 /* One asset of a batched call: a scene with its views and its own outputs. */
 typedef struct {
     sge_scene *scene;          /* distinct within one call                                  */
@@ -279,6 +317,12 @@ typedef struct {
 int sge_estimate_grad_batch(const sge_batch_entry *entries, int32_t n_entries, uint64_t seed, uint32_t iter,
                             int32_t pairs_per_view, const sge_batch_tuning *tuning, sge_stream_t stream);
 
+/* sge_estimate_grad_batch with the iteration index read from state->iter (device) when the
+ * kernels run (see sge_iter_state); results, outputs and errors as sge_estimate_grad_batch's. */
+int sge_estimate_grad_batch_state(const sge_batch_entry *entries, int32_t n_entries, uint64_t seed,
+                                  const sge_iter_state *state, int32_t pairs_per_view,
+                                  const sge_batch_tuning *tuning, sge_stream_t stream);
+
 /* Autotuner of sge_estimate_grad_batch's launch shape (no counterpart in the paper,
  * which runs one asset at a time) for these entries: times
  * candidate shapes (pairs per item 1..64, 1 or 2 CTAs per SM, light-bin limit
@@ -303,8 +347,11 @@ int sge_status(sge_scene *scene, sge_stream_t stream, int32_t *device_status);
  * be NULL).  Its scratch is a fixed array in the library's device memory,
  * SGE_STATIC_SCRATCH limits below, held on every GPU that loads the library until
  * the process exits; requests beyond the limits return SGE_ERR_INVALID_ARG and
- * launch nothing, and transparent scenes SGE_ERR_UNSUPPORTED.  The first call on a device (that device current) looks up the
- * array's address; make it before any stream capture.  All calls share the
+ * launch nothing, and transparent scenes SGE_ERR_UNSUPPORTED; the descriptor is
+ * checked exactly as sge_create_scene checks it.  The first call on a device (that
+ * device current) looks up the array's address; make it before any stream capture.
+ * The address is kept per device and CUDA context: the first call after a
+ * cudaDeviceReset looks it up again, so it too should precede any capture.  All calls share the
  * array: calls that overlap on the GPU (other streams or threads) race; order
  * them on one stream.  device_status (device int32, or NULL) receives SGE_OK or
  * SGE_ERR_BIN_OVERFLOW (tiles whose lists did not fit render as background).
@@ -316,6 +363,14 @@ int sge_status(sge_scene *scene, sge_stream_t stream, int32_t *device_status);
 int sge_render_idb_static(const sge_scene_desc *desc, int32_t view, uint64_t seed, uint32_t iter,
                           uint32_t pair, int32_t side, uint64_t *depth_id, float *uv, float *rgb,
                           int32_t *device_status, sge_stream_t stream);
+
+/* Throughput probe of global float atomics, for benchmarks (the paper has no counterpart; it
+ * measures the ceiling of Algorithm 2's per-contribution AtomicAdd).  Enqueues n_threads device
+ * threads that each add 1.0f per_thread times to buf[i mod n_addr] (device float32 [n_addr],
+ * caller-owned; its contents grow by the additions), as fire-and-forget reductions.  Time it with
+ * CUDA events on `stream`: n_threads * per_thread reductions.  n_addr = n_threads gives one
+ * address per thread; small n_addr gives 1-of-n_addr hot addresses. */
+int sge_atomic_bench(float *buf, int64_t n_addr, int64_t n_threads, int32_t per_thread, sge_stream_t stream);
 
 /* Timing of the estimator kernels, for benchmarks (the paper has no counterpart).
  * While enabled, each sge_estimate_grad call records CUDA events on its stream right

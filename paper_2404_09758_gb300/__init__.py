@@ -15,13 +15,13 @@ import ctypes as C
 from typing import List, Optional, Sequence
 
 from . import _abi
-from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, MAX_LAYERS, MAX_TEXTURES, MAX_VIEWS_PER_CALL, OK,
+from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, FOOT_BILINEAR, FOOT_NEAREST, MAX_LAYERS, MAX_TEXTURES, MAX_VIEWS_PER_CALL, OK,
                    SHADE_GGX, SHADE_LAMBERT, SHADE_TRANSPARENT, SHADE_UNLIT, STEP_ADAM, STEP_SGD, STEP_SGD_MEAN,
                    SGEError)
 from ._build import build
 
-__all__ = ["Scene", "Batch", "ControlMesh", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
-           "STEP_SGD_MEAN", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
+__all__ = ["Scene", "Batch", "ControlMesh", "IterState", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
+           "STEP_SGD_MEAN", "FOOT_BILINEAR", "FOOT_NEAREST", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
 
 
 def load(build_if_missing: bool = False):
@@ -54,7 +54,8 @@ class Scene:
                  width: int, height: int, targets=None, near: float = 0.1, shading: int = 0,
                  light_dir=(0.0, 0.0, 1.0), light_rgb=(1.0, 1.0, 1.0), ambient: float = 0.0,
                  background=(0.0, 0.0, 0.0), max_views_per_call: int = 0, bin_capacity: int = 0,
-                 pairs_per_item: int = 0, blocks_per_sm: int = 0, max_pairs_per_call: int = 0, device=None):
+                 pairs_per_item: int = 0, blocks_per_sm: int = 0, max_pairs_per_call: int = 0,
+                 footprint: int = 0, device=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("sge needs a CUDA device; there is no CPU path")
@@ -114,7 +115,7 @@ class Scene:
         d.ambient = float(ambient)
         self._desc = d
         cfg = _abi.Config(int(max_views_per_call), int(bin_capacity), int(pairs_per_item), int(blocks_per_sm),
-                          int(max_pairs_per_call))
+                          int(max_pairs_per_call), int(footprint))
         self._cfg = cfg
         nbytes = C.c_size_t()
         _abi.check(L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(nbytes)))
@@ -223,13 +224,20 @@ class Scene:
         arr = (C.c_int32 * len(view_ids))(*[int(v) for v in view_ids])
         return arr, len(view_ids)
 
-    def estimate_grad(self, seed: int, it: int, view_ids: Sequence[int], pairs_per_view: int, grad, counts,
+    def estimate_grad(self, seed: int, it, view_ids: Sequence[int], pairs_per_view: int, grad, counts,
                       loss=None, delta_f=None, stream=None) -> None:
-        """Accumulate Eq. 9's numerators into grad [d] and counts [d] (batched, one launch)."""
+        """Accumulate Eq. 9's numerators into grad [d] and counts [d] (batched, one launch).
+        `it` is the iteration index, or an IterState whose device word the kernels read when
+        they run (a loop captured once in a CUDA graph)."""
         arr, n = self._views(view_ids)
-        _abi.check(_abi.load().sge_estimate_grad(self._h, int(seed), int(it), arr, n, int(pairs_per_view),
+        L = _abi.load()
+        if isinstance(it, IterState):
+            _abi.check(L.sge_estimate_grad_state(self._h, int(seed), it.ptr, arr, n, int(pairs_per_view),
                                                  _ptr(grad), _ptr(counts), _ptr(loss), _ptr(delta_f),
                                                  _stream_ptr(stream)))
+            return
+        _abi.check(L.sge_estimate_grad(self._h, int(seed), int(it), arr, n, int(pairs_per_view),
+                                       _ptr(grad), _ptr(counts), _ptr(loss), _ptr(delta_f), _stream_ptr(stream)))
 
     def estimate_grad_plain(self, seed: int, it: int, view_ids: Sequence[int], pairs_per_view: int, grad,
                             counts, loss=None, stream=None) -> None:
@@ -287,17 +295,48 @@ class Scene:
         return out
 
     def step(self, kind: int, grad, counts, n_pairs_total: int, lr_pos: float, lr_tex: Sequence[float],
-             m=None, v=None, t: int = 1, beta1: float = 0.9, beta2: float = 0.999, adam_eps: float = 1e-8,
+             m=None, v=None, t=1, beta1: float = 0.9, beta2: float = 0.999, adam_eps: float = 1e-8,
              stream=None) -> None:
-        """Descent step D on every group (Section 5); zeroes grad and counts."""
+        """Descent step D on every group (Section 5); zeroes grad and counts.  `t` is Adam's step
+        number, or an IterState whose device word the step reads when it runs."""
         o = _abi.Opt()
         o.kind = int(kind)
         o.lr_pos = float(lr_pos)
         for k, lr in enumerate(lr_tex):
             o.lr_tex[k] = float(lr)
-        o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), int(t)
-        _abi.check(_abi.load().sge_step(self._h, C.byref(o), _ptr(grad), _ptr(counts), int(n_pairs_total),
+        L = _abi.load()
+        if isinstance(t, IterState):
+            o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), 1
+            _abi.check(L.sge_step_state(self._h, C.byref(o), t.ptr, _ptr(grad), _ptr(counts), int(n_pairs_total),
                                         _ptr(m), _ptr(v), _stream_ptr(stream)))
+            return
+        o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), int(t)
+        _abi.check(L.sge_step(self._h, C.byref(o), _ptr(grad), _ptr(counts), int(n_pairs_total),
+                              _ptr(m), _ptr(v), _stream_ptr(stream)))
+
+
+class IterState:
+    """The (iteration index, Adam step number) of an optimizer loop in device memory
+    (sge_iter_state): estimate_grad and step read it when their kernels run, and advance()
+    enqueues its increment, so a loop captured once in a CUDA graph draws fresh signs and takes
+    the next Adam step on every replay (Section 5)."""
+
+    def __init__(self, it: int = 0, t: int = 1, device=None):
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.tensor = torch.tensor([int(it), int(t)], dtype=torch.int32, device=dev)
+
+    @property
+    def ptr(self) -> int:
+        return int(self.tensor.data_ptr())
+
+    def advance(self, d_iter: int = 1, d_t: int = 1, stream=None) -> None:
+        _abi.check(_abi.load().sge_iter_advance(self.ptr, int(d_iter), int(d_t), _stream_ptr(stream)))
+
+    def value(self):
+        """(iteration, t) as they stand (synchronises)."""
+        it, t = (int(x) for x in self.tensor.tolist())
+        return it & 0xFFFFFFFF, t
 
 
 def draw_views(seed: int, it: int, n_views: int, count: int) -> List[int]:
@@ -410,10 +449,17 @@ class Batch:
             E.grad_sums, E.counts, E.loss_out = _ptr(grad), _ptr(counts), _ptr(loss)
         self.tuning = _abi.BatchTuning()
 
-    def estimate_grad(self, seed: int, it: int, pairs_per_view: int, stream=None) -> None:
-        _abi.check(_abi.load().sge_estimate_grad_batch(self._arr, len(self.scenes), int(seed), int(it),
+    def estimate_grad(self, seed: int, it, pairs_per_view: int, stream=None) -> None:
+        """Every entry's estimates in one persistent launch per kernel; `it` is the iteration
+        index or an IterState read on the device (a loop captured in a CUDA graph)."""
+        L = _abi.load()
+        if isinstance(it, IterState):
+            _abi.check(L.sge_estimate_grad_batch_state(self._arr, len(self.scenes), int(seed), it.ptr,
                                                        int(pairs_per_view), C.byref(self.tuning),
                                                        _stream_ptr(stream)))
+            return
+        _abi.check(L.sge_estimate_grad_batch(self._arr, len(self.scenes), int(seed), int(it),
+                                             int(pairs_per_view), C.byref(self.tuning), _stream_ptr(stream)))
 
     def autotune(self, pairs_per_view: int, repeats: int = 2, stream=None) -> float:
         """Pick the launch shape for these entries (zeroes their buffers); returns its ms."""

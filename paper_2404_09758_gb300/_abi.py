@@ -18,6 +18,7 @@ MAX_LAYERS = 4  # fragments per pixel of a transparent scene's deep ID buffer
 
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_BIN_OVERFLOW, ERR_BAD_INDEX, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
 STEP_SGD, STEP_ADAM, STEP_SGD_MEAN = 0, 1, 2
+FOOT_BILINEAR, FOOT_NEAREST = 0, 1
 SHADE_UNLIT, SHADE_LAMBERT, SHADE_GGX, SHADE_TRANSPARENT = 0, 1, 2, 3
 
 EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_targets", "sge_validate",
@@ -25,7 +26,8 @@ EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_
            "sge_destroy_scene", "sge_last_error", "sge_render_idb_static", "sge_loss", "sge_gradient",
            "sge_estimate_grad_batch", "sge_autotune_batch", "sge_kernel_timing", "sge_kernel_time",
            "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image",
-           "sge_refine", "sge_render_deep")
+           "sge_refine", "sge_render_deep", "sge_estimate_grad_state", "sge_step_state", "sge_iter_advance",
+           "sge_estimate_grad_batch_state", "sge_atomic_bench")
 
 
 class Texture(C.Structure):
@@ -47,7 +49,7 @@ class SceneDesc(C.Structure):
 class Config(C.Structure):
     _fields_ = [("max_views_per_call", C.c_int32), ("bin_capacity", C.c_int64),
                 ("pairs_per_item", C.c_int32), ("blocks_per_sm", C.c_int32),
-                ("max_pairs_per_call", C.c_int32)]
+                ("max_pairs_per_call", C.c_int32), ("footprint", C.c_int32)]
 
 
 class BatchEntry(C.Structure):
@@ -101,6 +103,11 @@ def load(build_if_missing: bool = False):
         L.sge_estimate_grad.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P, P]
         L.sge_estimate_grad_plain.argtypes = [P, U64, U32, P, I32, I32, P, P, P, P]
         L.sge_step.argtypes = [P, P, P, P, I64, P, P, P]
+        L.sge_estimate_grad_state.argtypes = [P, U64, P, P, I32, I32, P, P, P, P, P]
+        L.sge_step_state.argtypes = [P, P, P, P, P, I64, P, P, P]
+        L.sge_iter_advance.argtypes = [P, I32, I32, P]
+        L.sge_estimate_grad_batch_state.argtypes = [P, I32, U64, P, I32, P, P]
+        L.sge_atomic_bench.argtypes = [P, I64, I64, I32, P]
         L.sge_status.argtypes = [P, P, C.POINTER(I32)]
         L.sge_render_idb_static.argtypes = [P, I32, U64, U32, U32, I32, P, P, P, P, P]
         L.sge_loss.argtypes = [P, P, I32, P, P]

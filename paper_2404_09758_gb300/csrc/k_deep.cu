@@ -116,7 +116,8 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     const int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
     const float u = persp_interp(pw, __ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t2));
     const float v = persp_interp(pw, __ldg(S.uvs + 2 * t0 + 1), __ldg(S.uvs + 2 * t1 + 1), __ldg(S.uvs + 2 * t2 + 1));
-    const Foot f = footprint(u, v, A.w, A.h);
+    Foot f = footprint(u, v, A.w, A.h);
+    if (S.foot_nearest) f.nearest = nearest_texel(u, v, A.w, A.h);
     float a[4];
     sample_tex(A, f, key, side, a);
     const float al = fminf(fmaxf(a[3], 0.0f), 1.0f);
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
   const int row = row0 + (int)blockIdx.y;
   const int slot = row / a.pair_count, pair = a.pair_begin + row % a.pair_count;
   const int view = vl.id[slot];
-  const uint64_t key = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)pair);
+  const uint64_t key = pair_key(a.seed, iter_of(a), (uint32_t)view, (uint32_t)pair);
   const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
   const int dx = threadIdx.x % TILE, dy = threadIdx.x / TILE;
   const int px = tx * TILE + dx, py = ty * TILE + dy;
@@ -178,6 +179,10 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     auto credit_keys = [&](int tri, const Foot& f) {
 #pragma unroll
       for (int v = 0; v < 3; ++v) add(vkey(__ldg(S.pidx + 3 * tri + v)));
+      if (S.foot_nearest) {
+        add(tkey(A.index, f.nearest));
+        return;
+      }
       add(tkey(A.index, f.y0 * A.w + f.x0));
       add(tkey(A.index, f.y0 * A.w + f.x1));
       add(tkey(A.index, f.y1 * A.w + f.x0));

@@ -271,11 +271,11 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
       cand[4 * w + 2] = (uint32_t)cw.z;
       cand[4 * w + 3] = (uint32_t)cw.w;
     }
-    const int ncand = ws.ncand[ti * TILE_PX + tid];
+    const int ncand = ws.ncand[ti * TILE_PX + tid] & 127;  // bit 7: surely covered (the fast kernel's)
     const bool all_live = ncand > kHeavyCand;
 
     for (int pair = p0; pair < p1; ++pair) {
-      const uint64_t pkey = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)pair);
+      const uint64_t pkey = pair_key(a.seed, iter_of(a), (uint32_t)view, (uint32_t)pair);
       const long long vb = ((long long)slot * ws.max_pairs + (pair - a.pair_begin)) * S.nv;
       unsigned long long best[2] = {~0ull, ~0ull};
       int bestj[2] = {-1, -1}, bestc[2] = {-1, -1};

@@ -49,14 +49,13 @@ struct Model {
   static constexpr int NREAD = SH == SHADE_UNLIT ? 1 : (SH == SHADE_LAMBERT ? 2 : 4);
   // footprints computed and inserted per side: one for a group, one per texture otherwise
   static constexpr int NFOOT = GR ? 1 : NREAD;
-  // at about one texel per pixel a tile's bilinear footprints hold ~300 texels per footprint;
-  // the lit models run one CTA per SM (register-bound), so their tables can take the shared
-  // memory the second CTA of the unlit model would use
-  static constexpr int TABLE = SH == SHADE_UNLIT ? 512 : (GR ? 1024 : 2048);
+  // a tile's bilinear footprints over a run of pairs hold a few hundred texels at about one
+  // texel per pixel, more where the surface is seen at a grazing angle
+  static constexpr int TABLE = (SH == SHADE_UNLIT || GR) ? 1024 : 2048;
   static constexpr int TSC = GR ? 4 * NREAD : 4;  // channel sums per table entry
 };
 
-// One side of a staged triangle (the unperturbed set-up also keeps its margin).
+// One side of a staged triangle (unperturbed set-up for the pruning pass, with its margin).
 struct __align__(16) TriS {
   long long e0[3];  // oriented edge functions at the tile's first pixel centre
   int bias;         // bit k set: edge k is not a top/left edge
@@ -68,12 +67,26 @@ struct __align__(16) TriS {
   int pad[2];
 };
 
+// One side of a live triangle set up for one pair of the estimator (the triangle's id is the
+// item's btri[]); 80 bytes.
+struct __align__(16) SideTri {
+  long long e0[3];  // oriented edge functions at the tile's first pixel centre
+  int a[3], b[3];   // oriented edge steps per fixed-point unit in x and y
+  int flags;        // bits 0-2: edge k is not a top/left edge; bit 3: drawn on this side; bit 4: every
+                    // edge function over the tile fits 32 bits (|a|, |b| < 2^16, |e0| < 2^29)
+  float inv_area;
+  float z[3], iw[3];
+};
+static_assert(sizeof(SideTri) == 80, "SideTri layout");
+constexpr int kDrawn = 8, kSmall = 16;
+
 template <int TABLE, int TSC>
 struct FastSmem {
-  TriS side[2][NB];
+  SideTri side[2][NB];
   float uv[NB][6];
   int vid[NB][3];
-  int btri[NB];          // triangle id of each bin entry
+  int btri[NB];          // triangle id of each live entry
+  uint32_t zminb[NB];    // ordered bits of its smallest depth under any perturbation of the call
   uint32_t sgn9[2][NB];  // bit 3k+c: coordinate c of corner k has s = -1 (by pair parity)
   float A_tri[NB];
   uint32_t n_tri[NB];
@@ -84,15 +97,20 @@ struct FastSmem {
   uint32_t tkey[TABLE];
   float tA[TABLE];
   uint32_t tn[TABLE];
-  uint32_t tstamp[TABLE];
-  uint32_t tsb[2][TABLE];  // sign bits of the stamped pair, by pair parity
   float tS[TSC][TABLE];
   uint32_t tcnt[TABLE];
-  uint64_t pk[kMaxPairsPerItem];  // sign keys of the run's pairs
+  uint32_t tsb[TABLE];   // the current pair's sign bits of the entry's channels (4 r + c), stored by
+                         // every pixel that samples the texel (all store the same value)
+  uint16_t used[TABLE];  // slots holding a key in this item, in insertion order
+  uint32_t n_used;
   float m[16];
   float red[TILE_PX / 32];
   uint32_t item;
 };
+
+// Two unlit CTAs share an SM: 228 KB of shared memory less 1 KB reserved per CTA.
+static_assert(2 * (sizeof(FastSmem<Model<SHADE_UNLIT>::TABLE, Model<SHADE_UNLIT>::TSC>) + 1024) <= 228 * 1024,
+              "the unlit fast estimator must fit two CTAs per SM");
 
 __device__ __forceinline__ void store_side(TriS& d, const Tri& t, int tri) {
   if (!t.ok) {
@@ -114,21 +132,51 @@ __device__ __forceinline__ void store_side(TriS& d, const Tri& t, int tri) {
   d.tri = tri;
 }
 
-// Exact coverage at pixel offset (dx, dy): oriented edge functions into e, or false.
-__device__ __forceinline__ bool cover_s(const TriS& t, int dx, int dy, long long e[3]) {
-  bool in = true;
+__device__ __forceinline__ void store_side_tri(SideTri& d, const Tri& t) {
+  if (!t.ok) {
+    d.flags = 0;
+    return;
+  }
+  int flags = kDrawn;
+  bool small = true;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    e[k] = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
-    in = in && (e[k] - ((t.bias >> k) & 1) >= 0);
+    d.e0[k] = t.e0[k];
+    d.a[k] = t.a[k];
+    d.b[k] = t.b[k];
+    d.z[k] = t.z[k];
+    d.iw[k] = t.iw[k];
+    flags |= (t.bias[k] ? 1 : 0) << k;
+    // over the tile's pixel offsets (0..15) * 256: |a dx| + |b dy| < 2 * 2^28, so |e| < 2^30
+    small = small && abs(t.a[k]) < (1 << 16) && abs(t.b[k]) < (1 << 16) && t.e0[k] > -(1ll << 29) &&
+            t.e0[k] < (1ll << 29);
   }
-  return in;
+  d.flags = flags | (small ? kSmall : 0);
+  d.inv_area = t.inv_area;
 }
 
-__device__ __forceinline__ unsigned long long key_s(const TriS& t, const long long e[3]) {
-  float l[3];
-  lambdas(e, t.inv_area, l);
-  return ((unsigned long long)ordered_bits(interp_depth(l, t.z)) << 32) | (uint32_t)t.tri;
+// Exact coverage at pixel offset (dx, dy) and the barycentric weights lambda_k = E_k / area there
+// (as lambdas() forms them): 32-bit edge functions for a small triangle, 64-bit otherwise; the
+// integers are the same, and so is each float conversion.
+__device__ __forceinline__ bool cover_lambdas(const SideTri& t, int dx, int dy, float l[3]) {
+  bool in = true;
+  if (t.flags & kSmall) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = (int)t.e0[k] + t.a[k] * (dx * 256) + t.b[k] * (dy * 256);
+      in = in && (e - ((t.flags >> k) & 1) >= 0);
+      l[k] = __fmul_rn(__int2float_rn(e), t.inv_area);
+    }
+  } else {
+    long long e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      e[k] = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
+      in = in && (e[k] - ((t.flags >> k) & 1) >= 0);
+    }
+    lambdas(e, t.inv_area, l);
+  }
+  return in;
 }
 
 __device__ __forceinline__ uint32_t hslot(uint32_t k, int table) {
@@ -138,38 +186,21 @@ __device__ __forceinline__ uint32_t hslot(uint32_t k, int table) {
   return k & (uint32_t)(table - 1);
 }
 
-// Find or insert a texel key; the first pixel to touch the entry in this pair draws
-// the pair's signs of the texel's channels (stamp = pair + 1) into tsb[par].
-template <int TABLE, int TSC, int NG>
-__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE, TSC>& sm, uint32_t key, uint32_t stamp,
-                                                 const SceneDev& S, const TexDev& T, uint64_t pkey, int par) {
+// Find or insert a texel key (keys stay for the whole item; a new one is listed in used[]).
+template <int TABLE, int TSC>
+__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE, TSC>& sm, uint32_t key) {
   uint32_t slot = hslot(key, TABLE);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
     uint32_t k = *(volatile uint32_t*)&sm.tkey[slot];
     if (k == EMPTY) {
       k = atomicCAS(&sm.tkey[slot], EMPTY, key);
-      if (k == EMPTY) k = key;
-    }
-    if (k == key) {
-      if (*(volatile uint32_t*)&sm.tstamp[slot] != stamp && atomicExch(&sm.tstamp[slot], stamp) != stamp) {
-        uint32_t sb = 0;
-        if (NG == 0) {
-          const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
-          for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << c;
-        } else {
-          // a group entry: the texel's channels of every read texture, at bit 4 r + c
-#pragma unroll
-          for (int r = 0; r < NG; ++r) {
-            const TexDev& U = S.rtex[r];
-            const long long base = U.offset + (long long)(key & 0x0FFFFFFFu) * U.c;
-            for (int c = 0; c < U.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(base + c)) << (4 * r + c);
-          }
-        }
-        sm.tsb[par][slot] = sb;
+      if (k == EMPTY) {
+        sm.used[atomicAdd(&sm.n_used, 1u)] = (uint16_t)slot;
+        return slot;
       }
-      return slot;
     }
+    if (k == key) return slot;
     slot = (slot + 1) & (TABLE - 1);
   }
   return NOSLOT;
@@ -181,20 +212,41 @@ __device__ __forceinline__ int foot_texel(const Foot& f, int q, int w) {
 }
 
 // Texel id of footprint corner q from the packed (x0,y0) id and its edge flags.
-__device__ __forceinline__ long long texel_of(uint32_t pk, int q, int w) {
-  long long t = pk & 0x3FFFFFFFu;
-  if (q & 1) t += (pk & (1u << 30)) ? -(long long)(w - 1) : 1;
+__device__ __forceinline__ int texel_of(uint32_t pk, int q, int w) {
+  int t = (int)(pk & 0x3FFFFFFFu);
+  if (q & 1) t += (pk & (1u << 30)) ? -(w - 1) : 1;
   if ((q & 2) && !(pk & (1u << 31))) t += w;
   return t;
 }
 
+// Sign bits of texel t's channels (bit c: s = -1) in one texture's sign plane of an estimate.
+__device__ __forceinline__ uint32_t plane_nibble(const uint32_t* plane, int t) {
+  return (__ldg(plane + (t >> 3)) >> (4 * (t & 7))) & 0xFu;
+}
+
+// Every slot of the table empty (once per call of the estimator loop in a CTA).
 template <int TABLE, int TSC>
-__device__ __forceinline__ void clear_item_table(FastSmem<TABLE, TSC>& sm) {
+__device__ __forceinline__ void clear_table(FastSmem<TABLE, TSC>& sm) {
   for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
     sm.tkey[s] = EMPTY;
     sm.tA[s] = 0.0f;
     sm.tn[s] = 0u;
-    sm.tstamp[s] = 0u;
+    sm.tcnt[s] = 0u;
+    sm.tsb[s] = 0u;
+#pragma unroll
+    for (int c = 0; c < TSC; ++c) sm.tS[c][s] = 0.0f;
+  }
+  if (threadIdx.x == 0) sm.n_used = 0;
+}
+
+// The n_used slots an item used back to empty (after its flush).
+template <int TABLE, int TSC>
+__device__ __forceinline__ void clear_used(FastSmem<TABLE, TSC>& sm, uint32_t n_used) {
+  for (uint32_t i = threadIdx.x; i < n_used; i += blockDim.x) {
+    const uint32_t s = sm.used[i];
+    sm.tkey[s] = EMPTY;
+    sm.tA[s] = 0.0f;
+    sm.tn[s] = 0u;
     sm.tcnt[s] = 0u;
 #pragma unroll
     for (int c = 0; c < TSC; ++c) sm.tS[c][s] = 0.0f;
@@ -202,25 +254,32 @@ __device__ __forceinline__ void clear_item_table(FastSmem<TABLE, TSC>& sm) {
 }
 
 // Fold a pair's credits (table entries and triangle corners) into the per-channel sums with
-// that pair's signs (texel signs in tsb[parity], vertex signs in sgn9[parity]).
-template <int TABLE, int TSC>
+// that pair's signs: texel signs in tsb (stored while sampling), vertex signs in sgn9[parity].
+template <int TABLE, int TSC, bool GR, int NREAD>
 __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE, TSC>& sm, int nb, int parity) {
-  for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
+  // the item's keys only (the used list), not the whole table
+  const uint32_t n_used = sm.n_used;
+  for (uint32_t i = threadIdx.x; i < n_used; i += blockDim.x) {
+    const uint32_t s = sm.used[i];
     const uint32_t nn = sm.tn[s];
     if (!nn) continue;
     const uint32_t key = sm.tkey[s];
     const float A = sm.tA[s];
-    const uint32_t sb = sm.tsb[parity][s];
-    if (TSC == 4) {
+    const uint32_t sbits = sm.tsb[s];
+    if (!GR) {
       const int cn = S.tex[(key >> 28) - 1].c;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
-        if (c < cn) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
+        if (c < cn) sm.tS[c][s] += ((sbits >> c) & 1) ? -A : A;
     } else {
-      // group entry: channel c of read texture r at 4 r + c (unused channels stay 0)
+      // group entry: channel c of read texture r at 4 r + c
 #pragma unroll
-      for (int c = 0; c < TSC; ++c)
-        if (c % 4 < S.rtex[c / 4].c) sm.tS[c][s] += ((sb >> c) & 1) ? -A : A;
+      for (int r = 0; r < NREAD; ++r) {
+        const int cn = S.rtex[r].c;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c < cn) sm.tS[4 * r + c][s] += ((sbits >> (4 * r + c)) & 1) ? -A : A;
+      }
     }
     sm.tcnt[s] += nn;
     sm.tA[s] = 0.0f;
@@ -246,6 +305,24 @@ __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE, TSC>& sm
     sm.A_tri[j] = 0.0f;
     sm.n_tri[j] = 0u;
   }
+}
+
+// Sum of v over the run of consecutive lanes (in lane order) that share key k, for the run's
+// last lane; every lane of the warp calls it.  Returns whether the lane ends its run and sets n
+// to the run's length.
+__device__ __forceinline__ bool run_sum(int k, float& v, int& n) {
+  const int lane = threadIdx.x & 31;
+  const int kp = __shfl_up_sync(0xffffffffu, k, 1);
+  const int kn = __shfl_down_sync(0xffffffffu, k, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || kp != k);
+  const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float o = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane - d >= start) v += o;
+  }
+  n = lane - start + 1;
+  return lane == 31 || kn != k;
 }
 
 // ---------------------------------------------------------------- bin pruning
@@ -358,9 +435,12 @@ struct CandList {
   }
 };
 
-// Store a pixel's list: 8-bit indices (light tile, <= CMAX kept) or 16-bit ones.
+// Store a pixel's list: 8-bit indices (light tile, <= CMAX kept, in ascending order of the
+// triangles' smallest depth under any perturbation, zr(j) of live index j) or 16-bit ones.  The
+// count byte holds min(n, 127) and, in bit 7, whether some triangle surely covers the pixel.
+template <typename ZR>
 __device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_index, int tid, const CandList& c,
-                                            bool wide) {
+                                            bool wide, bool sure, ZR&& zr) {
   const long long ci = tile_index * kCandWords * TILE_PX + tid;
   if (wide) {
 #pragma unroll
@@ -368,12 +448,28 @@ __device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_
       ws.cand[ci + w * TILE_PX] =
           make_int4((int)c.w[4 * w], (int)c.w[4 * w + 1], (int)c.w[4 * w + 2], (int)c.w[4 * w + 3]);
   } else {
-    uint32_t b[CMAX / 4] = {};
+    // insertion sort by smallest depth: the estimator stops at the first candidate that lies
+    // wholly behind the nearest covering triangle found so far
+    uint32_t id[CMAX];
+    float z[CMAX];
     const int k = min(c.n, CMAX);
-    for (int q = 0; q < k; ++q) b[q >> 2] |= c.get(q) << (8 * (q & 3));
+    for (int q = 0; q < k; ++q) {
+      const uint32_t j = c.get(q);
+      const float zj = zr(j);
+      int at = q;
+      while (at > 0 && z[at - 1] > zj) {
+        z[at] = z[at - 1];
+        id[at] = id[at - 1];
+        --at;
+      }
+      z[at] = zj;
+      id[at] = j;
+    }
+    uint32_t b[CMAX / 4] = {};
+    for (int q = 0; q < k; ++q) b[q >> 2] |= id[q] << (8 * (q & 3));
     ws.cand[ci] = make_int4((int)b[0], (int)b[1], (int)b[2], (int)b[3]);
   }
-  ws.ncand[tile_index * TILE_PX + tid] = (uint8_t)min(c.n, 255);
+  ws.ncand[tile_index * TILE_PX + tid] = (uint8_t)(min(c.n, 127) | (sure ? 128 : 0));
 }
 
 // Per (view slot, tile): drop from the bin every triangle that no perturbation of the call can
@@ -467,7 +563,10 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     const int k = min(cl.n, kHeavyCand);
     for (int q = 0; q < k; ++q) out.push(sm.remap[cl.get(q)]);
     out.n = cl.n;
-    store_cands(ws, tix, tid, out, wide);
+    // live index -> bin position of the staged chunk, for the depth order
+    if (tid < nb && sm.live[tid]) sm.id[sm.remap[tid]] = (uint32_t)tid;
+    __syncthreads();
+    store_cands(ws, tix, tid, out, wide, zsure < 3.4e38f, [&](uint32_t j) { return sm.zr[sm.id[j]].x; });
     return;
   }
   // pass 3 (bins of more than one chunk): each pixel's candidates among the live triangles, in
@@ -484,7 +583,8 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
           else ++cl.n;
         }
   }
-  store_cands(ws, tix, tid, cl, wide);
+  // a light tile's live triangles are one staged chunk here, indexed by live position
+  store_cands(ws, tix, tid, cl, wide, zsure < 3.4e38f, [&](uint32_t j) { return sm.zr[j].x; });
 }
 
 __global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws, ViewList vl) {
@@ -519,6 +619,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
   const int ntl = n_tiles(S);
   const int n_chunks = (a.pair_count + a.pairs_per_item - 1) / a.pairs_per_item;
   const long long n_work = (long long)ws.counters[0] * n_chunks;
+  clear_table(sm);
 
   for (;;) {
     __syncthreads();
@@ -539,15 +640,13 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     const int p0 = a.pair_begin + chunk * a.pairs_per_item;
     const int p1 = min(a.pair_begin + a.pair_count, p0 + a.pairs_per_item);
     if (tid < 16) sm.m[tid] = S.mvp[16 * view + tid];
-    if (tid < p1 - p0) sm.pk[tid] = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)(p0 + tid));
-    clear_item_table(sm);
-    __syncthreads();
 
-    // ---- per item: the bin's live triangles (pruned and compacted by k_bin_prune) and this
-    //      pixel's candidates among them
+    // ---- per item: the bin's live triangles (pruned and compacted by k_bin_prune), their
+    //      smallest depths, and this pixel's candidates among them (in order of that depth)
     if (tid < nb) {
       const int tri = (int)ws.bins[bin_beg + tid];
       sm.btri[tid] = tri;
+      sm.zminb[tid] = ordered_bits(ws.tri_z[(long long)slot * S.nt + tri].x);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         sm.vid[tid][k] = __ldg(S.pidx + 3 * tri + k);
@@ -566,8 +665,12 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     const long long ci = ((long long)slot * ntl + tile) * TILE_PX + tid;
     const int4 cw = ws.cand[((long long)slot * ntl + tile) * kCandWords * TILE_PX + tid];
     const uint32_t cand[CMAX / 4] = {(uint32_t)cw.x, (uint32_t)cw.y, (uint32_t)cw.z, (uint32_t)cw.w};
-    const int ncand = ws.ncand[ci];
+    const int nc_byte = ws.ncand[ci];
+    const int ncand = nc_byte & 127;
     const bool all_bin = ncand > CMAX;
+    // the pixel's only candidate covers it under every perturbation of the call: it is the
+    // visible triangle on both sides, no test needed
+    const bool sure_one = (nc_byte & 128) && ncand == 1;
     float3 tgt = f3(0.f, 0.f, 0.f);
     if (valid) {
       const float* tp = S.targets + (((long long)view * S.H + py) * S.W + px) * 3;
@@ -576,15 +679,16 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     float loss_acc = 0.0f;
 
     for (int pair = p0; pair < p1; ++pair) {
-      const uint64_t pkey = sm.pk[pair - p0];
       const int par = pair & 1;
+      const long long pb = pair - a.pair_begin;
+      const uint32_t* planes = ws.tsign + ((long long)slot * ws.max_pairs + pb) * ws.sgn_words;
       // the previous pair is complete (and the item's set-up is done)
       __syncthreads();
       // ---- F: fold the previous pair's credits with its signs (other parity buffers)
-      if (pair > p0) fold(S, sm, nb, par ^ 1);
+      if (pair > p0) fold<TABLE, TSC, GR, NREAD>(S, sm, nb, par ^ 1);
       // ---- S: set up the bin's triangles on both sides from the projected perturbed vertices
       {
-        const long long vb = ((long long)slot * ws.max_pairs + (pair - a.pair_begin)) * S.nv;
+        const long long vb = ((long long)slot * ws.max_pairs + pb) * S.nv;
         for (int t2 = tid; t2 < 2 * nb; t2 += TILE_PX) {
           const int sd = t2 < nb ? 0 : 1, j = t2 - sd * nb;
           PVert v[3];
@@ -603,61 +707,70 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           if (sd == 0) sm.sgn9[par][j] = sg;
           Tri t;
           setup_tri(v[0], v[1], v[2], rx, ry, t);
-          store_side(sm.side[sd][j], t, sm.btri[j]);
+          store_side_tri(sm.side[sd][j], t);
         }
       }
       __syncthreads();
 
-      // ---- R: visible triangle on both sides among the candidates
-      unsigned long long best[2] = {~0ull, ~0ull};
+      // ---- R: visible triangle on both sides among the candidates (nearest-first order: a
+      //      candidate wholly behind both sides' best so far ends the search)
       int bj[2] = {-1, -1};
-      if (valid) {
-        auto test = [&](int j) {
+      if (valid && ncand > 0) {
+        if (sure_one) {
+          const int j = (int)(cand[0] & 0xFFu);
 #pragma unroll
-          for (int sd = 0; sd < 2; ++sd) {
-            const TriS& t = sm.side[sd][j];
-            if (t.tri < 0) continue;
-            long long e[3];
-            if (!cover_s(t, dx, dy, e)) continue;
-            const unsigned long long k = key_s(t, e);
-            if (k < best[sd]) {
-              best[sd] = k;
-              bj[sd] = j;
-            }
-          }
-        };
-        if (all_bin) {
-          for (int j = 0; j < nb; ++j) test(j);
+          for (int sd = 0; sd < 2; ++sd) bj[sd] = (sm.side[sd][j].flags & kDrawn) ? j : -1;
         } else {
+          unsigned long long best[2] = {~0ull, ~0ull};
+          auto test = [&](int j) {
 #pragma unroll
-          for (int wd = 0; wd < CMAX / 4; ++wd) {
-            uint32_t word = cand[wd];
-            const int left = ncand - 4 * wd;
-            if (left <= 0) break;
-            for (int q = 0; q < 4 && q < left; ++q, word >>= 8) test((int)(word & 0xFFu));
+            for (int sd = 0; sd < 2; ++sd) {
+              const SideTri& t = sm.side[sd][j];
+              if (!(t.flags & kDrawn)) continue;
+              float l[3];
+              if (!cover_lambdas(t, dx, dy, l)) continue;
+              const unsigned long long k =
+                  ((unsigned long long)ordered_bits(interp_depth(l, t.z)) << 32) | (uint32_t)sm.btri[j];
+              if (k < best[sd]) {
+                best[sd] = k;
+                bj[sd] = j;
+              }
+            }
+          };
+          if (all_bin) {
+            for (int j = 0; j < nb; ++j) test(j);
+          } else {
+            bool more = true;
+#pragma unroll
+            for (int wd = 0; wd < CMAX / 4; ++wd) {
+              uint32_t word = cand[wd];
+              const int left = ncand - 4 * wd;
+              for (int q = 0; more && q < 4 && q < left; ++q, word >>= 8) {
+                const int j = (int)(word & 0xFFu);
+                const uint32_t zb = sm.zminb[j];
+                more = zb <= (uint32_t)(best[0] >> 32) || zb <= (uint32_t)(best[1] >> 32);
+                if (more) test(j);
+              }
+            }
           }
         }
       }
 
       // ---- U: UV buffer values and texel keys of both sides (footprints computed once)
-      float2 uvs[2];
       float bary[2][3];
       float ffx[2][NFOOT], ffy[2][NFOOT];
       uint32_t tpk[2][NFOOT];       // texel (x0,y0) id | 1<<30 if x1 wrapped | 1<<31 if y1 == y0
       uint32_t tslot[2][NFOOT][2];  // four 16-bit table slots per side and footprint
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
-        uvs[sd] = make_float2(0.f, 0.f);
         if (bj[sd] < 0) continue;
-        const TriS& t = sm.side[sd][bj[sd]];
-        long long e[3];
-        cover_s(t, dx, dy, e);
+        const SideTri& t = sm.side[sd][bj[sd]];
         float l[3];
-        lambdas(e, t.inv_area, l);
+        cover_lambdas(t, dx, dy, l);
         const PerspW pw = persp(l, t.iw);
         const float* uvt = sm.uv[bj[sd]];
-        uvs[sd].x = persp_interp(pw, uvt[0], uvt[2], uvt[4]);
-        uvs[sd].y = persp_interp(pw, uvt[1], uvt[3], uvt[5]);
+        const float u = persp_interp(pw, uvt[0], uvt[2], uvt[4]);
+        const float v = persp_interp(pw, uvt[1], uvt[3], uvt[5]);
         if (SH == SHADE_GGX) {
 #pragma unroll
           for (int k = 0; k < 3; ++k) bary[sd][k] = pw.q[k] / pw.qs;
@@ -665,11 +778,19 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
         for (int r = 0; r < NFOOT; ++r) {
           const TexDev& T = S.rtex[r];
-          const Foot f = footprint(uvs[sd].x, uvs[sd].y, T.w, T.h);
+          const Foot f = footprint(u, v, T.w, T.h);
           ffx[sd][r] = f.fx;
           ffy[sd][r] = f.fy;
           tpk[sd][r] = (uint32_t)(f.y0 * T.w + f.x0) | (f.x1 != f.x0 + 1 ? 1u << 30 : 0u) |
                        (f.y1 == f.y0 ? 1u << 31 : 0u);
+          if (S.foot_nearest) {
+            // the one credited texel (Section 4.4): its slot, and its id in the second word
+            const uint32_t nt = (uint32_t)nearest_texel(u, v, T.w, T.h);
+            tslot[sd][r][1] = nt;
+            tslot[sd][r][0] = (sd == 1 && bj[0] >= 0 && tslot[0][r][1] == nt) ? tslot[0][r][0]
+                                                                                : table_insert(sm, tkey(T.index, (int)nt));
+            continue;
+          }
           if (sd == 1 && bj[0] >= 0 && tpk[1][r] == tpk[0][r]) {  // same footprint on both sides
             tslot[1][r][0] = tslot[0][r][0];
             tslot[1][r][1] = tslot[0][r][1];
@@ -677,125 +798,172 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           }
           uint32_t sl[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            sl[q] = table_insert<TABLE, TSC, GR ? NREAD : 0>(sm, tkey(T.index, foot_texel(f, q, T.w)),
-                                                             (uint32_t)pair + 1, S, T, pkey, par);
+          for (int q = 0; q < 4; ++q) sl[q] = table_insert(sm, tkey(T.index, foot_texel(f, q, T.w)));
           tslot[sd][r][0] = sl[0] | (sl[1] << 16);
           tslot[sd][r][1] = sl[2] | (sl[3] << 16);
         }
       }
-      __syncthreads();  // the pair's texel signs are drawn
 
-      // ---- G: shade both sides, f+ - f-, credits
+      // ---- G: sample the perturbed texels (signs from the pair's planes), shade both sides,
+      //      f+ - f-, credits
       float3 col[2];
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        col[sd] = f3(S.bg[0], S.bg[1], S.bg[2]);
-        if (bj[sd] < 0) continue;
-        float tex[NREAD][4];
-#pragma unroll
-        for (int r = 0; r < NREAD; ++r) {
-          const TexDev& T = S.rtex[r];
-          const int fi = GR ? 0 : r;  // the footprint (and table entries) this texture uses
-          const float fx = ffx[sd][fi], fy = ffy[sd][fi];
-          const float wq[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
-#pragma unroll
-          for (int c = 0; c < 4; ++c) tex[r][c] = 0.0f;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t sl = (tslot[sd][fi][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-            const long long texel = texel_of(tpk[sd][fi], q, T.w);
-            const float* src = T.ptr + texel * T.c;
-            uint32_t sb;
-            if (sl != NOSLOT) {
-              sb = sm.tsb[par][sl] >> (GR ? 4 * r : 0);
-            } else {
-              sb = 0;
-              for (int c = 0; c < T.c; ++c) sb |= (uint32_t)sign_neg(pkey, (uint64_t)(T.offset + texel * T.c + c)) << c;
-            }
-            if (sd == 1) sb = ~sb;  // side -: theta - s eps
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              if (c < T.c) tex[r][c] += wq[q] * __fadd_rn(__ldg(src + c), ((sb >> c) & 1) ? -T.eps : T.eps);
-          }
-          if (T.c == 1) tex[r][1] = tex[r][2] = tex[r][0];
+      col[0] = col[1] = f3(S.bg[0], S.bg[1], S.bg[2]);
+      if (SH == SHADE_UNLIT && bj[0] >= 0 && bj[1] >= 0 && tpk[0][0] == tpk[1][0]) {
+        // one footprint on both sides: each texel value and sign word is read once
+        const TexDev& T = S.rtex[0];
+        const uint32_t* plane = planes + ws.sgn_off[T.index];
+        float w0[4], w1[4];
+        {
+          const float fx = ffx[0][0], fy = ffy[0][0], gx = ffx[1][0], gy = ffy[1][0];
+          w0[0] = (1.0f - fx) * (1.0f - fy); w0[1] = fx * (1.0f - fy); w0[2] = (1.0f - fx) * fy; w0[3] = fx * fy;
+          w1[0] = (1.0f - gx) * (1.0f - gy); w1[1] = gx * (1.0f - gy); w1[2] = (1.0f - gx) * gy; w1[3] = gx * gy;
         }
-        if (SH == SHADE_UNLIT) {
-          col[sd] = f3(tex[0][0], tex[0][1], tex[0][2]);
-        } else {
-          const int j = bj[sd];
-          const uint32_t sg = sm.sgn9[par][j] ^ (sd == 1 ? 0x1FFu : 0u);
-          float3 p[3];
+        float t0[4] = {0.f, 0.f, 0.f, 0.f}, t1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const float* src = S.pos + 3ll * sm.vid[j][k];
-            float q[3];
+        for (int q = 0; q < 4; ++q) {
+          const int texel = texel_of(tpk[0][0], q, T.w);
+          const uint32_t sb = plane_nibble(plane, texel);
+          if (!S.foot_nearest) {
+            const uint32_t sl = (tslot[0][0][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+            if (sl != NOSLOT) sm.tsb[sl] = sb;
+          } else {
+            // either side's nearest texel (they may differ inside one bilinear footprint)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-              q[c] = __fadd_rn(__ldg(src + c), ((sg >> (3 * k + c)) & 1) ? -S.eps_pos : S.eps_pos);
-            p[k] = f3(q[0], q[1], q[2]);
+            for (int sd = 0; sd < 2; ++sd)
+              if (texel == (int)tslot[sd][0][1] && (tslot[sd][0][0] & 0xFFFFu) != NOSLOT)
+                sm.tsb[tslot[sd][0][0] & 0xFFFFu] = sb;
           }
-          const float2 uvv[3] = {make_float2(sm.uv[j][0], sm.uv[j][1]), make_float2(sm.uv[j][2], sm.uv[j][3]),
-                                 make_float2(sm.uv[j][4], sm.uv[j][5])};
-          float alb[4] = {1.f, 1.f, 1.f, 1.f}, nm[4] = {0.5f, 0.5f, 1.f, 0.f}, rough[4] = {0.5f, 0.f, 0.f, 0.f},
-                metal[4] = {0.f, 0.f, 0.f, 0.f};
+          const float* src = T.ptr + (long long)texel * T.c;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c < T.c) {
+              const float th = __ldg(src + c), d = ((sb >> c) & 1) ? -T.eps : T.eps;
+              t0[c] += w0[q] * __fadd_rn(th, d);
+              t1[c] += w1[q] * __fadd_rn(th, -d);
+            }
+        }
+        if (T.c == 1) t0[1] = t0[2] = t0[0], t1[1] = t1[2] = t1[0];
+        col[0] = f3(t0[0], t0[1], t0[2]);
+        col[1] = f3(t1[0], t1[1], t1[2]);
+      } else {
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+          if (bj[sd] < 0) continue;
+          float tex[NREAD][4];
+          uint32_t gsb[4] = {0u, 0u, 0u, 0u};  // a texel group's sign bits per corner (4 r + c)
 #pragma unroll
           for (int r = 0; r < NREAD; ++r) {
-            const int role = S.rtex[r].role;
-            float* dst = role == ROLE_ALBEDO ? alb : role == ROLE_NORMAL ? nm : role == ROLE_ROUGHNESS ? rough : metal;
+            const TexDev& T = S.rtex[r];
+            const uint32_t* plane = planes + ws.sgn_off[T.index];
+            const int fi = GR ? 0 : r;  // the footprint this texture uses
+            const float fx = ffx[sd][fi], fy = ffy[sd][fi];
+            const float wq[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
 #pragma unroll
-            for (int c = 0; c < 4; ++c) dst[c] = tex[r][c];
-          }
-          const float bz[3] = {SH == SHADE_GGX ? bary[sd][0] : 0.f, SH == SHADE_GGX ? bary[sd][1] : 0.f,
-                               SH == SHADE_GGX ? bary[sd][2] : 0.f};
-          col[sd] = shade(S, view, alb, nm, rough, metal, p, uvv, bz);
-        }
-      }
-      if (valid) {
-        float fp, fm;
-        const float df = loss_diff(col[0], col[1], tgt, fp, fm);
-        loss_acc += 0.5f * (fp + fm);
-        if (a.delta_f) a.delta_f[(((long long)slot * a.pairs + pair) * S.H + py) * S.W + px] = df;
-        // vertices: the visible triangle of each side (union of corners)
-        if (bj[0] >= 0) {
-          atomicAdd(&sm.A_tri[bj[0]], df);
-          atomicAdd(&sm.n_tri[bj[0]], 1u);
-          if (bj[1] >= 0 && bj[1] != bj[0]) {
+            for (int c = 0; c < 4; ++c) tex[r][c] = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              const int v = sm.vid[bj[1]][k];
-              if (v != sm.vid[bj[0]][0] && v != sm.vid[bj[0]][1] && v != sm.vid[bj[0]][2]) {
-                atomicAdd(&sm.A_cor[bj[1]][k], df);
-                atomicAdd(&sm.n_cor[bj[1]][k], 1u);
+            for (int q = 0; q < 4; ++q) {
+              const int texel = texel_of(tpk[sd][fi], q, T.w);
+              const uint32_t sb_s = plane_nibble(plane, texel);
+              if (GR) {
+                gsb[q] |= sb_s << (4 * r);
+              } else if (!S.foot_nearest) {
+                const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+                if (sl != NOSLOT) sm.tsb[sl] = sb_s;
+              } else if (texel == (int)tslot[sd][r][1] && (tslot[sd][r][0] & 0xFFFFu) != NOSLOT) {
+                sm.tsb[tslot[sd][r][0] & 0xFFFFu] = sb_s;
               }
+              const uint32_t sb = sd == 1 ? ~sb_s : sb_s;  // side -: theta - s eps
+              const float* src = T.ptr + (long long)texel * T.c;
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (c < T.c) tex[r][c] += wq[q] * __fadd_rn(__ldg(src + c), ((sb >> c) & 1) ? -T.eps : T.eps);
+            }
+            if (T.c == 1) tex[r][1] = tex[r][2] = tex[r][0];
+          }
+          if (GR) {
+            // the group entry of each corner carries every read texture's signs
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              uint32_t sl;
+              if (!S.foot_nearest) sl = (tslot[sd][0][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+              else sl = texel_of(tpk[sd][0], q, S.rtex[0].w) == (int)tslot[sd][0][1] ? (tslot[sd][0][0] & 0xFFFFu)
+                                                                                     : NOSLOT;
+              if (sl != NOSLOT) sm.tsb[sl] = gsb[q];
             }
           }
-        } else if (bj[1] >= 0) {
-          atomicAdd(&sm.A_tri[bj[1]], df);
-          atomicAdd(&sm.n_tri[bj[1]], 1u);
+          if (SH == SHADE_UNLIT) {
+            col[sd] = f3(tex[0][0], tex[0][1], tex[0][2]);
+          } else {
+            const int j = bj[sd];
+            const uint32_t sg = sm.sgn9[par][j] ^ (sd == 1 ? 0x1FFu : 0u);
+            float3 p[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              const float* src = S.pos + 3ll * sm.vid[j][k];
+              float q[3];
+#pragma unroll
+              for (int c = 0; c < 3; ++c)
+                q[c] = __fadd_rn(__ldg(src + c), ((sg >> (3 * k + c)) & 1) ? -S.eps_pos : S.eps_pos);
+              p[k] = f3(q[0], q[1], q[2]);
+            }
+            const float2 uvv[3] = {make_float2(sm.uv[j][0], sm.uv[j][1]), make_float2(sm.uv[j][2], sm.uv[j][3]),
+                                   make_float2(sm.uv[j][4], sm.uv[j][5])};
+            float alb[4] = {1.f, 1.f, 1.f, 1.f}, nm[4] = {0.5f, 0.5f, 1.f, 0.f}, rough[4] = {0.5f, 0.f, 0.f, 0.f},
+                  metal[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int r = 0; r < NREAD; ++r) {
+              const int role = S.rtex[r].role;
+              float* dst = role == ROLE_ALBEDO ? alb : role == ROLE_NORMAL ? nm : role == ROLE_ROUGHNESS ? rough : metal;
+#pragma unroll
+              for (int c = 0; c < 4; ++c) dst[c] = tex[r][c];
+            }
+            const float bz[3] = {SH == SHADE_GGX ? bary[sd][0] : 0.f, SH == SHADE_GGX ? bary[sd][1] : 0.f,
+                                 SH == SHADE_GGX ? bary[sd][2] : 0.f};
+            col[sd] = shade(S, view, alb, nm, rough, metal, p, uvv, bz);
+          }
         }
-        // texels: union of both sides' footprints of every read texture (of the group)
+      }
+      float df = 0.0f;
+      if (valid) {
+        float fp, fm;
+        df = loss_diff(col[0], col[1], tgt, fp, fm);  // 0 where both sides show the background
+        loss_acc += 0.5f * (fp + fm);
+      }
+      if (valid && a.delta_f) a.delta_f[(((long long)slot * a.pairs + pair) * S.H + py) * S.W + px] = df;
+      // vertices: the visible triangle of side + (else side -), summed over each run of lanes that
+      // share it, one shared atomic per run
+      {
+        const int kt = !valid ? -1 : (bj[0] >= 0 ? bj[0] : bj[1]);
+        float v = df;
+        int n;
+        if (run_sum(kt, v, n) && kt >= 0) {
+          atomicAdd(&sm.A_tri[kt], v);
+          atomicAdd(&sm.n_tri[kt], (uint32_t)n);
+        }
+      }
+      if (valid && bj[0] >= 0 && bj[1] >= 0 && bj[1] != bj[0]) {
+        // side -'s corners that side +'s triangle does not share
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int v = sm.vid[bj[1]][k];
+          if (v != sm.vid[bj[0]][0] && v != sm.vid[bj[0]][1] && v != sm.vid[bj[0]][2]) {
+            atomicAdd(&sm.A_cor[bj[1]][k], df);
+            atomicAdd(&sm.n_cor[bj[1]][k], 1u);
+          }
+        }
+      }
+      // texels: union of both sides' footprints of every read texture (of the group)
+      if (valid) {
 #pragma unroll
         for (int r = 0; r < NFOOT; ++r) {
           const TexDev& T = S.rtex[r];
-          const bool same = bj[0] >= 0 && bj[1] >= 0 && tpk[0][r] == tpk[1][r];
+          if (S.foot_nearest) {
 #pragma unroll
-          for (int sd = 0; sd < 2; ++sd) {
-            if (bj[sd] < 0 || (sd == 1 && same)) continue;
-            int ids[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) ids[q] = (int)texel_of(tpk[sd][r], q, T.w);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              bool dup = false;
-#pragma unroll
-              for (int o = 0; o < q; ++o) dup = dup || ids[o] == ids[q];
-              if (sd == 1 && bj[0] >= 0) {
-#pragma unroll
-                for (int o = 0; o < 4; ++o) dup = dup || (int)texel_of(tpk[0][r], o, T.w) == ids[q];
-              }
-              if (dup) continue;
-              const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+            for (int sd = 0; sd < 2; ++sd) {
+              if (bj[sd] < 0) continue;
+              const int id = (int)tslot[sd][r][1];
+              if (sd == 1 && bj[0] >= 0 && (int)tslot[0][r][1] == id) continue;
+              const uint32_t sl = tslot[sd][r][0] & 0xFFFFu;
               if (sl != NOSLOT) {
                 atomicAdd(&sm.tA[sl], df);
                 atomicAdd(&sm.tn[sl], 1u);
@@ -803,9 +971,51 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
                 for (int g = 0; g < (GR ? NREAD : 1); ++g) {
                   const TexDev& U = S.rtex[GR ? g : r];
-                  const long long base = U.offset + (long long)ids[q] * U.c;
+                  const uint32_t sb = plane_nibble(planes + ws.sgn_off[U.index], id);
+                  const long long base = U.offset + (long long)id * U.c;
                   for (int c = 0; c < U.c; ++c) {
-                    atomicAdd(a.grad + base + c, sign_neg(pkey, (uint64_t)(base + c)) ? -df : df);
+                    atomicAdd(a.grad + base + c, ((sb >> c) & 1) ? -df : df);
+                    atomicAdd(a.counts + base + c, 1u);
+                  }
+                }
+              }
+            }
+            continue;
+          }
+          int id0[4] = {-1, -1, -1, -1};
+          if (bj[0] >= 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) id0[q] = texel_of(tpk[0][r], q, T.w);
+          }
+          const bool same = bj[0] >= 0 && bj[1] >= 0 && tpk[0][r] == tpk[1][r];
+#pragma unroll
+          for (int sd = 0; sd < 2; ++sd) {
+            if (bj[sd] < 0 || (sd == 1 && same)) continue;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int id = sd == 0 ? id0[q] : texel_of(tpk[1][r], q, T.w);
+              bool dup = false;
+              // the footprint's own repeats (clamped rows, a one-texel-wide texture)
+#pragma unroll
+              for (int o = 0; o < q; ++o) dup = dup || (sd == 0 ? id0[o] : texel_of(tpk[1][r], o, T.w)) == id;
+              if (sd == 1) {
+#pragma unroll
+                for (int o = 0; o < 4; ++o) dup = dup || id0[o] == id;
+              }
+              if (dup) continue;
+              const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+              if (sl != NOSLOT) {
+                atomicAdd(&sm.tA[sl], df);
+                atomicAdd(&sm.tn[sl], 1u);
+              } else {
+                // table full: straight to the global sums with this pair's signs
+#pragma unroll
+                for (int g = 0; g < (GR ? NREAD : 1); ++g) {
+                  const TexDev& U = S.rtex[GR ? g : r];
+                  const uint32_t sb = plane_nibble(planes + ws.sgn_off[U.index], id);
+                  const long long base = U.offset + (long long)id * U.c;
+                  for (int c = 0; c < U.c; ++c) {
+                    atomicAdd(a.grad + base + c, ((sb >> c) & 1) ? -df : df);
                     atomicAdd(a.counts + base + c, 1u);
                   }
                 }
@@ -816,12 +1026,14 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       }
     }
     __syncthreads();
-    fold(S, sm, nb, (p1 - 1) & 1);
+    fold<TABLE, TSC, GR, NREAD>(S, sm, nb, (p1 - 1) & 1);
     __syncthreads();
     // ---- flush: one global atomic per credited vertex corner / texel and channel
-    for (int s = tid; s < TABLE; s += blockDim.x) {
+    const uint32_t n_used = sm.n_used;
+    for (uint32_t i = tid; i < n_used; i += blockDim.x) {
+      const uint32_t s = sm.used[i];
       const uint32_t key = sm.tkey[s];
-      if (key == EMPTY || sm.tcnt[s] == 0) continue;
+      if (sm.tcnt[s] == 0) continue;
       if (!GR) {
         const TexDev& T = S.tex[(key >> 28) - 1];
         const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
@@ -855,6 +1067,9 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
         }
       }
     }
+    __syncthreads();
+    clear_used(sm, n_used);  // n_used as read before the flush: thread 0 resets the shared count
+    if (tid == 0) sm.n_used = 0;
     if (a.loss) {
       float v = loss_acc;
 #pragma unroll

@@ -224,7 +224,11 @@ __global__ void k_scatter(SceneDev S, Workspace ws, uint64_t key, float* grad, u
     float2 uv = ws.uvbuf[s * npx + p];
 #pragma unroll
     for (int r = 0; r < MAX_READ; ++r)
-      if (r < S.nread) foot[s][r] = footprint(uv.x, uv.y, S.tex[S.read_k[r]].w, S.tex[S.read_k[r]].h);
+      if (r < S.nread) {
+        const TexDev& T = S.tex[S.read_k[r]];
+        foot[s][r] = footprint(uv.x, uv.y, T.w, T.h);
+        if (S.foot_nearest) foot[s][r].nearest = nearest_texel(uv.x, uv.y, T.w, T.h);
+      }
   }
   const float df = ws.dfbuf[p];
   for_each_contrib(S, tris, foot, [&](uint32_t ck) {

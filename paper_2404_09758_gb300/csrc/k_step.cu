@@ -18,8 +18,16 @@ struct StepGroups {
 };
 
 __global__ void k_step(StepGroups G, int kind, float* grad, uint32_t* counts, float inv_n, float b1, float b2,
-                       float c1, float c2, float aeps, float* m, float* v) {
+                       int t_host, float aeps, float* m, float* v, const int32_t* t_dev) {
   const long long d = G.begin[G.n];
+  // Adam's bias corrections 1 - beta^t for the step number t (from device memory in a replayed
+  // graph's step), formed as -expm1(t log beta): no cancellation when beta^t is close to 1
+  float c1 = 1.0f, c2 = 1.0f;
+  if (kind == SGE_STEP_ADAM) {
+    const float t = (float)(t_dev ? *t_dev : t_host);
+    c1 = -expm1f(t * logf(b1));
+    c2 = -expm1f(t * logf(b2));
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (long long)gridDim.x * blockDim.x) {
     int g = 0;
 #pragma unroll 1
@@ -43,6 +51,12 @@ __global__ void k_step(StepGroups G, int kind, float* grad, uint32_t* counts, fl
     grad[i] = 0.0f;
     counts[i] = 0u;
   }
+}
+
+// Moves a captured loop's iteration state on: the iteration index and Adam's step number.
+__global__ void k_iter_advance(uint32_t* state, int d_iter, int d_t) {
+  state[0] += (uint32_t)d_iter;
+  state[1] = (uint32_t)((int)state[1] + d_t);
 }
 
 // g_i = scale * grad_i / (2 eps_i n_total): the estimate of Eq. 9 (scale: device scalar or NULL).
@@ -140,7 +154,7 @@ cudaError_t launch_gradient(const SceneDev& S, const float* grad, long long n_to
 }
 
 cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32_t* counts, long long n_total,
-                        float* m, float* v, cudaStream_t st) {
+                        float* m, float* v, cudaStream_t st, const int32_t* t_dev) {
   StepGroups G;
   G.n = 1 + S.ntex;
   G.begin[0] = 0;
@@ -154,11 +168,6 @@ cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32
     G.lr[k + 1] = o.lr_tex[k];
   }
   G.begin[G.n] = S.n_params;
-  double c1 = 1.0, c2 = 1.0;
-  if (o.kind == SGE_STEP_ADAM) {
-    c1 = 1.0 - pow((double)o.beta1, (double)o.t);
-    c2 = 1.0 - pow((double)o.beta2, (double)o.t);
-  }
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -166,7 +175,12 @@ cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32
   if (blocks > 8ll * sms) blocks = 8ll * sms;
   if (blocks < 1) blocks = 1;
   k_step<<<(unsigned)blocks, 256, 0, st>>>(G, o.kind, grad, counts, (float)(1.0 / (double)n_total), o.beta1,
-                                           o.beta2, (float)c1, (float)c2, o.adam_eps, m, v);
+                                           o.beta2, o.t, o.adam_eps, m, v, t_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iter_advance(uint32_t* state, int d_iter, int d_t, cudaStream_t st) {
+  k_iter_advance<<<1, 1, 0, st>>>(state, d_iter, d_t);
   return cudaGetLastError();
 }
 

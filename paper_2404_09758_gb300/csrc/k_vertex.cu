@@ -20,7 +20,7 @@ __global__ void k_vertex_pass(SceneDev S, Workspace ws, ViewList vl, EstimateArg
   __syncthreads();
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= S.nv) return;
-  const uint64_t pkey = pair_key(a.seed, a.iter, (uint32_t)view, (uint32_t)(a.pair_begin + pb));
+  const uint64_t pkey = pair_key(a.seed, iter_of(a), (uint32_t)view, (uint32_t)(a.pair_begin + pb));
   const float* p = S.pos + 3ll * v;
   float qp[3], qm[3];
   uint32_t bits = 0;
@@ -41,12 +41,43 @@ __global__ void k_vertex_pass(SceneDev S, Workspace ws, ViewList vl, EstimateArg
   ws.vbits[o] = (uint8_t)bits;
 }
 
+// Texel sign planes of a block of estimates: word w of estimate (slot, pair) holds the signs of
+// eight consecutive texels of one read texture, four bits per texel (bit c: channel c has
+// s = -1), the same signs sign_neg draws for those parameters.  The fused estimators read them
+// when they sample and fold, instead of hashing per texel and pixel.
+__global__ void k_texel_signs(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
+  const int slot = blockIdx.z, pb = blockIdx.y;
+  const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= ws.sgn_words) return;
+  const uint64_t pkey = pair_key(a.seed, iter_of(a), (uint32_t)vl.id[slot], (uint32_t)(a.pair_begin + pb));
+  // the read texture whose plane holds word w (planes in read order, each starting on a word)
+  int r = 0;
+#pragma unroll
+  for (int q = 1; q < MAX_READ; ++q)
+    if (q < S.nread && w >= ws.sgn_off[S.read_k[q]]) r = q;
+  const TexDev& T = S.rtex[r];
+  const long long t0 = (w - ws.sgn_off[S.read_k[r]]) * 8;
+  const long long n_tex = (long long)T.w * T.h;
+  uint32_t bits = 0;
+  for (int j = 0; j < 8; ++j) {
+    const long long t = t0 + j;
+    if (t >= n_tex) break;
+    const uint64_t base = (uint64_t)(T.offset + t * T.c);
+    for (int c = 0; c < T.c; ++c) bits |= (uint32_t)sign_neg(pkey, base + c) << (4 * j + c);
+  }
+  ws.tsign[((long long)slot * ws.max_pairs + pb) * ws.sgn_words + w] = bits;
+}
+
 }  // namespace
 
 cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                                cudaStream_t st) {
   dim3 grid((S.nv + 255) / 256, a.pair_count, vl.n);
   k_vertex_pass<<<grid, 256, 0, st>>>(S, ws, vl, a);
+  if (ws.tsign && ws.sgn_words > 0) {
+    dim3 gs((unsigned)((ws.sgn_words + 255) / 256), a.pair_count, vl.n);
+    k_texel_signs<<<gs, 256, 0, st>>>(S, ws, vl, a);
+  }
   return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // The C ABI of include/sge.h: argument checks, workspace layout and launches.
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -54,17 +55,24 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t tri_rect, tri_margin, tri_z, pverts, vbits, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf,
-      desc, tile_live, cand, ncand, total;
+      desc, tile_live, cand, ncand, tsign, total;
   int max_views, max_pairs;
   long long bin_capacity;
+  long long sgn_words;
+  int sgn_off[SGE_MAX_TEXTURES];
 };
 
 int tiles_of(int n) { return (n + TILE - 1) / TILE; }
 
-int check_desc(const sge_scene_desc* d) {
+}  // namespace
+
+namespace sge {
+
+int check_desc(const sge_scene_desc* d, bool need_targets) {
   if (!d) return fail(SGE_ERR_INVALID_ARG, "desc is NULL");
-  if (!d->positions || !d->pos_idx || !d->uvs || !d->uv_idx || !d->mvp || !d->targets)
-    return fail(SGE_ERR_INVALID_ARG, "positions, pos_idx, uvs, uv_idx, mvp and targets must be non-NULL");
+  if (!d->positions || !d->pos_idx || !d->uvs || !d->uv_idx || !d->mvp)
+    return fail(SGE_ERR_INVALID_ARG, "positions, pos_idx, uvs, uv_idx and mvp must be non-NULL");
+  if (need_targets && !d->targets) return fail(SGE_ERR_INVALID_ARG, "targets must be non-NULL");
   if (d->n_vertices < 3 || d->n_vertices >= (1 << 28)) return fail(SGE_ERR_INVALID_ARG, "n_vertices %d out of [3, 2^28)", d->n_vertices);
   if (d->n_triangles < 1) return fail(SGE_ERR_INVALID_ARG, "n_triangles must be >= 1");
   if (d->n_uvs < 1) return fail(SGE_ERR_INVALID_ARG, "n_uvs must be >= 1");
@@ -109,12 +117,18 @@ int check_desc(const sge_scene_desc* d) {
   return SGE_OK;
 }
 
+}  // namespace sge
+
+namespace {
+
 int unsupported_transparent(const char* call) {
   return fail(SGE_ERR_UNSUPPORTED, "%s: transparent scenes run through sge_estimate_grad, sge_loss and "
               "sge_render_deep", call);
 }
 
 int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
+  if (c && c->footprint != SGE_FOOT_BILINEAR && c->footprint != SGE_FOOT_NEAREST)
+    return fail(SGE_ERR_INVALID_ARG, "footprint %d is neither SGE_FOOT_BILINEAR nor SGE_FOOT_NEAREST", c->footprint);
   L.max_views = (c && c->max_views_per_call > 0) ? c->max_views_per_call : d->n_views;
   if (L.max_views > SGE_MAX_VIEWS_PER_CALL) L.max_views = SGE_MAX_VIEWS_PER_CALL;
   const long long ntl = (long long)tiles_of(d->width) * tiles_of(d->height);
@@ -143,9 +157,25 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   L.tile_live = take(sizeof(uint32_t) * (size_t)(L.max_views * ntl));
   L.cand = take(sizeof(int4) * (size_t)(L.max_views * ntl) * kCandWords * TILE_PX);
   L.ncand = take((size_t)(L.max_views * ntl) * TILE_PX);
+  // texel sign planes of every estimate of a block of pairs: 4 bits per texel of each texture the
+  // shading model reads (transparent scenes do not use them)
+  SceneDev S;
+  make_dev(d, S);
+  L.sgn_words = 0;
+  for (int k = 0; k < SGE_MAX_TEXTURES; ++k) L.sgn_off[k] = -1;
+  if (d->shading != SGE_SHADE_TRANSPARENT)
+    for (int r = 0; r < S.nread; ++r) {
+      L.sgn_off[S.read_k[r]] = (int)L.sgn_words;
+      L.sgn_words += ((long long)S.rtex[r].w * S.rtex[r].h + 7) / 8;
+    }
+  L.tsign = take(sizeof(uint32_t) * (size_t)L.max_views * L.max_pairs * (size_t)L.sgn_words);
   L.total = o;
   return SGE_OK;
 }
+
+}  // namespace
+
+namespace sge {
 
 void make_dev(const sge_scene_desc* d, SceneDev& S) {
   memset(&S, 0, sizeof(S));
@@ -205,6 +235,10 @@ void make_dev(const sge_scene_desc* d, SceneDev& S) {
   S.tiles_y = tiles_of(d->height);
 }
 
+}  // namespace sge
+
+namespace {
+
 // The binning arms the estimator kernels' work counters; every further block of pairs of the
 // same call re-arms them.
 cudaError_t rearm_work(const Workspace& ws, cudaStream_t st) {
@@ -236,7 +270,7 @@ const char* sge_last_error(void) { return g_err; }
 
 int sge_workspace_size(const sge_scene_desc* desc, const sge_config* cfg, size_t* bytes) {
   if (!bytes) return fail(SGE_ERR_INVALID_ARG, "bytes is NULL");
-  int rc = check_desc(desc);
+  int rc = check_desc(desc, true);
   if (rc) return rc;
   Layout L;
   rc = make_layout(desc, cfg, L);
@@ -249,7 +283,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
                      sge_scene** out) {
   if (!out) return fail(SGE_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  int rc = check_desc(desc);
+  int rc = check_desc(desc, true);
   if (rc) return rc;
   Layout L;
   rc = make_layout(desc, cfg, L);
@@ -263,6 +297,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   s->desc = *desc;
   s->cfg = cfg ? *cfg : sge_config{};
   make_dev(desc, s->dev);
+  s->dev.foot_nearest = s->cfg.footprint == SGE_FOOT_NEAREST;
   char* base = static_cast<char*>(workspace);
   Workspace& w = s->ws;
   w.tri_rect = reinterpret_cast<int4*>(base + L.tri_rect);
@@ -283,6 +318,9 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   w.keys = reinterpret_cast<unsigned long long*>(base + L.keys);
   w.uvbuf = reinterpret_cast<float2*>(base + L.uvbuf);
   w.dfbuf = reinterpret_cast<float*>(base + L.dfbuf);
+  w.tsign = L.sgn_words > 0 ? reinterpret_cast<uint32_t*>(base + L.tsign) : nullptr;
+  w.sgn_words = L.sgn_words;
+  for (int k = 0; k < SGE_MAX_TEXTURES; ++k) w.sgn_off[k] = L.sgn_off[k];
   w.bin_capacity = L.bin_capacity;
   w.max_views = L.max_views;
   w.light_bin = kLightBin;
@@ -301,7 +339,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   int bps = (s->cfg.blocks_per_sm > 0) ? s->cfg.blocks_per_sm : fast_blocks_per_sm(desc->shading, s->dev.grouped);
   s->grid_fast = sms * bps;
   s->grid_heavy = sms * estimate_blocks_per_sm(desc->shading, s->dev.grouped);
-  if (s->cfg.pairs_per_item <= 0) s->cfg.pairs_per_item = 16;
+  if (s->cfg.pairs_per_item <= 0) s->cfg.pairs_per_item = 8;
   if (s->cfg.pairs_per_item > kMaxPairsPerItem) s->cfg.pairs_per_item = kMaxPairsPerItem;
   *out = s;
   return SGE_OK;
@@ -360,9 +398,15 @@ int sge_render_deep(sge_scene* s, int32_t view, uint64_t seed, uint32_t iter, ui
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_render_deep");
 }
 
-int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids, int32_t n_views,
-                      int32_t pairs_per_view, float* grad_sums, uint32_t* counts, float* loss_out, float* delta_f_out,
-                      sge_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// Every estimate of one call (sge_estimate_grad and its device-state form): iter_dev, when
+// non-NULL, is the device word the kernels read the iteration index from.
+int estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const uint32_t* iter_dev, const int32_t* view_ids,
+                  int32_t n_views, int32_t pairs_per_view, float* grad_sums, uint32_t* counts, float* loss_out,
+                  float* delta_f_out, sge_stream_t stream) {
   if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
   if (!grad_sums || !counts) return fail(SGE_ERR_INVALID_ARG, "grad_sums and counts must be non-NULL");
   if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
@@ -371,7 +415,7 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   EstimateArgs a{seed, iter, pairs_per_view, s->cfg.pairs_per_item, 0, pairs_per_view, grad_sums, counts, loss_out,
-                 delta_f_out};
+                 delta_f_out, iter_dev};
   cudaError_t e = cudaSuccess;
   if (delta_f_out)
     e = cudaMemsetAsync(delta_f_out, 0, sizeof(float) * (size_t)n_views * pairs_per_view * s->dev.W * s->dev.H, st);
@@ -394,6 +438,60 @@ int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t*
     if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, b, s->grid_fast, s->grid_heavy, st, ev);
   }
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
+}
+
+// Descent step (sge_step and its device-state form; t_dev: Adam's step number read at run time).
+int step(sge_scene* s, const sge_opt* o, const int32_t* t_dev, float* grad_sums, uint32_t* counts,
+         int64_t n_pairs_total, float* adam_m, float* adam_v, sge_stream_t stream) {
+  if (!s || !o) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  if (!grad_sums || !counts) return fail(SGE_ERR_INVALID_ARG, "grad_sums and counts must be non-NULL");
+  if (o->kind < SGE_STEP_SGD || o->kind > SGE_STEP_SGD_MEAN) return fail(SGE_ERR_INVALID_ARG, "bad step kind %d", o->kind);
+  if (o->kind != SGE_STEP_SGD_MEAN && n_pairs_total < 1) return fail(SGE_ERR_INVALID_ARG, "n_pairs_total must be >= 1");
+  if (o->kind == SGE_STEP_ADAM) {
+    if (!adam_m || !adam_v) return fail(SGE_ERR_INVALID_ARG, "Adam needs m and v");
+    if (!t_dev && o->t < 1) return fail(SGE_ERR_INVALID_ARG, "Adam step t must be >= 1");
+  }
+  if (s->desc.eps_pos <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "eps_pos must be > 0 to form Eq. 9's estimate");
+  for (int k = 0; k < s->dev.ntex; ++k)
+    if (s->dev.tex[k].eps <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be > 0 to step", k);
+  cudaError_t e = launch_step(s->dev, *o, grad_sums, counts, n_pairs_total > 0 ? n_pairs_total : 1, adam_m, adam_v,
+                              (cudaStream_t)stream, t_dev);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_step");
+}
+
+bool aligned4(const void* p) { return ((uintptr_t)p & 3) == 0; }
+static_assert(offsetof(sge_iter_state, iter) == 0 && offsetof(sge_iter_state, t) == 4,
+              "k_iter_advance reads the state as two 32-bit words");
+
+}  // namespace
+
+extern "C" {
+
+int sge_estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids, int32_t n_views,
+                      int32_t pairs_per_view, float* grad_sums, uint32_t* counts, float* loss_out, float* delta_f_out,
+                      sge_stream_t stream) {
+  return estimate_grad(s, seed, iter, nullptr, view_ids, n_views, pairs_per_view, grad_sums, counts, loss_out,
+                       delta_f_out, stream);
+}
+
+int sge_estimate_grad_state(sge_scene* s, uint64_t seed, const sge_iter_state* state, const int32_t* view_ids,
+                            int32_t n_views, int32_t pairs_per_view, float* grad_sums, uint32_t* counts,
+                            float* loss_out, float* delta_f_out, sge_stream_t stream) {
+  if (!state || !aligned4(state)) return fail(SGE_ERR_INVALID_ARG, "state must be a 4-byte aligned device pointer");
+  return estimate_grad(s, seed, 0, &state->iter, view_ids, n_views, pairs_per_view, grad_sums, counts, loss_out,
+                       delta_f_out, stream);
+}
+
+int sge_step_state(sge_scene* s, const sge_opt* o, const sge_iter_state* state, float* grad_sums, uint32_t* counts,
+                   int64_t n_pairs_total, float* adam_m, float* adam_v, sge_stream_t stream) {
+  if (!state || !aligned4(state)) return fail(SGE_ERR_INVALID_ARG, "state must be a 4-byte aligned device pointer");
+  return step(s, o, &state->t, grad_sums, counts, n_pairs_total, adam_m, adam_v, stream);
+}
+
+int sge_iter_advance(sge_iter_state* state, int32_t d_iter, int32_t d_t, sge_stream_t stream) {
+  if (!state || !aligned4(state)) return fail(SGE_ERR_INVALID_ARG, "state must be a 4-byte aligned device pointer");
+  cudaError_t e = launch_iter_advance(&state->iter, d_iter, d_t, (cudaStream_t)stream);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_iter_advance");
 }
 
 int sge_estimate_grad_plain(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids, int32_t n_views,
@@ -450,20 +548,7 @@ int sge_refine(const int32_t* row_ptr, const int32_t* col, const float* w, int32
 
 int sge_step(sge_scene* s, const sge_opt* o, float* grad_sums, uint32_t* counts, int64_t n_pairs_total, float* adam_m,
              float* adam_v, sge_stream_t stream) {
-  if (!s || !o) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
-  if (!grad_sums || !counts) return fail(SGE_ERR_INVALID_ARG, "grad_sums and counts must be non-NULL");
-  if (o->kind < SGE_STEP_SGD || o->kind > SGE_STEP_SGD_MEAN) return fail(SGE_ERR_INVALID_ARG, "bad step kind %d", o->kind);
-  if (o->kind != SGE_STEP_SGD_MEAN && n_pairs_total < 1) return fail(SGE_ERR_INVALID_ARG, "n_pairs_total must be >= 1");
-  if (o->kind == SGE_STEP_ADAM) {
-    if (!adam_m || !adam_v) return fail(SGE_ERR_INVALID_ARG, "Adam needs m and v");
-    if (o->t < 1) return fail(SGE_ERR_INVALID_ARG, "Adam step t must be >= 1");
-  }
-  if (s->desc.eps_pos <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "eps_pos must be > 0 to form Eq. 9's estimate");
-  for (int k = 0; k < s->dev.ntex; ++k)
-    if (s->dev.tex[k].eps <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be > 0 to step", k);
-  cudaError_t e = launch_step(s->dev, *o, grad_sums, counts, n_pairs_total > 0 ? n_pairs_total : 1, adam_m, adam_v,
-                              (cudaStream_t)stream);
-  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_step");
+  return step(s, o, nullptr, grad_sums, counts, n_pairs_total, adam_m, adam_v, stream);
 }
 
 int sge_loss(sge_scene* s, const int32_t* view_ids, int32_t n_views, float* loss_out, sge_stream_t stream) {
@@ -492,8 +577,15 @@ int sge_gradient(sge_scene* s, const float* grad_sums, int64_t n_pairs_total, co
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_gradient");
 }
 
-int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t seed, uint32_t iter,
-                            int32_t pairs_per_view, const sge_batch_tuning* tuning, sge_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// Every estimate of several scenes in one persistent launch per estimator kernel (the batched
+// call and its device-state form; iter_dev as in estimate_grad).
+int estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t seed, uint32_t iter,
+                        const uint32_t* iter_dev, int32_t pairs_per_view, const sge_batch_tuning* tuning,
+                        sge_stream_t stream) {
   if (!entries) return fail(SGE_ERR_INVALID_ARG, "entries is NULL");
   if (n < 1 || n > SGE_MAX_BATCH) return fail(SGE_ERR_INVALID_ARG, "n_entries %d out of [1, %d]", n, SGE_MAX_BATCH);
   if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
@@ -569,7 +661,7 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
       sge_scene* s = entries[i].scene;
       EstimateArgs b{seed, iter, pairs_per_view, tu.pairs_per_item, p0, pc, entries[i].grad_sums, entries[i].counts,
-                     entries[i].loss_out, nullptr};
+                     entries[i].loss_out, nullptr, iter_dev};
       if (p0 > 0) e = rearm_work(s->ws, st);
       if (e == cudaSuccess) e = launch_vertex_pass(s->dev, s->ws, vls[i], b, st);
     }
@@ -578,6 +670,7 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
       memset(&P, 0, sizeof(P));
       P.seed = seed;
       P.iter = iter;
+      P.iter_dev = iter_dev;
       P.pairs = pairs_per_view;
       P.pairs_per_item = tu.pairs_per_item;
       P.pair_begin = p0;
@@ -602,6 +695,22 @@ int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t 
     }
   }
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad_batch");
+}
+
+}  // namespace
+
+extern "C" {
+
+int sge_estimate_grad_batch(const sge_batch_entry* entries, int32_t n, uint64_t seed, uint32_t iter,
+                            int32_t pairs_per_view, const sge_batch_tuning* tuning, sge_stream_t stream) {
+  return estimate_grad_batch(entries, n, seed, iter, nullptr, pairs_per_view, tuning, stream);
+}
+
+int sge_estimate_grad_batch_state(const sge_batch_entry* entries, int32_t n, uint64_t seed,
+                                  const sge_iter_state* state, int32_t pairs_per_view,
+                                  const sge_batch_tuning* tuning, sge_stream_t stream) {
+  if (!state || !aligned4(state)) return fail(SGE_ERR_INVALID_ARG, "state must be a 4-byte aligned device pointer");
+  return estimate_grad_batch(entries, n, seed, 0, &state->iter, pairs_per_view, tuning, stream);
 }
 
 int sge_autotune_batch(const sge_batch_entry* entries, int32_t n, int32_t pairs_per_view, int32_t repeats,
@@ -780,6 +889,13 @@ int sge_draw_views(uint64_t seed, uint32_t iter, int32_t n_views, int32_t count,
   }
   for (int32_t i = 0; i < keep; ++i) out[i] = perm[i];
   return SGE_OK;
+}
+
+int sge_atomic_bench(float* buf, int64_t n_addr, int64_t n_threads, int32_t per_thread, sge_stream_t stream) {
+  if (!buf || n_addr < 1 || n_threads < 1 || per_thread < 1 || n_threads > 256ll * 0x7FFFFFFF)
+    return fail(SGE_ERR_INVALID_ARG, "sge_atomic_bench: need buf, n_addr >= 1, 1 <= n_threads, per_thread >= 1");
+  cudaError_t e = launch_red_bench(buf, n_addr, n_threads, per_thread, (cudaStream_t)stream);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_atomic_bench");
 }
 
 void sge_destroy_scene(sge_scene* s) {

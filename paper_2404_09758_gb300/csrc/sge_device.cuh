@@ -172,6 +172,7 @@ __device__ __forceinline__ float persp_interp(const PerspW& p, float a0, float a
 struct Foot {
   int x0, x1, y0, y1;  // wrapped / clamped texel coordinates
   float fx, fy;
+  int nearest;         // texel id of the nearest texel (set where SceneDev::foot_nearest asks for it)
 };
 
 // i mod n in [0, n); one add or subtract for the i in [-n, 2n) a texel lookup produces
@@ -198,6 +199,14 @@ __device__ __forceinline__ Foot footprint(float u, float v, int W, int H) {
   f.y0 = clamp_i(iy, H);
   f.y1 = clamp_i(iy + 1, H);
   return f;
+}
+
+// The texel whose square holds the sample point, (floor(u W) wrapped, floor(v H) clamped): the one
+// texel Section 4.4 credits ("nearest" footprint); its id y W + x.
+__device__ __forceinline__ int nearest_texel(float u, float v, int W, int H) {
+  const int x = wrap_i((int)floorf(__fmul_rn(u, (float)W)), W);
+  const int y = clamp_i((int)floorf(__fmul_rn(v, (float)H)), H);
+  return y * W + x;
 }
 
 // ---------------------------------------------------------------- device scene view
@@ -331,6 +340,7 @@ __device__ __forceinline__ void surface(const SceneDev& S, int view, int tri, co
     if (r >= S.nread) break;
     const TexDev& T = S.tex[S.read_k[r]];
     out.foot[r] = footprint(out.u, out.v, T.w, T.h);
+    if (S.foot_nearest) out.foot[r].nearest = nearest_texel(out.u, out.v, T.w, T.h);
     float* dst = T.role == ROLE_ALBEDO ? alb : T.role == ROLE_NORMAL ? nm : T.role == ROLE_ROUGHNESS ? rough : metal;
     sample_tex(T, out.foot[r], key, side, dst);
   }
@@ -438,6 +448,13 @@ __device__ __forceinline__ void for_each_contrib(const SceneDev& S, const int tr
     if (r >= S.nread) break;
     const int k = S.read_k[r];
     const int tw = S.tex[k].w;
+    if (S.foot_nearest) {
+      // one texel per side: the nearest one (Section 4.4), each once
+      const int n0 = tris[0] >= 0 ? foot[0][r].nearest : -1;
+      if (n0 >= 0) f(tkey(k, n0));
+      if (tris[1] >= 0 && foot[1][r].nearest != n0) f(tkey(k, foot[1][r].nearest));
+      continue;
+    }
     int ids[2][4];
 #pragma unroll
     for (int sd = 0; sd < 2; ++sd) {
@@ -494,7 +511,7 @@ __device__ __forceinline__ void load_asset(const BatchArgs& P, int ai, BatchSmem
   if (threadIdx.x == 0) {
     b.vl.n = A.n_views;
     b.a = EstimateArgs{P.seed, P.iter, P.pairs, P.pairs_per_item, P.pair_begin, P.pair_count,
-                       A.grad, A.counts, A.loss, nullptr};
+                       A.grad, A.counts, A.loss, nullptr, P.iter_dev};
   }
   if (threadIdx.x < SGE_MAX_BATCH_VIEWS) b.vl.id[threadIdx.x] = A.view[threadIdx.x];
 }

@@ -59,6 +59,7 @@ struct SceneDev {
   float light_dir[3], light_rgb[3], ambient;
   long long n_params;
   int tiles_x, tiles_y;
+  int foot_nearest;  // credit the nearest texel instead of the bilinear 2x2 footprint (SGE_FOOT_NEAREST)
 };
 
 // Views of one estimate call, by value (graph capture bakes them in).
@@ -88,6 +89,10 @@ struct Workspace {
   unsigned long long* keys;  // [2][H*W] staged depth|ID buffers (both sides)
   float2* uvbuf;             // [2][H*W] staged UV buffers
   float* dfbuf;              // [H*W] staged loss differences
+  uint32_t* tsign;       // [max_views][max_pairs][sgn_words] texel sign planes of each estimate: 4 bits
+                         // per texel (bit c: channel c has s = -1) of every texture the shading reads
+  long long sgn_words;   // 32-bit words of one estimate's planes
+  int sgn_off[SGE_MAX_TEXTURES];  // word offset of texture k's plane in them (-1: not read)
   long long bin_capacity;
   int max_views;
   int max_pairs;
@@ -117,6 +122,7 @@ struct BatchAsset {
 struct BatchArgs {
   uint64_t seed;
   uint32_t iter;
+  const uint32_t* iter_dev;  // device iteration index read at run time instead of iter (or NULL)
   int pairs;           // pairs per view of the whole call
   int pairs_per_item;
   int pair_begin;
@@ -150,7 +156,10 @@ struct EstimateArgs {
   uint32_t* counts;
   float* loss;
   float* delta_f;
+  const uint32_t* iter_dev;  // device iteration index read at run time instead of iter (or NULL)
 };
+// Iteration index of an estimate call: the device word when the call reads it at run time.
+__host__ __device__ inline uint32_t iter_of(const EstimateArgs& a) { return a.iter_dev ? *a.iter_dev : a.iter; }
 // Both estimator kernels: the fast path over light bins, the general one over heavy bins.
 // ev_fast (three events, or NULL) are recorded on st right before and after the fast kernel
 // and after the heavy one.
@@ -201,17 +210,31 @@ cudaError_t launch_deep_estimate(const SceneDev& S, const Workspace& ws, const V
 cudaError_t launch_render_deep(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key, int side,
                                unsigned long long* deep, float* rgb, float* loss, cudaStream_t st);
 
+// Throughput probe of global float reductions: n_threads threads, per_thread each, thread i on
+// buf[i mod n_addr].
+cudaError_t launch_red_bench(float* buf, long long n_addr, long long n_threads, int per_thread, cudaStream_t st);
+
 // Image error of unperturbed renders (forward of the autograd form), added to loss[slot].
 cudaError_t launch_render_loss(const SceneDev& S, const Workspace& ws, int slot, int view, float* loss,
                                cudaStream_t st);
 // out = scale * grad / (2 eps n_total) per parameter (Eq. 9).
 cudaError_t launch_gradient(const SceneDev& S, const float* grad, long long n_total, const float* scale, float* out,
                             cudaStream_t st);
+// t_dev (device, or NULL for o.t): Adam's step number read at run time.
 cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32_t* counts,
-                        long long n_total, float* m, float* v, cudaStream_t st);
+                        long long n_total, float* m, float* v, cudaStream_t st, const int32_t* t_dev = nullptr);
+// state[0] += d_iter, state[1] += d_t (one thread).
+cudaError_t launch_iter_advance(uint32_t* state, int d_iter, int d_t, cudaStream_t st);
 cudaError_t launch_validate(const SceneDev& S, uint32_t* status, cudaStream_t st);
 
 __host__ __device__ inline int n_tiles(const SceneDev& S) { return S.tiles_x * S.tiles_y; }
+
+// Host checks of a scene descriptor shared by every entry point that takes one (targets are
+// required unless need_targets is false); returns an SGE_ code and leaves the message for
+// sge_last_error.
+int check_desc(const sge_scene_desc* d, bool need_targets);
+// Device view of a checked descriptor (texture offsets, read textures, texel groups, tiles).
+void make_dev(const sge_scene_desc* d, SceneDev& S);
 
 // The calling thread's message for sge_last_error (host).
 void set_last_error(const char* msg);

@@ -11,6 +11,8 @@
 //
 // Set-up: the first call on a device (with that device current) looks up the
 // array's device address once; make that first call before any stream capture.
+// The address belongs to the device's context: after cudaDeviceReset the next call
+// looks it up again (in the new context), so that call too should precede a capture.
 // Every call shares the one array and leaves its contents behind; each call
 // clears what must start at zero.  Two calls whose work overlaps on the GPU (on
 // different streams, or from different host threads) race on the array: order
@@ -49,7 +51,14 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_lock;
-void* g_addr[kMaxDevices] = {};
+// Per device: the scratch address and the ID of the context it was looked up in.  A context
+// that goes away (cudaDeviceReset) takes the address with it, so a changed ID means a new lookup.
+struct Cached {
+  void* addr;
+  unsigned long long ctx_id;
+  bool keyed;  // ctx_id is known; without it the address is looked up on every call
+};
+Cached g_cache[kMaxDevices] = {};
 
 // Errors return their code and leave their message for sge_last_error.
 int fail(int code, const char* msg) {
@@ -57,19 +66,49 @@ int fail(int code, const char* msg) {
   return code;
 }
 
-// Device address of the scratch on the current device (looked up once per device).
+// ID of the calling thread's current CUDA context, through the driver's entry points that the
+// runtime hands out (the library does not link the driver library itself).  Called with g_lock held.
+bool current_context_id(unsigned long long* id) {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void**>(&get_current), 12000,
+                                         cudaEnableDefault, &q) != cudaSuccess || q != cudaDriverEntryPointSuccess)
+      get_current = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void**>(&get_id), 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess || q != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+  }
+  if (!get_current || !get_id) return false;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch on the current device: looked up once per device and context.
 int scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(SGE_ERR_CUDA, "sge_render_idb_static: no usable current device");
   std::lock_guard<std::mutex> g(g_lock);
-  if (!g_addr[dev]) {
+  unsigned long long id = 0;
+  bool keyed = current_context_id(&id);
+  Cached& c = g_cache[dev];
+  if (!c.addr || !c.keyed || !keyed || c.ctx_id != id) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || !p) return fail(SGE_ERR_CUDA, "sge_render_idb_static: cudaGetSymbolAddress failed");
-    g_addr[dev] = p;
+    if (!keyed) keyed = current_context_id(&id);  // the lookup made the device's context current
+    c.addr = p;
+    c.ctx_id = id;
+    c.keyed = keyed;
   }
-  *out = g_addr[dev];
+  *out = c.addr;
   return SGE_OK;
 }
 
@@ -80,79 +119,25 @@ __global__ void k_copy_status(const uint32_t* counters, int32_t* out) { *out = (
 extern "C" int sge_render_idb_static(const sge_scene_desc* d, int32_t view, uint64_t seed, uint32_t iter,
                                      uint32_t pair, int32_t side, uint64_t* depth_id, float* uv, float* rgb,
                                      int32_t* device_status, sge_stream_t stream) {
-  if (!d || !d->positions || !d->pos_idx || !d->uvs || !d->uv_idx || !d->mvp)
-    return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: NULL scene pointer");
-  if (d->n_vertices < 3 || d->n_vertices >= (1 << 28) || d->n_triangles < 1 || d->n_uvs < 1 || d->n_views < 1)
-    return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: bad scene counts");
+  // the same descriptor checks as every workspace-based entry point (targets are not read here)
+  int rc = check_desc(d, false);
+  if (rc) return rc;
   if (d->n_triangles > kMaxTriangles)
     return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: more triangles than SGE_STATIC_MAX_TRIANGLES");
-  if (d->width < 1 || d->height < 1 ||
-      (long long)((d->width + TILE - 1) / TILE) * ((d->height + TILE - 1) / TILE) > kMaxTiles)
+  if ((long long)((d->width + TILE - 1) / TILE) * ((d->height + TILE - 1) / TILE) > kMaxTiles)
     return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: render larger than SGE_STATIC_MAX_PIXELS");
   if (view < 0 || view >= d->n_views) return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: bad view");
   if (side < -1 || side > 1) return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: side not in {-1, 0, 1}");
   if (d->shading == SGE_SHADE_TRANSPARENT)
     return fail(SGE_ERR_UNSUPPORTED, "sge_render_idb_static: transparent scenes render through sge_render_deep");
-  if (d->shading < SGE_SHADE_UNLIT || d->shading > SGE_SHADE_GGX || (d->shading == SGE_SHADE_GGX && !d->cam_pos))
-    return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: bad shading");
-  if (d->n_textures < 0 || d->n_textures > SGE_MAX_TEXTURES)
-    return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: bad texture count");
-  for (int k = 0; k < d->n_textures; ++k) {
-    const sge_texture& t = d->textures[k];
-    if (!t.texels || t.width < 1 || t.height < 1 || (long long)t.width * t.height >= (1ll << 28) || t.channels < 1 ||
-        t.channels > 4 || t.role < SGE_ROLE_ALBEDO || t.role > SGE_ROLE_METALLIC)
-      return fail(SGE_ERR_INVALID_ARG, "sge_render_idb_static: bad texture");
-  }
 
   void* base = nullptr;
-  int rc = scratch_address(&base);
+  rc = scratch_address(&base);
   if (rc) return rc;
 
-  // device view of the scene (the same fields the workspace-based entry points use)
+  // device view of the scene, built as the workspace-based entry points build it
   SceneDev S;
-  memset(&S, 0, sizeof(S));
-  S.pos = d->positions;
-  S.nv = d->n_vertices;
-  S.eps_pos = d->eps_pos;
-  S.pidx = d->pos_idx;
-  S.nt = d->n_triangles;
-  S.uvs = d->uvs;
-  S.uvidx = d->uv_idx;
-  S.nuv = d->n_uvs;
-  S.ntex = d->n_textures;
-  long long off = 3ll * d->n_vertices;
-  int first_of_role[4] = {-1, -1, -1, -1};
-  for (int k = 0; k < d->n_textures; ++k) {
-    const sge_texture& t = d->textures[k];
-    S.tex[k] = TexDev{t.texels, t.width, t.height, t.channels, t.eps, t.role, 0, off, k};
-    off += (long long)t.width * t.height * t.channels;
-    if (first_of_role[t.role] < 0) first_of_role[t.role] = k;
-  }
-  S.n_params = off;
-  for (int k = 0; k < d->n_textures; ++k) {
-    const int role = d->textures[k].role;
-    const bool read = first_of_role[role] == k &&
-                      (d->shading == SGE_SHADE_GGX || role == SGE_ROLE_ALBEDO ||
-                       (d->shading == SGE_SHADE_LAMBERT && role == SGE_ROLE_NORMAL));
-    S.tex[k].read = read;
-    if (read) S.read_k[S.nread++] = k;
-  }
-  S.mvp = d->mvp;
-  S.cam_pos = d->cam_pos;
-  S.nviews = d->n_views;
-  S.W = d->width;
-  S.H = d->height;
-  S.near_w = d->near_w;
-  S.targets = d->targets;
-  for (int c = 0; c < 3; ++c) {
-    S.bg[c] = d->background[c];
-    S.light_dir[c] = d->light_dir[c];
-    S.light_rgb[c] = d->light_rgb[c];
-  }
-  S.shading = d->shading;
-  S.ambient = d->ambient;
-  S.tiles_x = (d->width + TILE - 1) / TILE;
-  S.tiles_y = (d->height + TILE - 1) / TILE;
+  make_dev(d, S);
 
   char* b = static_cast<char*>(base);
   // every field the binning and render kernels use points into the scratch; the

@@ -145,6 +145,36 @@ def test_invalid_descriptions_are_rejected_on_the_host(field, value):
         setattr(d, field, value)
     assert L.sge_workspace_size(C.byref(d), None, C.byref(n)) == _abi.ERR_INVALID_ARG
     assert L.sge_last_error()  # a message says which
+    # the allocation-free render checks the description with the same code (it reads no targets)
+    rc = L.sge_render_idb_static(C.byref(d), 0, 0, 0, 0, 0, None, None, None, None, None)
+    if field == "targets":
+        assert rc != _abi.ERR_INVALID_ARG or b"targets" not in L.sge_last_error()
+    else:
+        assert rc == _abi.ERR_INVALID_ARG, (field, value, L.sge_last_error())
+
+
+def test_static_render_checks_roles_and_its_own_limits_on_the_host():
+    """A lit description without the textures its model reads, and a request one triangle over
+    the fixed scratch's limit, are refused before any device call."""
+    import ctypes as C
+    from paper_2404_09758_gb300 import _abi
+    L = _abi.load(build_if_missing=True)
+    d = _valid_desc()
+    d.shading = 1  # Lambert without a normal map
+    rc = L.sge_render_idb_static(C.byref(d), 0, 0, 0, 0, 0, None, None, None, None, None)
+    assert rc == _abi.ERR_INVALID_ARG and b"role" in L.sge_last_error()
+    d = _valid_desc()
+    header = open(os.path.join(ROOT, "include", "sge.h")).read()
+    limit = int(re.search(r"#define SGE_STATIC_MAX_TRIANGLES (\d+)", header).group(1))
+    d.n_triangles = limit + 1
+    n = C.c_size_t()
+    assert L.sge_workspace_size(C.byref(d), None, C.byref(n)) == _abi.OK  # fine for a workspace
+    rc = L.sge_render_idb_static(C.byref(d), 0, 0, 0, 0, 0, None, None, None, None, None)
+    assert rc == _abi.ERR_INVALID_ARG and b"SGE_STATIC_MAX_TRIANGLES" in L.sge_last_error()
+    d = _valid_desc()
+    for view, side in ((2, 0), (-1, 0), (0, 2)):
+        rc = L.sge_render_idb_static(C.byref(d), view, 0, 0, 0, side, None, None, None, None, None)
+        assert rc == _abi.ERR_INVALID_ARG
 
 
 def test_workspace_grows_with_views_and_pairs():
@@ -161,6 +191,10 @@ def test_workspace_grows_with_views_and_pairs():
     assert sizes[0] < sizes[1] < sizes[2]
     cfg = _abi.Config(0, 1 << 33, 0, 0, 0)  # bin capacity must stay below 2^32 entries
     assert L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(C.c_size_t())) == _abi.ERR_INVALID_ARG
+    # the texel footprint is bilinear or nearest
+    for foot, rc in ((_abi.FOOT_BILINEAR, _abi.OK), (_abi.FOOT_NEAREST, _abi.OK), (2, _abi.ERR_INVALID_ARG)):
+        cfg = _abi.Config(0, 0, 0, 0, 0, foot)
+        assert L.sge_workspace_size(C.byref(d), C.byref(cfg), C.byref(C.c_size_t())) == rc
 
 
 def test_static_render_refuses_transparent_scenes_on_the_host():

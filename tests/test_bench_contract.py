@@ -27,5 +27,6 @@ def test_every_workload_is_offered():
     out = subprocess.run([sys.executable, "bench.py", "--help"], cwd=ROOT, capture_output=True, text=True,
                          timeout=120)
     assert out.returncode == 0
-    for w in ("batched", "uneven", "scale", "full_image", "converge", "transparent", "soup", "catmull_clark"):
+    for w in ("batched", "uneven", "scale", "full_image", "converge", "transparent", "soup", "atomics",
+              "catmull_clark"):
         assert w in out.stdout, w

@@ -145,6 +145,37 @@ def test_estimate_grad_plain_matches_oracle(case):
     assert_parity(sc, r)
 
 
+NEAREST_CASES = {
+    # fast kernel (light bins), several pairs per item, a ragged image
+    "fast_ragged": ("sphere8k_3views_ragged", False),
+    # the general kernel's bins and the fast one's mixed
+    "mixed_bins": ("dense_mixed_bins", False),
+    # texel groups (Lambert: albedo and normal map of one size) in both kernels
+    "lambert_groups": ("dense_lambert", False),
+    # the plain path (staged renders, global scatter)
+    "plain_path": ("plain_256_1view", True),
+}
+
+
+@pytest.mark.parametrize("case", list(NEAREST_CASES))
+def test_nearest_texel_footprint_matches_oracle(case):
+    """Section 4.4's contributor set (the nearest texel, not the bilinear 2x2) on the GPU against
+    the oracle's nearest-footprint estimate: counts bit-exact, sums within the tolerance."""
+    from paper_2404_09758_gb300 import FOOT_NEAREST
+    name, plain = NEAREST_CASES[case]
+    make, views, pairs, kw = ESTIMATE_CASES[name]
+    sc = make()
+    tg = _with_targets(sc)
+    r = run_both(sc, tg, seed=13, it=1, views=views, pairs=pairs, plain=plain, footprint=oracle.FOOT_NEAREST,
+                 gpu_kwargs=dict(kw, footprint=FOOT_NEAREST))
+    assert_parity(sc, r)
+    # fewer texel credits than the bilinear footprint would give, and some
+    tex = slice(sc.n_pos_params, None)
+    assert 0 < r["C"][tex].sum()
+    rb = run_both(sc, tg, seed=13, it=1, views=views, pairs=pairs, plain=plain, gpu_kwargs=kw, want_df=False)
+    assert r["C"][tex].sum() < rb["C"][tex].sum()
+
+
 def test_small_table_and_many_chunks_still_match():
     """One pair per work item and a scene whose tiles touch many texels (texture 4x the render)."""
     sc = _sphere(32, 32, 1024, 64, 64, np.array([[0.0, 0.0, 3.0]], np.float32), True)

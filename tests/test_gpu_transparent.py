@@ -67,6 +67,24 @@ def test_estimate_matches_oracle(render, views, pairs):
     assert (odf != 0).sum() > 100
 
 
+def test_estimate_with_nearest_texel_footprint_matches_oracle():
+    """Every listed fragment credits only its nearest texel (Section 4.4's footprint)."""
+    import torch
+    from paper_2404_09758_gb300 import FOOT_NEAREST
+    sc, tg = _scene(64, 2, 3)
+    g = gpu_scene(sc, tg, footprint=FOOT_NEAREST)
+    grad, counts = g.new_grad_buffers()
+    loss = torch.zeros(2, device=g.device)
+    g.estimate_grad(SEED, ITER, [0, 1], 3, grad, counts, loss=loss)
+    st = g.status()
+    torch.cuda.synchronize()
+    S, Cn, oloss = oracle.estimate(oracle.OracleScene(sc, tg, footprint=oracle.FOOT_NEAREST), SEED, ITER, [0, 1], 3)
+    assert_parity(sc, dict(status=st, grad=grad.cpu().numpy().astype(np.float64),
+                           counts=counts.cpu().numpy().astype(np.int64).astype(np.uint64),
+                           loss=loss.cpu().numpy().astype(np.float64), S=S, C=Cn, oloss=oloss))
+    assert Cn[sc.n_pos_params:].sum() > 0
+
+
 def test_loss_and_targets_match_oracle():
     import torch
     sc, tg = _scene()

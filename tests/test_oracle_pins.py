@@ -400,6 +400,61 @@ def test_sgd_step_is_scaled_estimate():
     assert np.allclose(out2, want, rtol=0, atol=1e-12)
 
 
+def test_sgd_step_normalisation_gives_the_exact_gradient_step():
+    """Eq. 9's normalisation inside the SGD step, pinned by mathematics: feeding the step the
+    sums of Eq. 8 over all 2^d sign vectors of a 2x2 RGB texture (N = 2^d estimates) must move
+    theta by exactly lr times the true gradient (f is quadratic in the texels).  A wrong 2,
+    eps or N in the step's scale fails this; Adam's scale invariance would hide it."""
+    sc, tgt = _quad_texture_scene(n=2, W=8)
+    d_pos, d = sc.n_pos_params, sc.n_params
+    eps = sc.textures[0].eps
+    key = oracle.pair_key(5, 0, 0, 0)
+    s_hash = np.array([oracle.sign(key, i) for i in range(d)], np.float64)
+    n_tex = d - d_pos
+    S_all = np.zeros(d)
+    C_all = np.zeros(d, np.uint64)
+    for mask in range(1 << n_tex):
+        sigma = np.array([1.0 if (mask >> j) & 1 else -1.0 for j in range(n_tex)])
+        eps_vec = np.zeros(d, np.float32)
+        eps_vec[d_pos:] = (sigma * s_hash[d_pos:] * eps).astype(np.float32)
+        S, Cn, _ = oracle.estimate(oracle.OracleScene(sc, tgt, eps_vec=eps_vec), 5, 0, [0], 1)
+        # the sums a step sees when the perturbation of parameter i is sigma_i eps (not s_i eps)
+        S_all[d_pos:] += S[d_pos:] * sigma * s_hash[d_pos:]
+        C_all += Cn
+    theta = sc.textures[0].data.ravel().astype(np.float32)
+    lr = 0.125
+    out, _, _ = oracle.step(0, theta, S_all[d_pos:], C_all[d_pos:], eps, lr, 1 << n_tex)
+    g = _exact_texel_gradient(sc, tgt)
+    assert np.allclose(out, theta.astype(np.float64) - lr * g, rtol=0, atol=1e-9)
+    # the same sums counted as twice as many estimates halve the step
+    out2, _, _ = oracle.step(0, theta, S_all[d_pos:], C_all[d_pos:], eps, lr, 2 << n_tex)
+    assert np.allclose(theta - out2, 0.5 * lr * g, rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("kind", [0, 2])
+def test_sgd_steps_match_torch_sgd(kind):
+    """The SGD step (kind 0, Eq. 9's 1 / (2 eps N)) and the per-pixel-mean step (kind 2,
+    1 / (2 eps max(C, 1)), zero counts included) against torch.optim.SGD fed those gradients."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    d, N = 64, 12
+    th = rng.normal(size=d).astype(np.float32)
+    eps = rng.choice([1e-3, 1.0 / 255.0], size=d).astype(np.float32)
+    lr = rng.uniform(0.05, 0.5, size=d).astype(np.float32)
+    S = rng.normal(size=d) * 0.01
+    Cn = rng.integers(0, 20, size=d).astype(np.uint64)
+    Cn[:5] = 0
+    out, _, _ = oracle.step(kind, th, S, Cn, eps, lr, N)
+    scale = N if kind == 0 else np.maximum(Cn, 1).astype(np.float64)
+    grad = S / (2.0 * eps.astype(np.float64) * scale)
+    for i in range(d):
+        p = torch.tensor([float(th[i])], dtype=torch.float64, requires_grad=True)
+        opt = torch.optim.SGD([p], lr=float(lr[i]))
+        p.grad = torch.tensor([grad[i]], dtype=torch.float64)
+        opt.step()
+        assert abs(out[i] - float(p.detach()[0])) <= 1e-12 * max(1.0, abs(out[i])), (kind, i)
+
+
 def test_adam_step_matches_torch_adam():
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(1)
