@@ -271,7 +271,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
       cand[4 * w + 2] = (uint32_t)cw.z;
       cand[4 * w + 3] = (uint32_t)cw.w;
     }
-    const int ncand = ws.ncand[ti * TILE_PX + tid] & 127;  // bit 7: surely covered (the fast kernel's)
+    const int ncand = ws.ncand[ti * TILE_PX + tid];
     const bool all_live = ncand > kHeavyCand;
 
     for (int pair = p0; pair < p1; ++pair) {

@@ -53,6 +53,15 @@ struct Model {
   // texel per pixel, more where the surface is seen at a grazing angle
   static constexpr int TABLE = (SH == SHADE_UNLIT || GR) ? 1024 : 2048;
   static constexpr int TSC = GR ? 4 * NREAD : 4;  // channel sums per table entry
+  // one footprint per side (unlit, texel groups): the table's first WCAP slots can hold an item's
+  // texel window, indexed directly; the rest stay hashed for footprints outside it
+  static constexpr bool DIRECT = NFOOT == 1;
+  // one read texture: a footprint outside the window credits the global sums directly (its
+  // texels are rarely shared with other pixels there, and hashing costs more than it saves), so
+  // the window may take the whole table; texel groups keep a hashed quarter (a global credit
+  // would cost one atomic per channel of every grouped texture)
+  static constexpr bool HASH_OUTSIDE = NREAD > 1;
+  static constexpr int WCAP = HASH_OUTSIDE ? TABLE * 3 / 4 : TABLE;
 };
 
 // One side of a staged triangle (unperturbed set-up for the pruning pass, with its margin).
@@ -103,6 +112,9 @@ struct FastSmem {
                          // every pixel that samples the texel (all store the same value)
   uint16_t used[TABLE];  // slots holding a key in this item, in insertion order
   uint32_t n_used;
+  int win[4];            // the item's texel window: x (before wrapping) from win[0] to win[1], rows
+                         // win[2] to win[3]; slot (y - win[2]) * width + x - win[0]
+  uint32_t n_win;        // its slots (the first entries of used[]), 0 without a window
   float m[16];
   float red[TILE_PX / 32];
   uint32_t item;
@@ -186,12 +198,15 @@ __device__ __forceinline__ uint32_t hslot(uint32_t k, int table) {
   return k & (uint32_t)(table - 1);
 }
 
-// Find or insert a texel key (keys stay for the whole item; a new one is listed in used[]).
+// Find or insert a texel key in the hashed slots [hbase, hbase + hsize) (hsize a power of two;
+// keys stay for the whole item; a new one is listed in used[]).
 template <int TABLE, int TSC>
-__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE, TSC>& sm, uint32_t key) {
-  uint32_t slot = hslot(key, TABLE);
+__device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE, TSC>& sm, uint32_t key, uint32_t hbase,
+                                                 uint32_t hsize) {
+  uint32_t h = hslot(key, hsize);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
+    const uint32_t slot = hbase + h;
     uint32_t k = *(volatile uint32_t*)&sm.tkey[slot];
     if (k == EMPTY) {
       k = atomicCAS(&sm.tkey[slot], EMPTY, key);
@@ -201,14 +216,9 @@ __device__ __forceinline__ uint32_t table_insert(FastSmem<TABLE, TSC>& sm, uint3
       }
     }
     if (k == key) return slot;
-    slot = (slot + 1) & (TABLE - 1);
+    h = (h + 1) & (hsize - 1);
   }
   return NOSLOT;
-}
-
-// Texel id (y * W + x) of footprint corner q (0: x0y0, 1: x1y0, 2: x0y1, 3: x1y1).
-__device__ __forceinline__ int foot_texel(const Foot& f, int q, int w) {
-  return ((q & 2) ? f.y1 : f.y0) * w + ((q & 1) ? f.x1 : f.x0);
 }
 
 // Texel id of footprint corner q from the packed (x0,y0) id and its edge flags.
@@ -257,17 +267,17 @@ __device__ __forceinline__ void clear_used(FastSmem<TABLE, TSC>& sm, uint32_t n_
 // that pair's signs: texel signs in tsb (stored while sampling), vertex signs in sgn9[parity].
 template <int TABLE, int TSC, bool GR, int NREAD>
 __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE, TSC>& sm, int nb, int parity) {
-  // the item's keys only (the used list), not the whole table
-  const uint32_t n_used = sm.n_used;
+  // the item's keys only (the used list, whose first n_win entries are the window's slots 0, 1, ...
+  // in order: those are swept directly, lane i on slot i)
+  const uint32_t n_used = sm.n_used, n_win = sm.n_win;
   for (uint32_t i = threadIdx.x; i < n_used; i += blockDim.x) {
-    const uint32_t s = sm.used[i];
+    const uint32_t s = i < n_win ? i : sm.used[i];
     const uint32_t nn = sm.tn[s];
     if (!nn) continue;
-    const uint32_t key = sm.tkey[s];
     const float A = sm.tA[s];
     const uint32_t sbits = sm.tsb[s];
     if (!GR) {
-      const int cn = S.tex[(key >> 28) - 1].c;
+      const int cn = NREAD == 1 ? S.rtex[0].c : S.tex[(sm.tkey[s] >> 28) - 1].c;
 #pragma unroll
       for (int c = 0; c < 4; ++c)
         if (c < cn) sm.tS[c][s] += ((sbits >> c) & 1) ? -A : A;
@@ -436,11 +446,11 @@ struct CandList {
 };
 
 // Store a pixel's list: 8-bit indices (light tile, <= CMAX kept, in ascending order of the
-// triangles' smallest depth under any perturbation, zr(j) of live index j) or 16-bit ones.  The
-// count byte holds min(n, 127) and, in bit 7, whether some triangle surely covers the pixel.
+// triangles' smallest depth under any perturbation, zr(j) of live index j) or 16-bit ones, and
+// its length min(n, 255).
 template <typename ZR>
 __device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_index, int tid, const CandList& c,
-                                            bool wide, bool sure, ZR&& zr) {
+                                            bool wide, ZR&& zr) {
   const long long ci = tile_index * kCandWords * TILE_PX + tid;
   if (wide) {
 #pragma unroll
@@ -469,7 +479,7 @@ __device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_
     for (int q = 0; q < k; ++q) b[q >> 2] |= id[q] << (8 * (q & 3));
     ws.cand[ci] = make_int4((int)b[0], (int)b[1], (int)b[2], (int)b[3]);
   }
-  ws.ncand[tile_index * TILE_PX + tid] = (uint8_t)(min(c.n, 127) | (sure ? 128 : 0));
+  ws.ncand[tile_index * TILE_PX + tid] = (uint8_t)min(c.n, 255);
 }
 
 // Per (view slot, tile): drop from the bin every triangle that no perturbation of the call can
@@ -566,7 +576,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     // live index -> bin position of the staged chunk, for the depth order
     if (tid < nb && sm.live[tid]) sm.id[sm.remap[tid]] = (uint32_t)tid;
     __syncthreads();
-    store_cands(ws, tix, tid, out, wide, zsure < 3.4e38f, [&](uint32_t j) { return sm.zr[sm.id[j]].x; });
+    store_cands(ws, tix, tid, out, wide, [&](uint32_t j) { return sm.zr[sm.id[j]].x; });
     return;
   }
   // pass 3 (bins of more than one chunk): each pixel's candidates among the live triangles, in
@@ -584,7 +594,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
         }
   }
   // a light tile's live triangles are one staged chunk here, indexed by live position
-  store_cands(ws, tix, tid, cl, wide, zsure < 3.4e38f, [&](uint32_t j) { return sm.zr[j].x; });
+  store_cands(ws, tix, tid, cl, wide, [&](uint32_t j) { return sm.zr[j].x; });
 }
 
 __global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws, ViewList vl) {
@@ -665,12 +675,13 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     const long long ci = ((long long)slot * ntl + tile) * TILE_PX + tid;
     const int4 cw = ws.cand[((long long)slot * ntl + tile) * kCandWords * TILE_PX + tid];
     const uint32_t cand[CMAX / 4] = {(uint32_t)cw.x, (uint32_t)cw.y, (uint32_t)cw.z, (uint32_t)cw.w};
-    const int nc_byte = ws.ncand[ci];
-    const int ncand = nc_byte & 127;
+    const int ncand = ws.ncand[ci];
     const bool all_bin = ncand > CMAX;
-    // the pixel's only candidate covers it under every perturbation of the call: it is the
-    // visible triangle on both sides, no test needed
-    const bool sure_one = (nc_byte & 128) && ncand == 1;
+    if (tid == 0) {
+      sm.win[0] = sm.win[2] = 0x7FFFFFFF;
+      sm.win[1] = sm.win[3] = -0x7FFFFFFF;
+      sm.n_win = 0;
+    }
     float3 tgt = f3(0.f, 0.f, 0.f);
     if (valid) {
       const float* tp = S.targets + (((long long)view * S.H + py) * S.W + px) * 3;
@@ -716,11 +727,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       //      candidate wholly behind both sides' best so far ends the search)
       int bj[2] = {-1, -1};
       if (valid && ncand > 0) {
-        if (sure_one) {
-          const int j = (int)(cand[0] & 0xFFu);
-#pragma unroll
-          for (int sd = 0; sd < 2; ++sd) bj[sd] = (sm.side[sd][j].flags & kDrawn) ? j : -1;
-        } else {
+        {
           unsigned long long best[2] = {~0ull, ~0ull};
           auto test = [&](int j) {
 #pragma unroll
@@ -740,27 +747,24 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           if (all_bin) {
             for (int j = 0; j < nb; ++j) test(j);
           } else {
-            bool more = true;
-#pragma unroll
-            for (int wd = 0; wd < CMAX / 4; ++wd) {
-              uint32_t word = cand[wd];
-              const int left = ncand - 4 * wd;
-              for (int q = 0; more && q < 4 && q < left; ++q, word >>= 8) {
-                const int j = (int)(word & 0xFFu);
-                const uint32_t zb = sm.zminb[j];
-                more = zb <= (uint32_t)(best[0] >> 32) || zb <= (uint32_t)(best[1] >> 32);
-                if (more) test(j);
-              }
+            for (int q = 0; q < ncand; ++q) {
+              const uint32_t word = q < 4 ? cand[0] : (q < 8 ? cand[1] : (q < 12 ? cand[2] : cand[3]));
+              const int j = (int)((word >> (8 * (q & 3))) & 0xFFu);
+              const uint32_t zb = sm.zminb[j];
+              if (zb > (uint32_t)(best[0] >> 32) && zb > (uint32_t)(best[1] >> 32)) break;
+              test(j);
             }
           }
         }
       }
 
-      // ---- U: UV buffer values and texel keys of both sides (footprints computed once)
+      // ---- U: UV buffer values and footprints of both sides
       float bary[2][3];
       float ffx[2][NFOOT], ffy[2][NFOOT];
       uint32_t tpk[2][NFOOT];       // texel (x0,y0) id | 1<<30 if x1 wrapped | 1<<31 if y1 == y0
       uint32_t tslot[2][NFOOT][2];  // four 16-bit table slots per side and footprint
+      int fix[2][NFOOT];            // footprint column before wrapping (nearest mode: the texel id)
+      int fy0[2][NFOOT];            // footprint row y0
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
         if (bj[sd] < 0) continue;
@@ -783,24 +787,78 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           ffy[sd][r] = f.fy;
           tpk[sd][r] = (uint32_t)(f.y0 * T.w + f.x0) | (f.x1 != f.x0 + 1 ? 1u << 30 : 0u) |
                        (f.y1 == f.y0 ? 1u << 31 : 0u);
-          if (S.foot_nearest) {
-            // the one credited texel (Section 4.4): its slot, and its id in the second word
-            const uint32_t nt = (uint32_t)nearest_texel(u, v, T.w, T.h);
-            tslot[sd][r][1] = nt;
-            tslot[sd][r][0] = (sd == 1 && bj[0] >= 0 && tslot[0][r][1] == nt) ? tslot[0][r][0]
-                                                                                : table_insert(sm, tkey(T.index, (int)nt));
-            continue;
+          fix[sd][r] = S.foot_nearest ? nearest_texel(u, v, T.w, T.h) : f.ix;
+          fy0[sd][r] = f.y0;
+          if (Model<SH, GR>::DIRECT && pair == p0 && !S.foot_nearest && abs(f.ix) < (1 << 28)) {
+            // the item's texel window: every footprint of its first pair, two texels of margin
+            // (a perturbation moves a footprint by a fraction of a texel)
+            atomicMin(&sm.win[0], f.ix - 2);
+            atomicMax(&sm.win[1], f.ix + 3);
+            atomicMin(&sm.win[2], max(f.y0 - 2, 0));
+            atomicMax(&sm.win[3], min(f.y1 + 2, T.h - 1));
           }
-          if (sd == 1 && bj[0] >= 0 && tpk[1][r] == tpk[0][r]) {  // same footprint on both sides
-            tslot[1][r][0] = tslot[0][r][0];
-            tslot[1][r][1] = tslot[0][r][1];
-            continue;
+        }
+      }
+      if (Model<SH, GR>::DIRECT && pair == p0) {
+        __syncthreads();  // the window's bounds are reduced
+        const long long ww = (long long)sm.win[1] - sm.win[0] + 1, wh = (long long)sm.win[3] - sm.win[2] + 1;
+        if (!S.foot_nearest && ww > 0 && wh > 0 && ww * wh <= Model<SH, GR>::WCAP) {
+          // window slots hold their texel's key from the start (and are listed as used)
+          const TexDev& T = S.rtex[0];
+          for (int s2 = tid; s2 < (int)(ww * wh); s2 += TILE_PX) {
+            const int y = sm.win[2] + s2 / (int)ww, x = wrap_i(sm.win[0] + s2 % (int)ww, T.w);
+            sm.tkey[s2] = tkey(T.index, y * T.w + x);
+            sm.used[s2] = (uint16_t)s2;
           }
-          uint32_t sl[4];
+          if (tid == 0) sm.n_used = sm.n_win = (uint32_t)(ww * wh);
+        } else if (tid == 0) {
+          sm.win[0] = 1;  // no window: every key is hashed over the whole table
+          sm.win[1] = 0;
+        }
+        __syncthreads();
+      }
+      // ---- the table slots of the footprints' texels: computed in the window, hashed outside it
+      {
+        const bool direct = Model<SH, GR>::DIRECT && sm.win[0] <= sm.win[1];
+        // without a window every key is hashed over the whole table (nearest footprints, items
+        // whose window would not fit)
+        const uint32_t hbase = direct ? (uint32_t)Model<SH, GR>::WCAP : 0u;
+        const uint32_t hsize = direct ? (uint32_t)(TABLE - Model<SH, GR>::WCAP) : (uint32_t)TABLE;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) sl[q] = table_insert(sm, tkey(T.index, foot_texel(f, q, T.w)));
-          tslot[sd][r][0] = sl[0] | (sl[1] << 16);
-          tslot[sd][r][1] = sl[2] | (sl[3] << 16);
+        for (int sd = 0; sd < 2; ++sd) {
+          if (bj[sd] < 0) continue;
+#pragma unroll
+          for (int r = 0; r < NFOOT; ++r) {
+            const TexDev& T = S.rtex[r];
+            if (S.foot_nearest) {
+              // the one credited texel (Section 4.4): its slot, and its id in the second word
+              const uint32_t nt = (uint32_t)fix[sd][r];
+              tslot[sd][r][1] = nt;
+              tslot[sd][r][0] = (sd == 1 && bj[0] >= 0 && tslot[0][r][1] == nt)
+                                    ? tslot[0][r][0]
+                                    : table_insert(sm, tkey(T.index, (int)nt), hbase, hsize);
+              continue;
+            }
+            const int y0 = fy0[sd][r];
+            const int y1 = (tpk[sd][r] >> 31) ? y0 : y0 + 1;
+            const int ix = fix[sd][r];
+            if (direct && ix >= sm.win[0] && ix + 1 <= sm.win[1] && y0 >= sm.win[2] && y1 <= sm.win[3]) {
+              const int ww = sm.win[1] - sm.win[0] + 1;
+              const uint32_t s00 = (uint32_t)((y0 - sm.win[2]) * ww + ix - sm.win[0]);
+              const uint32_t s10 = (uint32_t)((y1 - sm.win[2]) * ww + ix - sm.win[0]);
+              tslot[sd][r][0] = s00 | ((s00 + 1) << 16);
+              tslot[sd][r][1] = s10 | ((s10 + 1) << 16);
+            } else if (!Model<SH, GR>::HASH_OUTSIDE) {
+              tslot[sd][r][0] = tslot[sd][r][1] = NOSLOT | (NOSLOT << 16);  // global credits
+            } else {
+              uint32_t sl[4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q)
+                sl[q] = table_insert(sm, tkey(T.index, texel_of(tpk[sd][r], q, T.w)), hbase, hsize);
+              tslot[sd][r][0] = sl[0] | (sl[1] << 16);
+              tslot[sd][r][1] = sl[2] | (sl[3] << 16);
+            }
+          }
         }
       }
 
@@ -808,44 +866,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       //      f+ - f-, credits
       float3 col[2];
       col[0] = col[1] = f3(S.bg[0], S.bg[1], S.bg[2]);
-      if (SH == SHADE_UNLIT && bj[0] >= 0 && bj[1] >= 0 && tpk[0][0] == tpk[1][0]) {
-        // one footprint on both sides: each texel value and sign word is read once
-        const TexDev& T = S.rtex[0];
-        const uint32_t* plane = planes + ws.sgn_off[T.index];
-        float w0[4], w1[4];
-        {
-          const float fx = ffx[0][0], fy = ffy[0][0], gx = ffx[1][0], gy = ffy[1][0];
-          w0[0] = (1.0f - fx) * (1.0f - fy); w0[1] = fx * (1.0f - fy); w0[2] = (1.0f - fx) * fy; w0[3] = fx * fy;
-          w1[0] = (1.0f - gx) * (1.0f - gy); w1[1] = gx * (1.0f - gy); w1[2] = (1.0f - gx) * gy; w1[3] = gx * gy;
-        }
-        float t0[4] = {0.f, 0.f, 0.f, 0.f}, t1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int texel = texel_of(tpk[0][0], q, T.w);
-          const uint32_t sb = plane_nibble(plane, texel);
-          if (!S.foot_nearest) {
-            const uint32_t sl = (tslot[0][0][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-            if (sl != NOSLOT) sm.tsb[sl] = sb;
-          } else {
-            // either side's nearest texel (they may differ inside one bilinear footprint)
-#pragma unroll
-            for (int sd = 0; sd < 2; ++sd)
-              if (texel == (int)tslot[sd][0][1] && (tslot[sd][0][0] & 0xFFFFu) != NOSLOT)
-                sm.tsb[tslot[sd][0][0] & 0xFFFFu] = sb;
-          }
-          const float* src = T.ptr + (long long)texel * T.c;
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            if (c < T.c) {
-              const float th = __ldg(src + c), d = ((sb >> c) & 1) ? -T.eps : T.eps;
-              t0[c] += w0[q] * __fadd_rn(th, d);
-              t1[c] += w1[q] * __fadd_rn(th, -d);
-            }
-        }
-        if (T.c == 1) t0[1] = t0[2] = t0[0], t1[1] = t1[2] = t1[0];
-        col[0] = f3(t0[0], t0[1], t0[2]);
-        col[1] = f3(t1[0], t1[1], t1[2]);
-      } else {
+      {
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
           if (bj[sd] < 0) continue;
@@ -954,6 +975,24 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       }
       // texels: union of both sides' footprints of every read texture (of the group)
       if (valid) {
+        // credit texel id (table slot sl, or NOSLOT: straight to the global sums)
+        auto credit_texel = [&](int r, int id, uint32_t sl) {
+          if (sl != NOSLOT) {
+            atomicAdd(&sm.tA[sl], df);
+            atomicAdd(&sm.tn[sl], 1u);
+            return;
+          }
+#pragma unroll
+          for (int g = 0; g < (GR ? NREAD : 1); ++g) {
+            const TexDev& U = S.rtex[GR ? g : r];
+            const uint32_t sb = plane_nibble(planes + ws.sgn_off[U.index], id);
+            const long long base = U.offset + (long long)id * U.c;
+            for (int c = 0; c < U.c; ++c) {
+              atomicAdd(a.grad + base + c, ((sb >> c) & 1) ? -df : df);
+              atomicAdd(a.counts + base + c, 1u);
+            }
+          }
+        };
 #pragma unroll
         for (int r = 0; r < NFOOT; ++r) {
           const TexDev& T = S.rtex[r];
@@ -963,22 +1002,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
               if (bj[sd] < 0) continue;
               const int id = (int)tslot[sd][r][1];
               if (sd == 1 && bj[0] >= 0 && (int)tslot[0][r][1] == id) continue;
-              const uint32_t sl = tslot[sd][r][0] & 0xFFFFu;
-              if (sl != NOSLOT) {
-                atomicAdd(&sm.tA[sl], df);
-                atomicAdd(&sm.tn[sl], 1u);
-              } else {
-#pragma unroll
-                for (int g = 0; g < (GR ? NREAD : 1); ++g) {
-                  const TexDev& U = S.rtex[GR ? g : r];
-                  const uint32_t sb = plane_nibble(planes + ws.sgn_off[U.index], id);
-                  const long long base = U.offset + (long long)id * U.c;
-                  for (int c = 0; c < U.c; ++c) {
-                    atomicAdd(a.grad + base + c, ((sb >> c) & 1) ? -df : df);
-                    atomicAdd(a.counts + base + c, 1u);
-                  }
-                }
-              }
+              credit_texel(r, id, tslot[sd][r][0] & 0xFFFFu);
             }
             continue;
           }
@@ -1003,23 +1027,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
                 for (int o = 0; o < 4; ++o) dup = dup || id0[o] == id;
               }
               if (dup) continue;
-              const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-              if (sl != NOSLOT) {
-                atomicAdd(&sm.tA[sl], df);
-                atomicAdd(&sm.tn[sl], 1u);
-              } else {
-                // table full: straight to the global sums with this pair's signs
-#pragma unroll
-                for (int g = 0; g < (GR ? NREAD : 1); ++g) {
-                  const TexDev& U = S.rtex[GR ? g : r];
-                  const uint32_t sb = plane_nibble(planes + ws.sgn_off[U.index], id);
-                  const long long base = U.offset + (long long)id * U.c;
-                  for (int c = 0; c < U.c; ++c) {
-                    atomicAdd(a.grad + base + c, ((sb >> c) & 1) ? -df : df);
-                    atomicAdd(a.counts + base + c, 1u);
-                  }
-                }
-              }
+              credit_texel(r, id, (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu);
             }
           }
         }

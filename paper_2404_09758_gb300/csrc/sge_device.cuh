@@ -172,6 +172,7 @@ __device__ __forceinline__ float persp_interp(const PerspW& p, float a0, float a
 struct Foot {
   int x0, x1, y0, y1;  // wrapped / clamped texel coordinates
   float fx, fy;
+  int ix;              // floor(u W - 1/2) before wrapping (x0 = ix mod W, x1 = (ix + 1) mod W)
   int nearest;         // texel id of the nearest texel (set where SceneDev::foot_nearest asks for it)
 };
 
@@ -194,6 +195,7 @@ __device__ __forceinline__ Foot footprint(float u, float v, int W, int H) {
   f.fx = __fsub_rn(x, xf);
   f.fy = __fsub_rn(y, yf);
   int ix = (int)xf, iy = (int)yf;
+  f.ix = ix;
   f.x0 = wrap_i(ix, W);
   f.x1 = wrap_i(ix + 1, W);
   f.y0 = clamp_i(iy, H);
