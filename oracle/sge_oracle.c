@@ -59,8 +59,9 @@ typedef struct {
  * say which.  This oracle uses SplitMix64 (Steele, Lea & Flood, OOPSLA 2014):
  * or_mix64 is its output function and or_splitmix_next its generator step.
  * The key of one estimate chains four generator steps over (seed, iteration,
- * view, pair); s_i is the top bit of the (i+1)-th output of the generator
- * seeded with that key (bit 0 -> +1, bit 1 -> -1).                                */
+ * view, pair); s_i is bit (i mod 64) of the (floor(i / 64) + 1)-th output of the
+ * generator seeded with that key (bit 0 -> +1, bit 1 -> -1): each 64-bit output
+ * gives the signs of 64 consecutive parameters, one bit each.                      */
 #define OR_GAMMA 0x9E3779B97F4A7C15ULL
 
 uint64_t or_mix64(uint64_t z)
@@ -92,9 +93,9 @@ uint64_t or_pair_key(uint64_t seed, uint32_t iter, uint32_t view, uint32_t pair)
 /* s_i for parameter i under key k: +1 or -1, each with probability 1/2 (Eq. 4). */
 int or_sign(uint64_t key, uint64_t i)
 {
-    uint64_t st = key + i * OR_GAMMA;   /* i steps of the generator ...  */
-    uint64_t out = or_splitmix_next(&st); /* ... then the (i+1)-th output */
-    return (out >> 63) ? -1 : 1;
+    uint64_t st = key + (i / 64) * OR_GAMMA; /* floor(i / 64) steps of the generator ... */
+    uint64_t out = or_splitmix_next(&st);    /* ... then the next output                 */
+    return ((out >> (i % 64)) & 1) ? -1 : 1;
 }
 
 /* The views of one iteration (Section 5 draws the view of each estimate at random): a

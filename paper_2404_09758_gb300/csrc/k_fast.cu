@@ -73,7 +73,8 @@ struct __align__(16) TriS {
   float inv_area;
   int margin;       // perturbation margin, fixed-point units (unperturbed set-up only)
   float z[3], iw[3];
-  int pad[2];
+  int small;        // the pruning tests fit 32 bits: |a|, |b| < 2^16, |e0| < 2^29, margin < 2^10
+  int pad;
 };
 
 // One side of a live triangle set up for one pair of the estimator (the triangle's id is the
@@ -360,6 +361,13 @@ __device__ __forceinline__ void stage_unperturbed(const SceneDev& S, const Works
     }
     reach[k] = r;
   }
+  // over the tile (offsets 0..15 * 256) |e| < 2^30 and the margin terms stay below 2^28
+  bool small = can && d.margin < (1 << 10);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    small = small && abs(d.a[k]) < (1 << 16) && abs(d.b[k]) < (1 << 16) && d.e0[k] > -(1ll << 29) &&
+            d.e0[k] < (1ll << 29);
+  d.small = small;
 }
 
 // Does every perturbed version of t cover pixel (dx, dy)?  (exact integer comparisons against the
@@ -367,6 +375,14 @@ __device__ __forceinline__ void stage_unperturbed(const SceneDev& S, const Works
 __device__ __forceinline__ bool surely_covers(const TriS& t, const long long (&reach)[3], int dx, int dy) {
   if (reach[0] < 0) return false;
   bool sure = true;
+  if (t.small) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = (int)t.e0[k] + t.a[k] * (dx * 256) + t.b[k] * (dy * 256);
+      sure = sure && e > (int)reach[k];
+    }
+    return sure;
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);
@@ -381,6 +397,14 @@ __device__ __forceinline__ bool surely_covers(const TriS& t, const long long (&r
 __device__ __forceinline__ bool maybe_visible(const TriS& t, float2 zr, float zsure, int dx, int dy) {
   if (t.tri == -2 || t.margin == 0x7FFFFFFF) return true;
   bool maybe = true;
+  if (t.small) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = (int)t.e0[k] + t.a[k] * (dx * 256) + t.b[k] * (dy * 256);
+      maybe = maybe && (e + t.margin * (abs(t.a[k]) + abs(t.b[k])) >= 0);
+    }
+    return maybe && zr.x <= zsure;
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const long long e = t.e0[k] + (long long)t.a[k] * (dx * 256) + (long long)t.b[k] * (dy * 256);

@@ -44,7 +44,27 @@ __global__ void k_vertex_pass(SceneDev S, Workspace ws, ViewList vl, EstimateArg
 // Texel sign planes of a block of estimates: word w of estimate (slot, pair) holds the signs of
 // eight consecutive texels of one read texture, four bits per texel (bit c: channel c has
 // s = -1), the same signs sign_neg draws for those parameters.  The fused estimators read them
-// when they sample and fold, instead of hashing per texel and pixel.
+// when they sample and fold, instead of hashing per texel and pixel.  A word's 8 C parameters are
+// consecutive, so they span at most two of the generator's 64-parameter outputs; C (the texture's
+// channel count) is a template argument so that the bit gathering unrolls.
+template <int C>
+__device__ __forceinline__ uint32_t sign_word(uint64_t pkey, long long first_param, int n_texels) {
+  const uint64_t i0 = (uint64_t)first_param, blk0 = i0 >> 6;
+  const uint64_t h0 = mix64(pkey + (blk0 + 1) * kGamma);
+  const uint64_t h1 = ((i0 + 8 * C - 1) >> 6) != blk0 ? mix64(pkey + (blk0 + 2) * kGamma) : h0;
+  uint32_t bits = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const uint64_t i = i0 + (uint64_t)(j * C + c);
+      const uint64_t h = (i >> 6) == blk0 ? h0 : h1;
+      if (j < n_texels) bits |= (uint32_t)((h >> (i & 63)) & 1) << (4 * j + c);
+    }
+  }
+  return bits;
+}
+
 __global__ void k_texel_signs(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
   const int slot = blockIdx.z, pb = blockIdx.y;
   const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -57,13 +77,15 @@ __global__ void k_texel_signs(SceneDev S, Workspace ws, ViewList vl, EstimateArg
     if (q < S.nread && w >= ws.sgn_off[S.read_k[q]]) r = q;
   const TexDev& T = S.rtex[r];
   const long long t0 = (w - ws.sgn_off[S.read_k[r]]) * 8;
-  const long long n_tex = (long long)T.w * T.h;
-  uint32_t bits = 0;
-  for (int j = 0; j < 8; ++j) {
-    const long long t = t0 + j;
-    if (t >= n_tex) break;
-    const uint64_t base = (uint64_t)(T.offset + t * T.c);
-    for (int c = 0; c < T.c; ++c) bits |= (uint32_t)sign_neg(pkey, base + c) << (4 * j + c);
+  const long long left = (long long)T.w * T.h - t0;
+  const int n = left < 8 ? (int)left : 8;
+  const long long first = T.offset + t0 * T.c;
+  uint32_t bits;
+  switch (T.c) {
+    case 1: bits = sign_word<1>(pkey, first, n); break;
+    case 2: bits = sign_word<2>(pkey, first, n); break;
+    case 3: bits = sign_word<3>(pkey, first, n); break;
+    default: bits = sign_word<4>(pkey, first, n); break;
   }
   ws.tsign[((long long)slot * ws.max_pairs + pb) * ws.sgn_words + w] = bits;
 }

@@ -24,6 +24,11 @@ struct sge_scene {
   static constexpr int kMaxTimed = 256;
   cudaEvent_t tev[4 * kMaxTimed];  // per timed call: before/after the fast kernel, after the heavy one
   int n_tev;                  // event pairs created (0 = timing off)
+  // a second stream for the work of an estimate call that does not depend on the binning (the
+  // vertex pass and the texel sign planes of its first block of pairs), forked from and joined
+  // back to the caller's stream with events (graph capture follows the fork)
+  cudaStream_t side;
+  cudaEvent_t fork, join;
   int n_timed;                // pairs recorded since the last sge_kernel_time
 };
 
@@ -328,11 +333,19 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   s->desc_dirty = true;
   s->n_tev = 0;
   s->n_timed = 0;
+  s->side = nullptr;
+  s->fork = s->join = nullptr;
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaMemset(w.counters, 0, 64);
   if (e != cudaSuccess) {
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->join) cudaEventDestroy(s->join);
     delete s;
     return cuda_fail(e, "sge_create_scene");
   }
@@ -425,14 +438,23 @@ int estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const uint32_t* it
     if (e == cudaSuccess) e = launch_deep_estimate(s->dev, s->ws, vl, a, st);
     return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
   }
+  // pairs run in blocks of at most max_pairs_per_call (the projected-vertex buffer holds one
+  // block); the first block's vertex pass and sign planes run on the side stream while the caller's
+  // stream bins and prunes
+  EstimateArgs b0 = a;
+  b0.pair_count = pairs_per_view < s->ws.max_pairs ? pairs_per_view : s->ws.max_pairs;
+  if (e == cudaSuccess) e = cudaEventRecord(s->fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->side, s->fork, 0);
+  if (e == cudaSuccess) e = launch_vertex_pass(s->dev, s->ws, vl, b0, s->side);
+  if (e == cudaSuccess) e = cudaEventRecord(s->join, s->side);
   if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st, true);
-  // pairs run in blocks of at most max_pairs_per_call (the projected-vertex buffer holds one block)
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, s->join, 0);
   for (int p0 = 0; p0 < pairs_per_view && e == cudaSuccess; p0 += s->ws.max_pairs) {
     EstimateArgs b = a;
     b.pair_begin = p0;
     b.pair_count = pairs_per_view - p0 < s->ws.max_pairs ? pairs_per_view - p0 : s->ws.max_pairs;
     if (p0 > 0) e = rearm_work(s->ws, st);
-    if (e == cudaSuccess) e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
+    if (e == cudaSuccess && p0 > 0) e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
     const cudaEvent_t* ev = nullptr;
     if (s->n_tev && s->n_timed < sge_scene::kMaxTimed) ev = s->tev + 4 * s->n_timed++;
     if (e == cudaSuccess) e = launch_estimate(s->dev, s->ws, vl, b, s->grid_fast, s->grid_heavy, st, ev);
@@ -899,7 +921,12 @@ int sge_atomic_bench(float* buf, int64_t n_addr, int64_t n_threads, int32_t per_
 }
 
 void sge_destroy_scene(sge_scene* s) {
-  if (s) sge_kernel_timing(s, 0);
+  if (s) {
+    sge_kernel_timing(s, 0);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->join) cudaEventDestroy(s->join);
+  }
   delete s;
 }
 

@@ -18,8 +18,9 @@ namespace sge {
 // The paper draws s_i with a hash function it does not name.  This uses
 // SplitMix64 (Steele, Lea & Flood 2014): mix64 is its output function; one
 // generator step adds the golden-ratio increment and mixes.  The key of an
-// estimate chains four steps over (seed, iteration, view, pair); s_i is the top
-// bit of the (i+1)-th output of the generator seeded with that key.
+// estimate chains four steps over (seed, iteration, view, pair); s_i is bit
+// (i mod 64) of the (floor(i / 64) + 1)-th output of the generator seeded with
+// that key: one output gives the signs of 64 consecutive parameters.
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 
 __host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -38,7 +39,7 @@ __host__ __device__ __forceinline__ uint64_t pair_key(uint64_t seed, uint32_t it
 
 // true when s_i = -1
 __device__ __forceinline__ bool sign_neg(uint64_t key, uint64_t i) {
-  return (mix64(key + (i + 1) * kGamma) >> 63) != 0;
+  return ((mix64(key + ((i >> 6) + 1) * kGamma) >> (i & 63)) & 1) != 0;
 }
 
 // theta_i + side * s_i * eps_i, rounded to float (the perturbed parameter Algorithm 1 stores).

@@ -91,7 +91,13 @@ def test_scale_full_call_matches_oracle_on_samples():
             d = df[view, pair].cpu().numpy().astype(np.float64)
             tol = 1e-5 * np.maximum(fmax, 1e-6) + color_k(sc) * U32 * cond
             bad = np.abs(d - odf) > tol
-            assert not bad.any(), f"view {view} pair {pair}: {bad.sum()} loss differences out of tolerance"
+            if bad.any():
+                r = np.abs(d - odf) / tol
+                y, x = np.unravel_index(int(np.argmax(r)), r.shape)
+                raise AssertionError(
+                    f"view {view} pair {pair}: {bad.sum()} loss differences out of tolerance; worst at (x {x}, "
+                    f"y {y}): gpu {d[y, x]!r} oracle {odf[y, x]!r} tolerance {tol[y, x]!r} (x{r[y, x]:.2f}), "
+                    f"f max {fmax[y, x]!r}, cond {cond[y, x]!r}")
             assert (odf != 0).sum() > 10**5
         else:
             S, C, oloss = out

@@ -46,11 +46,23 @@ def test_splitmix64_known_answers():
     assert got == want
 
 
-def test_sign_is_msb_of_splitmix_stream():
+def test_sign_is_a_bit_of_the_splitmix_stream():
+    """s_i is bit (i mod 64) of the (floor(i / 64) + 1)-th generator output."""
     key = oracle.pair_key(7, 3, 2, 5)
-    for i in (0, 1, 2, 1000, 2**26 + 3):
-        out = oracle.mix64((key + (i + 1) * GAMMA) & M64)
-        assert oracle.sign(key, i) == (-1 if out >> 63 else 1)
+    for i in (0, 1, 2, 63, 64, 65, 1000, 2**26 + 3):
+        out = oracle.mix64((key + (i // 64 + 1) * GAMMA) & M64)
+        assert oracle.sign(key, i) == (-1 if (out >> (i % 64)) & 1 else 1)
+
+
+def test_signs_within_one_output_are_uncorrelated():
+    """Neighbouring parameters take neighbouring bits of one output: their signs (and those one
+    output apart) must be uncorrelated over 10^6 draws (within 5 sigma)."""
+    L = oracle.lib()
+    key = oracle.pair_key(3, 1, 4, 1)
+    n = 1_000_000
+    s = np.fromiter((L.or_sign(key, i) for i in range(n + 64)), np.int64, n + 64)
+    for lag in (1, 2, 31, 32, 63, 64):
+        assert abs((s[:n] * s[lag:lag + n]).sum()) < 5 * math.sqrt(n), lag
 
 
 def test_sign_balance_and_independence():
