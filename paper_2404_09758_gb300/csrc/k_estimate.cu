@@ -128,7 +128,7 @@ __device__ __forceinline__ uint32_t slot_hash(uint32_t k) {
 // Credit df to key: shared-memory table, or global atomics when the table is full.
 template <int HT, int TSC, bool GR>
 __device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT, TSC>& tb, uint32_t key, float df,
-                                       uint64_t pkey, float* grad, uint32_t* counts) {
+                                       const PairSigns& ps, float* grad, uint32_t* counts) {
   uint32_t slot = slot_hash<HT>(key);
 #pragma unroll 1
   for (int p = 0; p < MAX_PROBE; ++p) {
@@ -141,22 +141,22 @@ __device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT, TSC>& tb
     }
     slot = (slot + 1) & (HT - 1);
   }
-  for_each_channel<GR>(S, key, [&](long long p, int) {
-    atomicAdd(grad + p, sign_neg(pkey, (uint64_t)p) ? -df : df);
+  for_each_signed_channel<GR>(S, ps, key, [&](long long p, int, bool neg) {
+    atomicAdd(grad + p, neg ? -df : df);
     atomicAdd(counts + p, 1u);
   });
 }
 
 // Fold the pair's per-key sums into the per-channel accumulators (signs of this pair).
 template <int HT, int TSC, bool GR>
-__device__ __forceinline__ void fold(const SceneDev& S, TableSmem<HT, TSC>& tb, uint64_t pkey) {
+__device__ __forceinline__ void fold(const SceneDev& S, TableSmem<HT, TSC>& tb, const PairSigns& ps) {
   for (int slot = threadIdx.x; slot < HT; slot += blockDim.x) {
     uint32_t key = tb.key[slot];
     if (key == EMPTY) continue;
     uint32_t nn = tb.n[slot];
     if (nn == 0) continue;
     float A = tb.A[slot];
-    for_each_channel<GR>(S, key, [&](long long p, int c) { tb.S[c][slot] += sign_neg(pkey, (uint64_t)p) ? -A : A; });
+    for_each_signed_channel<GR>(S, ps, key, [&](long long, int c, bool neg) { tb.S[c][slot] += neg ? -A : A; });
     tb.cnt[slot] += nn;
     tb.A[slot] = 0.0f;
     tb.n[slot] = 0u;
@@ -275,7 +275,8 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
     const bool all_live = ncand > kHeavyCand;
 
     for (int pair = p0; pair < p1; ++pair) {
-      const uint64_t pkey = pair_key(a.seed, iter_of(a), (uint32_t)view, (uint32_t)pair);
+      // the estimate's signs, from the vertex pass and the texel sign planes
+      const PairSigns ps = pair_signs(ws, slot, pair - a.pair_begin, S.nv);
       const long long vb = ((long long)slot * ws.max_pairs + (pair - a.pair_begin)) * S.nv;
       unsigned long long best[2] = {~0ull, ~0ull};
       int bestj[2] = {-1, -1}, bestc[2] = {-1, -1};
@@ -333,7 +334,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
         else setup_from_pverts(S, ws, vb, tri, sd, rx, ry, t);
         long long e[3];
         cover(t, dx, dy, e);
-        surface(S, view, tri, t, e, pkey, side, sf[sd]);
+        surface_ps(S, view, tri, t, e, ps, side, sf[sd]);
         col[sd] = sf[sd].rgb;
         tris[sd] = tri;
       }
@@ -349,10 +350,10 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
 #pragma unroll
           for (int r = 0; r < MAX_READ; ++r) foot[sd][r] = sf[sd].foot[r];
         for_each_contrib<GR>(S, tris, foot,
-                             [&](uint32_t key) { credit<HT, TSC, GR>(S, sm.tab, key, df, pkey, a.grad, a.counts); });
+                             [&](uint32_t key) { credit<HT, TSC, GR>(S, sm.tab, key, df, ps, a.grad, a.counts); });
       }
       __syncthreads();
-      fold<HT, TSC, GR>(S, sm.tab, pkey);
+      fold<HT, TSC, GR>(S, sm.tab, ps);
     }
     __syncthreads();
     flush_and_clear<HT, TSC, GR>(S, sm.tab, a.grad, a.counts);

@@ -358,6 +358,91 @@ __device__ __forceinline__ void surface(const SceneDev& S, int view, int tri, co
   out.rgb = shade(S, view, alb, nm, rough, metal, p, uv, b);
 }
 
+// ---------------------------------------------------------------- signs of one estimate, precomputed
+// The fused estimators read s_i from what the vertex pass stored (3 bits per welded vertex) and
+// from the texel sign planes (4 bits per texel) instead of hashing: the same values sign_neg gives.
+struct PairSigns {
+  const uint32_t* planes;  // this estimate's texel sign planes
+  const uint8_t* vbits;    // this estimate's vertex sign bits (bits 0-2: x, y, z have s = -1)
+  const int* sgn_off;      // word offset of texture k's plane (Workspace::sgn_off)
+};
+
+__device__ __forceinline__ PairSigns pair_signs(const Workspace& ws, int slot, int pb, int nv) {
+  const long long e = (long long)slot * ws.max_pairs + pb;
+  return PairSigns{ws.tsign + e * ws.sgn_words, ws.vbits + e * nv, ws.sgn_off};
+}
+
+// Sign bits of texel t of texture k (bit c: channel c has s = -1).
+__device__ __forceinline__ uint32_t texel_signs(const PairSigns& ps, int k, long long t) {
+  return (__ldg(ps.planes + ps.sgn_off[k] + (t >> 3)) >> (4 * (t & 7))) & 0xFu;
+}
+
+// Sign bits of welded vertex v (bit c: coordinate c has s = -1).
+__device__ __forceinline__ uint32_t vertex_signs(const PairSigns& ps, int v) { return __ldg(ps.vbits + v) & 7u; }
+
+// sample_tex with the signs of ps.
+__device__ __forceinline__ void sample_tex_ps(const TexDev& T, const Foot& f, const PairSigns& ps, int side,
+                                              float out[4]) {
+  float w[4] = {(1.0f - f.fx) * (1.0f - f.fy), f.fx * (1.0f - f.fy), (1.0f - f.fx) * f.fy, f.fx * f.fy};
+  int tx[4] = {f.x0, f.x1, f.x0, f.x1};
+  int ty[4] = {f.y0, f.y0, f.y1, f.y1};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) out[c] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    long long t = (long long)ty[j] * T.w + tx[j];
+    const float* src = T.ptr + t * T.c;
+    uint32_t sb = texel_signs(ps, T.index, t);
+    if (side < 0) sb = ~sb;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c < T.c) out[c] += w[j] * __fadd_rn(__ldg(src + c), ((sb >> c) & 1) ? -T.eps : T.eps);
+  }
+  if (T.c == 1) out[1] = out[2] = out[0];
+}
+
+// surface() with the signs of ps (side +1 or -1).
+__device__ __forceinline__ void surface_ps(const SceneDev& S, int view, int tri, const Tri& t, const long long e[3],
+                                           const PairSigns& ps, int side, Surf& out) {
+  float l[3];
+  lambdas(e, t.inv_area, l);
+  PerspW pw = persp(l, t.iw);
+  int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
+  float2 uv[3] = {make_float2(__ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t0 + 1)),
+                  make_float2(__ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t1 + 1)),
+                  make_float2(__ldg(S.uvs + 2 * t2), __ldg(S.uvs + 2 * t2 + 1))};
+  out.u = persp_interp(pw, uv[0].x, uv[1].x, uv[2].x);
+  out.v = persp_interp(pw, uv[0].y, uv[1].y, uv[2].y);
+  float alb[4] = {1.f, 1.f, 1.f, 1.f}, nm[4] = {0.5f, 0.5f, 1.f, 0.f}, rough[4] = {0.5f, 0.f, 0.f, 0.f},
+        metal[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int r = 0; r < MAX_READ; ++r) {
+    if (r >= S.nread) break;
+    const TexDev& T = S.rtex[r];
+    out.foot[r] = footprint(out.u, out.v, T.w, T.h);
+    if (S.foot_nearest) out.foot[r].nearest = nearest_texel(out.u, out.v, T.w, T.h);
+    float* dst = T.role == ROLE_ALBEDO ? alb : T.role == ROLE_NORMAL ? nm : T.role == ROLE_ROUGHNESS ? rough : metal;
+    sample_tex_ps(T, out.foot[r], ps, side, dst);
+  }
+  if (S.shading == SHADE_UNLIT) {
+    out.rgb = f3(alb[0], alb[1], alb[2]);
+    return;
+  }
+  float3 p[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int vi = __ldg(S.pidx + 3 * tri + k);
+    uint32_t sb = vertex_signs(ps, vi);
+    if (side < 0) sb = ~sb;
+    const float* src = S.pos + 3ll * vi;
+    p[k] = f3(__fadd_rn(__ldg(src), (sb & 1) ? -S.eps_pos : S.eps_pos),
+              __fadd_rn(__ldg(src + 1), (sb & 2) ? -S.eps_pos : S.eps_pos),
+              __fadd_rn(__ldg(src + 2), (sb & 4) ? -S.eps_pos : S.eps_pos));
+  }
+  float b[3] = {pw.q[0] / pw.qs, pw.q[1] / pw.qs, pw.q[2] / pw.qs};
+  out.rgb = shade(S, view, alb, nm, rough, metal, p, uv, b);
+}
+
 // Project the three perturbed vertices of `tri` and set it up at reference point (rx, ry).
 __device__ __forceinline__ void setup_from_scene(const SceneDev& S, const float* m, int tri, uint64_t key,
                                                  int side, long long rx, long long ry, Tri& t) {
@@ -411,6 +496,33 @@ __device__ __forceinline__ void for_each_channel(const SceneDev& S, uint32_t key
     const TexDev& T = S.tex[kind - 1];
     const long long base = T.offset + (long long)idx * T.c;
     for (int c = 0; c < T.c; ++c) f(base + c, c);
+  }
+}
+
+// Sign of every parameter channel of a contributor key under ps: f(parameter index, slot, s = -1).
+template <bool GR, typename F>
+__device__ __forceinline__ void for_each_signed_channel(const SceneDev& S, const PairSigns& ps, uint32_t key, F&& f) {
+  const uint32_t kind = key >> 28, idx = key & 0x0FFFFFFFu;
+  if (kind == 0) {
+    const uint32_t sb = vertex_signs(ps, (int)idx);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f(3ll * idx + c, c, ((sb >> c) & 1) != 0);
+    return;
+  }
+  if constexpr (GR) {
+#pragma unroll
+    for (int r = 0; r < MAX_READ; ++r) {
+      if (r >= S.nread) break;
+      const TexDev& T = S.rtex[r];
+      const long long base = T.offset + (long long)idx * T.c;
+      const uint32_t sb = texel_signs(ps, T.index, idx);
+      for (int c = 0; c < T.c; ++c) f(base + c, 4 * r + c, ((sb >> c) & 1) != 0);
+    }
+  } else {
+    const TexDev& T = S.tex[kind - 1];
+    const long long base = T.offset + (long long)idx * T.c;
+    const uint32_t sb = texel_signs(ps, T.index, idx);
+    for (int c = 0; c < T.c; ++c) f(base + c, c, ((sb >> c) & 1) != 0);
   }
 }
 
