@@ -48,11 +48,13 @@ __device__ __forceinline__ void deep_insert(unsigned long long (&L)[K], int (&P)
 // Deep lists of one pixel of the tile for NS sides (sides[s] = +1, -1 or 0), with each entry's
 // slot in the staged chunk.  Returns whether the whole bin fit one chunk: then sm.t[s][P[s][j]]
 // still holds the set-up of entry j when the raster is done.
+// pv: the estimate's projected vertices from the vertex pass ([nv][2]: sides +, -), for the two
+// sides of an estimate; NULL: each triangle is projected from the scene with key and sides[].
 template <int NS>
 __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& ws, DeepSmem<NS>& sm, int slot,
                                             int tile, uint64_t key, const int (&sides)[NS],
                                             unsigned long long (&L)[NS][K], int (&P)[NS][K], long long rx,
-                                            long long ry, int dx, int dy) {
+                                            long long ry, int dx, int dy, const int4* pv = nullptr) {
   const int ntl = n_tiles(S);
   const uint32_t beg = ws.tile_off[slot * ntl + tile];
   int nb = (int)(ws.tile_off[slot * ntl + tile + 1] - beg);
@@ -69,7 +71,23 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
       const int tri = (int)ws.bins[beg + c0 + threadIdx.x];
       sm.tri[threadIdx.x] = tri;
 #pragma unroll
-      for (int s = 0; s < NS; ++s) setup_from_scene(S, sm.m, tri, key, sides[s], rx, ry, sm.t[s][threadIdx.x]);
+      for (int s = 0; s < NS; ++s) {
+        if (pv) {
+          PVert v[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int4 q = __ldg(pv + 2 * __ldg(S.pidx + 3 * tri + k) + s);
+            v[k].X = q.x;
+            v[k].Y = q.y;
+            v[k].z = __int_as_float(q.z);
+            v[k].iw = __int_as_float(q.w);
+            v[k].ok = q.x != kNotDrawn;
+          }
+          setup_tri(v[0], v[1], v[2], rx, ry, sm.t[s][threadIdx.x]);
+        } else {
+          setup_from_scene(S, sm.m, tri, key, sides[s], rx, ry, sm.t[s][threadIdx.x]);
+        }
+      }
     }
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
@@ -94,11 +112,13 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
 // foot) is called for each listed fragment with its triangle and albedo footprint.
 // staged: the side's set-ups in shared memory (slots P) when the bin fit one chunk, else NULL
 // (each fragment is set up again; the same arithmetic gives the same set-up).
+// ps: the estimate's precomputed signs (vertex bits, texel planes), or NULL to hash with key.
 template <typename F>
 __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float* m, uint64_t key, int side,
                                                  const unsigned long long (&L)[K], const int (&P)[K],
                                                  const Tri* staged, long long rx, long long ry, int dx, int dy,
-                                                 F&& on_fragment) {
+                                                 F&& on_fragment, const PairSigns* ps = nullptr,
+                                                 const int4* pv = nullptr) {
   const TexDev& A = S.rtex[0];  // the RGBA albedo, the one texture this model reads
   float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
 #pragma unroll
@@ -106,7 +126,23 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     if (L[j] == ~0ull) continue;
     const int tri = (int)(L[j] & 0xFFFFFFFFu);
     Tri own;
-    if (!staged) setup_from_scene(S, m, tri, key, side, rx, ry, own);
+    if (!staged) {
+      if (pv) {
+        PVert v[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int4 q = __ldg(pv + 2 * __ldg(S.pidx + 3 * tri + k) + (side < 0 ? 1 : 0));
+          v[k].X = q.x;
+          v[k].Y = q.y;
+          v[k].z = __int_as_float(q.z);
+          v[k].iw = __int_as_float(q.w);
+          v[k].ok = q.x != kNotDrawn;
+        }
+        setup_tri(v[0], v[1], v[2], rx, ry, own);
+      } else {
+        setup_from_scene(S, m, tri, key, side, rx, ry, own);
+      }
+    }
     const Tri& t = staged ? staged[P[j]] : own;
     long long e[3];
     cover(t, dx, dy, e);
@@ -119,7 +155,8 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     Foot f = footprint(u, v, A.w, A.h);
     if (S.foot_nearest) f.nearest = nearest_texel(u, v, A.w, A.h);
     float a[4];
-    sample_tex(A, f, key, side, a);
+    if (ps) sample_tex_ps(A, f, *ps, side, a);
+    else sample_tex(A, f, key, side, a);
     const float al = fminf(fmaxf(a[3], 0.0f), 1.0f);
     const float w = T * al;
     c0 += w * a[0];
@@ -162,7 +199,11 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
   unsigned long long L[2][K];
   int P[2][K];
   const int sides[2] = {1, -1};
-  const bool resident = deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy);
+  // the estimate's projected vertices and signs, from the vertex pass and the texel sign planes
+  const int pb = pair - a.pair_begin;
+  const int4* pv = ws.pverts + 2 * (((long long)slot * ws.max_pairs + pb) * S.nv);
+  const PairSigns ps = pair_signs(ws, slot, pb, S.nv);
+  const bool resident = deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy, pv);
   float lv = 0.0f;
   if (px < S.W && py < S.H) {
     const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
@@ -189,23 +230,19 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
       add(tkey(A.index, f.y1 * A.w + f.x1));
     };
     const float3 cp = deep_composite(S, sm.m, key, 1, L[0], P[0], resident ? sm.t[0] : nullptr, rx, ry, dx, dy,
-                                     credit_keys);
+                                     credit_keys, &ps, pv);
     const float3 cm = deep_composite(S, sm.m, key, -1, L[1], P[1], resident ? sm.t[1] : nullptr, rx, ry, dx, dy,
-                                     credit_keys);
+                                     credit_keys, &ps, pv);
     const float* tp = S.targets + ((long long)view * npx + p) * 3;
     float fp, fm;
     const float df = loss_diff(cp, cm, f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2)), fp, fm);
     lv = 0.5f * (fp + fm);
     if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
-    for (int q = 0; q < nk; ++q) {
-      long long base;
-      int nch;
-      key_params(S, ks[q], base, nch);
-      for (int c = 0; c < nch; ++c) {
-        atomicAdd(a.grad + base + c, sign_neg(key, (uint64_t)(base + c)) ? -df : df);
-        atomicAdd(a.counts + base + c, 1u);
-      }
-    }
+    for (int q = 0; q < nk; ++q)
+      for_each_signed_channel<false>(S, ps, ks[q], [&](long long p, int, bool neg) {
+        atomicAdd(a.grad + p, neg ? -df : df);
+        atomicAdd(a.counts + p, 1u);
+      });
   }
   if (a.loss) cta_add(lv / (float)a.pairs, sm.red, a.loss + slot);
 }

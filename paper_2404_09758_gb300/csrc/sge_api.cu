@@ -163,16 +163,15 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
   L.cand = take(sizeof(int4) * (size_t)(L.max_views * ntl) * kCandWords * TILE_PX);
   L.ncand = take((size_t)(L.max_views * ntl) * TILE_PX);
   // texel sign planes of every estimate of a block of pairs: 4 bits per texel of each texture the
-  // shading model reads (transparent scenes do not use them)
+  // shading model reads
   SceneDev S;
   make_dev(d, S);
   L.sgn_words = 0;
   for (int k = 0; k < SGE_MAX_TEXTURES; ++k) L.sgn_off[k] = -1;
-  if (d->shading != SGE_SHADE_TRANSPARENT)
-    for (int r = 0; r < S.nread; ++r) {
-      L.sgn_off[S.read_k[r]] = (int)L.sgn_words;
-      L.sgn_words += ((long long)S.rtex[r].w * S.rtex[r].h + 7) / 8;
-    }
+  for (int r = 0; r < S.nread; ++r) {
+    L.sgn_off[S.read_k[r]] = (int)L.sgn_words;
+    L.sgn_words += ((long long)S.rtex[r].w * S.rtex[r].h + 7) / 8;
+  }
   L.tsign = take(sizeof(uint32_t) * (size_t)L.max_views * L.max_pairs * (size_t)L.sgn_words);
   L.total = o;
   return SGE_OK;
@@ -433,9 +432,16 @@ int estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const uint32_t* it
   if (delta_f_out)
     e = cudaMemsetAsync(delta_f_out, 0, sizeof(float) * (size_t)n_views * pairs_per_view * s->dev.W * s->dev.H, st);
   if (s->dev.shading == SHADE_TRANSPARENT) {
-    // deep lists need every binned triangle (no pruning); one launch covers every pair
+    // deep lists need every binned triangle (no pruning); per block of pairs the vertex pass
+    // (projected vertices, sign bits, texel sign planes) and one launch over its estimates
     if (e == cudaSuccess) e = launch_binning(s->dev, s->ws, vl, st);
-    if (e == cudaSuccess) e = launch_deep_estimate(s->dev, s->ws, vl, a, st);
+    for (int p0 = 0; p0 < pairs_per_view && e == cudaSuccess; p0 += s->ws.max_pairs) {
+      EstimateArgs b = a;
+      b.pair_begin = p0;
+      b.pair_count = pairs_per_view - p0 < s->ws.max_pairs ? pairs_per_view - p0 : s->ws.max_pairs;
+      e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
+      if (e == cudaSuccess) e = launch_deep_estimate(s->dev, s->ws, vl, b, st);
+    }
     return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
   }
   // pairs run in blocks of at most max_pairs_per_call (the projected-vertex buffer holds one
