@@ -64,15 +64,12 @@ struct Model {
   static constexpr int WCAP = HASH_OUTSIDE ? TABLE * 3 / 4 : TABLE;
 };
 
-// One side of a staged triangle (unperturbed set-up for the pruning pass, with its margin).
+// A bin triangle's unperturbed edge functions for the pruning pass, with its margin; 64 bytes.
 struct __align__(16) TriS {
   long long e0[3];  // oriented edge functions at the tile's first pixel centre
-  int bias;         // bit k set: edge k is not a top/left edge
-  int tri;          // triangle id; -1 not drawn; -2 (unperturbed) not drawable: always a candidate
   int a[3], b[3];   // oriented edge steps per fixed-point unit in x and y
-  float inv_area;
-  int margin;       // perturbation margin, fixed-point units (unperturbed set-up only)
-  float z[3], iw[3];
+  int tri;          // triangle id; -2: not drawable unperturbed, so always a candidate
+  int margin;       // perturbation margin, fixed-point units
   int small;        // the pruning tests fit 32 bits: |a|, |b| < 2^16, |e0| < 2^29, margin < 2^10
   int pad;
 };
@@ -124,26 +121,6 @@ struct FastSmem {
 // Two unlit CTAs share an SM: 228 KB of shared memory less 1 KB reserved per CTA.
 static_assert(2 * (sizeof(FastSmem<Model<SHADE_UNLIT>::TABLE, Model<SHADE_UNLIT>::TSC>) + 1024) <= 228 * 1024,
               "the unlit fast estimator must fit two CTAs per SM");
-
-__device__ __forceinline__ void store_side(TriS& d, const Tri& t, int tri) {
-  if (!t.ok) {
-    d.tri = -1;
-    return;
-  }
-  int bias = 0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    d.e0[k] = t.e0[k];
-    d.a[k] = t.a[k];
-    d.b[k] = t.b[k];
-    d.z[k] = t.z[k];
-    d.iw[k] = t.iw[k];
-    bias |= (t.bias[k] ? 1 : 0) << k;
-  }
-  d.bias = bias;
-  d.inv_area = t.inv_area;
-  d.tri = tri;
-}
 
 __device__ __forceinline__ void store_side_tri(SideTri& d, const Tri& t) {
   if (!t.ok) {
@@ -347,8 +324,13 @@ __device__ __forceinline__ void stage_unperturbed(const SceneDev& S, const Works
                                                   long long (&reach)[3]) {
   Tri t;
   setup_from_scene(S, m, tri, 0, 0, rx, ry, t);
-  store_side(d, t, tri);
-  if (!t.ok) d.tri = -2;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    d.e0[k] = t.e0[k];
+    d.a[k] = t.a[k];
+    d.b[k] = t.b[k];
+  }
+  d.tri = t.ok ? tri : -2;
   d.margin = ws.tri_margin[(long long)slot * S.nt + tri];
   zr = ws.tri_z[(long long)slot * S.nt + tri];
   const bool can = d.tri >= 0 && d.margin != 0x7FFFFFFF;
@@ -421,6 +403,7 @@ struct PruneSmem {
   uint32_t id[NB];
   uint8_t live[NB];
   uint16_t remap[NB];  // compacted position of each live entry of a single-chunk bin
+  uint16_t cl[kHeavyCand][TILE_PX];  // each pixel's first kHeavyCand candidates (column per pixel)
   float m[16];
   int wsum[TILE_PX / 32];
 };
@@ -444,66 +427,46 @@ __device__ __forceinline__ int block_prefix(int flag, int* wsum, int* total) {
   return before + in_warp;
 }
 
-// Candidate list of one pixel: up to kHeavyCand 16-bit entries (light tiles repack them as 8-bit).
-struct CandList {
-  uint32_t w[kHeavyCand / 2];
-  int n;
-  __device__ __forceinline__ void clear() {
-#pragma unroll
-    for (int i = 0; i < kHeavyCand / 2; ++i) w[i] = 0u;
-    n = 0;
-  }
-  __device__ __forceinline__ void push(uint32_t j) {
-    const uint32_t bits = j << (16 * (n & 1));
-#pragma unroll
-    for (int i = 0; i < kHeavyCand / 2; ++i)
-      if ((n >> 1) == i) w[i] |= bits;
-    ++n;
-  }
-  __device__ __forceinline__ uint32_t get(int q) const {
-    uint32_t v = 0;
-#pragma unroll
-    for (int i = 0; i < kHeavyCand / 2; ++i)
-      if ((q >> 1) == i) v = w[i];
-    return (v >> (16 * (q & 1))) & 0xFFFFu;
-  }
-};
-
-// Store a pixel's list: 8-bit indices (light tile, <= CMAX kept, in ascending order of the
-// triangles' smallest depth under any perturbation, zr(j) of live index j) or 16-bit ones, and
-// its length min(n, 255).
+// Store a pixel's list (its column of cl, n entries found): 8-bit indices (light tile, the first
+// CMAX, in ascending order of the triangles' smallest depth under any perturbation, zr(j) of live
+// index j, ties in list order) or 16-bit ones (the first kHeavyCand, in list order), and its
+// length min(n, 255).
 template <typename ZR>
-__device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_index, int tid, const CandList& c,
-                                            bool wide, ZR&& zr) {
+__device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_index, int tid,
+                                            const uint16_t (*cl)[TILE_PX], int n, bool wide, ZR&& zr) {
   const long long ci = tile_index * kCandWords * TILE_PX + tid;
   if (wide) {
+    const int k = min(n, kHeavyCand);
 #pragma unroll
-    for (int w = 0; w < kCandWords; ++w)
-      ws.cand[ci + w * TILE_PX] =
-          make_int4((int)c.w[4 * w], (int)c.w[4 * w + 1], (int)c.w[4 * w + 2], (int)c.w[4 * w + 3]);
-  } else {
-    // insertion sort by smallest depth: the estimator stops at the first candidate that lies
-    // wholly behind the nearest covering triangle found so far
-    uint32_t id[CMAX];
-    float z[CMAX];
-    const int k = min(c.n, CMAX);
-    for (int q = 0; q < k; ++q) {
-      const uint32_t j = c.get(q);
-      const float zj = zr(j);
-      int at = q;
-      while (at > 0 && z[at - 1] > zj) {
-        z[at] = z[at - 1];
-        id[at] = id[at - 1];
-        --at;
+    for (int w = 0; w < kCandWords; ++w) {
+      uint32_t v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int q = 8 * w + 2 * i;
+        v[i] = (q < k ? (uint32_t)cl[q][tid] : 0u) | (q + 1 < k ? (uint32_t)cl[q + 1][tid] << 16 : 0u);
       }
-      z[at] = zj;
-      id[at] = j;
+      ws.cand[ci + w * TILE_PX] = make_int4((int)v[0], (int)v[1], (int)v[2], (int)v[3]);
     }
+  } else {
+    // each entry goes to its rank in depth order: the estimator stops at the first candidate
+    // that lies wholly behind the nearest covering triangle found so far
+    const int k = min(n, CMAX);
     uint32_t b[CMAX / 4] = {};
-    for (int q = 0; q < k; ++q) b[q >> 2] |= id[q] << (8 * (q & 3));
+    for (int q = 0; q < k; ++q) {
+      const uint32_t j = cl[q][tid];
+      const float zj = zr(j);
+      int rank = 0;
+      for (int r = 0; r < k; ++r) {
+        const float zo = zr((uint32_t)cl[r][tid]);
+        rank += (zo < zj || (zo == zj && r < q)) ? 1 : 0;
+      }
+      const uint32_t bits = j << (8 * (rank & 3));
+#pragma unroll
+      for (int i = 0; i < CMAX / 4; ++i) b[i] |= (rank >> 2) == i ? bits : 0u;
+    }
     ws.cand[ci] = make_int4((int)b[0], (int)b[1], (int)b[2], (int)b[3]);
   }
-  ws.ncand[tile_index * TILE_PX + tid] = (uint8_t)min(c.n, 255);
+  ws.ncand[tile_index * TILE_PX + tid] = (uint8_t)min(n, 255);
 }
 
 // Per (view slot, tile): drop from the bin every triangle that no perturbation of the call can
@@ -549,8 +512,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
   // pass 2: mark and compact the triangles some pixel may see (a single chunk is still staged;
   // its pixels' candidate lists are found on the way, by bin position, and renumbered below)
   const bool single = nb <= NB;
-  CandList cl;
-  cl.clear();
+  int n_cl = 0;  // candidates found for this pixel (the first kHeavyCand kept in sm.cl)
   int n_live = 0;
   for (int c0 = 0; c0 < nb; c0 += NB) {
     const int cnt = min(NB, nb - c0);
@@ -564,8 +526,8 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
         for (int j = 0; j < cnt; ++j)
           if (maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
             sm.live[j] = 1;
-            if (cl.n < kHeavyCand) cl.push((uint32_t)j);
-            else ++cl.n;
+            if (n_cl < kHeavyCand) sm.cl[n_cl][tid] = (uint16_t)j;
+            ++n_cl;
           }
       } else {
         for (int j = 0; j < cnt; ++j)
@@ -592,15 +554,13 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
   const bool wide = n_live > light_bin;  // heavy tile: 16-bit indices
   if (single) {
     __syncthreads();
-    CandList out;
-    out.clear();
-    const int k = min(cl.n, kHeavyCand);
-    for (int q = 0; q < k; ++q) out.push(sm.remap[cl.get(q)]);
-    out.n = cl.n;
+    // bin positions -> live indices (each pixel renumbers its own column)
+    const int k = min(n_cl, kHeavyCand);
+    for (int q = 0; q < k; ++q) sm.cl[q][tid] = sm.remap[sm.cl[q][tid]];
     // live index -> bin position of the staged chunk, for the depth order
     if (tid < nb && sm.live[tid]) sm.id[sm.remap[tid]] = (uint32_t)tid;
     __syncthreads();
-    store_cands(ws, tix, tid, out, wide, [&](uint32_t j) { return sm.zr[sm.id[j]].x; });
+    store_cands(ws, tix, tid, sm.cl, n_cl, wide, [&](uint32_t j) { return sm.zr[sm.id[j]].x; });
     return;
   }
   // pass 3 (bins of more than one chunk): each pixel's candidates among the live triangles, in
@@ -613,22 +573,22 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     if (valid)
       for (int j = 0; j < cnt; ++j)
         if (maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
-          if (cl.n < kHeavyCand) cl.push((uint32_t)(c0 + j));
-          else ++cl.n;
+          if (n_cl < kHeavyCand) sm.cl[n_cl][tid] = (uint16_t)(c0 + j);
+          ++n_cl;
         }
   }
   // a light tile's live triangles are one staged chunk here, indexed by live position
-  store_cands(ws, tix, tid, cl, wide, [&](uint32_t j) { return sm.zr[j].x; });
+  store_cands(ws, tix, tid, sm.cl, n_cl, wide, [&](uint32_t j) { return sm.zr[j].x; });
 }
 
-__global__ void __launch_bounds__(TILE_PX) k_bin_prune(SceneDev S, Workspace ws, ViewList vl) {
+__global__ void __launch_bounds__(TILE_PX, 4) k_bin_prune(SceneDev S, Workspace ws, ViewList vl) {
   __shared__ PruneSmem sm;
   prune_tile(S, ws, vl.n, vl.id[blockIdx.y], blockIdx.y, blockIdx.x, ws.light_bin, sm);
 }
 
 // Batched form: every (tile, view slot, asset) of a batched call in one launch; each CTA reads
 // its asset's scene and workspace from the asset's launch descriptor in device memory.
-__global__ void __launch_bounds__(TILE_PX) k_bin_prune_batch(const BatchArgs P) {
+__global__ void __launch_bounds__(TILE_PX, 4) k_bin_prune_batch(const BatchArgs P) {
   __shared__ PruneSmem sm;
   const BatchAsset& A = P.as[blockIdx.z];
   const int slot = blockIdx.y;

@@ -45,49 +45,58 @@ __global__ void k_vertex_pass(SceneDev S, Workspace ws, ViewList vl, EstimateArg
 // eight consecutive texels of one read texture, four bits per texel (bit c: channel c has
 // s = -1), the same signs sign_neg draws for those parameters.  The fused estimators read them
 // when they sample and fold, instead of hashing per texel and pixel.  A word's 8 C parameters are
-// consecutive, so they span at most two of the generator's 64-parameter outputs; C (the texture's
-// channel count) is a template argument so that the bit gathering unrolls.
+// consecutive, so they are bits [i0 mod 64, i0 mod 64 + 8 C) of the generator's output for block
+// i0 / 64 followed by the next block's output: one funnel shift, then the 8 C bits are spread to
+// one nibble per texel.
 template <int C>
 __device__ __forceinline__ uint32_t sign_word(uint64_t pkey, long long first_param, int n_texels) {
   const uint64_t i0 = (uint64_t)first_param, blk0 = i0 >> 6;
-  const uint64_t h0 = mix64(pkey + (blk0 + 1) * kGamma);
-  const uint64_t h1 = ((i0 + 8 * C - 1) >> 6) != blk0 ? mix64(pkey + (blk0 + 2) * kGamma) : h0;
-  uint32_t bits = 0;
+  const int sh = (int)(i0 & 63);
+  uint64_t x = mix64(pkey + (blk0 + 1) * kGamma) >> sh;
+  if (sh + 8 * C > 64) x |= mix64(pkey + (blk0 + 2) * kGamma) << (64 - sh);
+  const uint32_t b = (uint32_t)x;
+  uint32_t bits;
+  if (C == 4) {
+    bits = b;
+  } else {
+    bits = 0;
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const uint64_t i = i0 + (uint64_t)(j * C + c);
-      const uint64_t h = (i >> 6) == blk0 ? h0 : h1;
-      if (j < n_texels) bits |= (uint32_t)((h >> (i & 63)) & 1) << (4 * j + c);
-    }
+    for (int j = 0; j < 8; ++j) bits |= ((b >> (C * j)) & ((1u << C) - 1u)) << (4 * j);
   }
-  return bits;
+  return n_texels < 8 ? bits & ((1u << (4 * n_texels)) - 1u) : bits;
 }
+
+constexpr int kSignWordsPerThread = 4;
 
 __global__ void k_texel_signs(SceneDev S, Workspace ws, ViewList vl, EstimateArgs a) {
   const int slot = blockIdx.z, pb = blockIdx.y;
-  const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= ws.sgn_words) return;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * kSignWordsPerThread;
+  if (w0 >= ws.sgn_words) return;
   const uint64_t pkey = pair_key(a.seed, iter_of(a), (uint32_t)vl.id[slot], (uint32_t)(a.pair_begin + pb));
-  // the read texture whose plane holds word w (planes in read order, each starting on a word)
-  int r = 0;
+  uint32_t* out = ws.tsign + ((long long)slot * ws.max_pairs + pb) * ws.sgn_words;
 #pragma unroll
-  for (int q = 1; q < MAX_READ; ++q)
-    if (q < S.nread && w >= ws.sgn_off[S.read_k[q]]) r = q;
-  const TexDev& T = S.rtex[r];
-  const long long t0 = (w - ws.sgn_off[S.read_k[r]]) * 8;
-  const long long left = (long long)T.w * T.h - t0;
-  const int n = left < 8 ? (int)left : 8;
-  const long long first = T.offset + t0 * T.c;
-  uint32_t bits;
-  switch (T.c) {
-    case 1: bits = sign_word<1>(pkey, first, n); break;
-    case 2: bits = sign_word<2>(pkey, first, n); break;
-    case 3: bits = sign_word<3>(pkey, first, n); break;
-    default: bits = sign_word<4>(pkey, first, n); break;
+  for (int q = 0; q < kSignWordsPerThread; ++q) {
+    const long long w = w0 + q;
+    if (w >= ws.sgn_words) break;
+    // the read texture whose plane holds word w (planes in read order, each starting on a word)
+    int r = 0;
+#pragma unroll
+    for (int k = 1; k < MAX_READ; ++k)
+      if (k < S.nread && w >= ws.sgn_off[S.read_k[k]]) r = k;
+    const TexDev& T = S.rtex[r];
+    const long long t0 = (w - ws.sgn_off[S.read_k[r]]) * 8;
+    const long long left = (long long)T.w * T.h - t0;
+    const int n = left < 8 ? (int)left : 8;
+    const long long first = T.offset + t0 * T.c;
+    uint32_t bits;
+    switch (T.c) {
+      case 1: bits = sign_word<1>(pkey, first, n); break;
+      case 2: bits = sign_word<2>(pkey, first, n); break;
+      case 3: bits = sign_word<3>(pkey, first, n); break;
+      default: bits = sign_word<4>(pkey, first, n); break;
+    }
+    out[w] = bits;
   }
-  ws.tsign[((long long)slot * ws.max_pairs + pb) * ws.sgn_words + w] = bits;
 }
 
 }  // namespace
@@ -97,7 +106,8 @@ cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const Vie
   dim3 grid((S.nv + 255) / 256, a.pair_count, vl.n);
   k_vertex_pass<<<grid, 256, 0, st>>>(S, ws, vl, a);
   if (ws.tsign && ws.sgn_words > 0) {
-    dim3 gs((unsigned)((ws.sgn_words + 255) / 256), a.pair_count, vl.n);
+    const long long threads = (ws.sgn_words + kSignWordsPerThread - 1) / kSignWordsPerThread;
+    dim3 gs((unsigned)((threads + 255) / 256), a.pair_count, vl.n);
     k_texel_signs<<<gs, 256, 0, st>>>(S, ws, vl, a);
   }
   return cudaGetLastError();

@@ -42,6 +42,15 @@ def _lambert_mixed_sizes():
                                target_textures=[sc.target_textures[0], synth.normal_map_texture(32, 32, seed=6)])
 
 
+def _unlit_channels(c, tw, th):
+    """Unlit sphere whose albedo has c channels at tw x th texels (a size whose sign planes end
+    mid-word: 8 texels per plane word)."""
+    import dataclasses
+    sc = _sphere(64, 64, 128, 96, 80, synth.random_eyes(2, 9))
+    tex = synth.Texture(synth.constant_texture(tw, th, c, 0.5), sc.textures[0].eps, synth.ROLE_ALBEDO)
+    return dataclasses.replace(sc, textures=[tex], target_textures=[synth.sinusoid_texture(tw, th, c, seed=8)])
+
+
 def _ggx_small():
     return synth.config_scale(n_views=2, pairs=2, render=96, tex=64, n_lon=64, n_lat=32)
 
@@ -117,6 +126,9 @@ ESTIMATE_CASES = {
     "dense_lambert": (lambda: synth.config_autograd(n_views=2, pairs=2, render=256, tex=64), [1, 0], 2, {}),
     "dense_ggx": (lambda: synth.config_scale(n_views=2, pairs=2, render=256, tex=64, n_lon=256, n_lat=128),
                   [0, 1], 2, {"pairs_per_item": 1}),
+    # one- and two-channel albedo of ragged sizes (every channel count of the texel sign planes)
+    "albedo_1ch_37x29": (lambda: _unlit_channels(1, 37, 29), [0, 1], 3, {}),
+    "albedo_2ch_50x21": (lambda: _unlit_channels(2, 50, 21), [1, 0], 3, {"pairs_per_item": 2}),
     # 5 pairs projected in blocks of 2 (max_pairs_per_call): three launches of each estimator kernel
     "pair_blocks": (lambda: _sphere(64, 64, 128, 96, 96, synth.random_eyes(2, 7)), [0, 1], 5,
                     {"max_pairs_per_call": 2, "pairs_per_item": 2}),
