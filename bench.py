@@ -51,10 +51,12 @@ OPS_VISIBLE, OPS_UV, OPS_FOOT, OPS_WEIGHTS, OPS_PER_TEXEL_CHANNEL = 20, 17, 14, 
 OPS_SHADE = {0: 0, 1: 55, 2: 125}  # unlit; Lambert with a normal map; GGX + Lambert (per side)
 OPS_LOSS_DIFF = 12  # per pixel pair: sum_c (I+ - I-)(I+ + I- - 2I)
 OPS_CREDIT = 2      # per contribution: one add to the parameter's sum, one to its count
-# ncu capture of this kernel build (profiles/k_estimate_fast_sphere8k_r512.md): executed thread
-# instructions per pixel pair and DRAM bytes per launch; None until captured for this build
-NCU_INSTR_PER_PIXEL_PAIR = None
-NCU_DRAM_BYTES_PER_LAUNCH = None
+# One ncu --set full capture of this build's k_estimate_fast<unlit> on this workload (one launch =
+# one estimate call, 134.2 M pixel pairs): smsp__inst_executed.sum 5.377 G x 22.13 active lanes =
+# 887 thread instructions per pixel pair; dram__bytes_read.sum + dram__bytes_write.sum =
+# 164.80 MB + 7.06 MB per launch.  Set to None when the kernel changes until it is captured again.
+NCU_INSTR_PER_PIXEL_PAIR = 887.0
+NCU_DRAM_BYTES_PER_LAUNCH = 171.86e6
 
 
 def method_ops(shading: int, read_channels, covered_sides: float, covered_pairs: float, contributions: float):
@@ -403,9 +405,10 @@ def run_ours(args):
             "batched_over_plain": plain_ms / (1000.0 * t_total / args.steps),
             "roofline": roofline,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            # per iteration: 3 binning kernels, the pruning pass, the vertex pass, the fast and the
-            # heavy-bin estimator, the background-loss kernel, the step kernel and the advance
-            "gpu_launches": 10 * args.steps,
+            # per iteration: 3 binning kernels, the pruning pass, the vertex pass, the texel sign
+            # planes, the fast and the heavy-bin estimator, the background-loss kernel, the step
+            # kernel and the advance
+            "gpu_launches": 11 * args.steps,
             "clocks": clocks}
     if rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline()
@@ -520,9 +523,10 @@ def measure_uneven(steps: int, warmup: int):
                                   "autotune_ms": tune_ms}},
             "param_gradients_per_s": sum(contributions) * steps / t_total,
             "contributions_per_asset": contributions,
-            # per asset: 3 binning kernels, background loss, vertex pass, Adam step; per call: the
-            # batched pruning pass, the fast and the heavy-bin estimator, the advance
-            "gpu_launches": (6 * len(assets) + 4) * steps,
+            # per asset: 3 binning kernels, background loss, vertex pass, texel sign planes, Adam
+            # step; per call: the batched pruning pass, the fast and the heavy-bin estimator, the
+            # advance
+            "gpu_launches": (7 * len(assets) + 4) * steps,
             "clocks": clk.summary()}
     return line
 
@@ -613,7 +617,8 @@ def measure_scale(steps: int, warmup: int):
             "param_gradients_per_s": contributions * steps / t_total,
             "contributions_per_step": contributions,
             "fast_kernel_ms": fast_ms / max(fast_n, 1),
-            "gpu_launches": 10 * steps,
+            # as the default workload's iteration: 11 kernels
+            "gpu_launches": 11 * steps,
             "clocks": clk.summary()}
     return line
 
@@ -762,8 +767,9 @@ def run_transparent(args):
                        "triangles": int(len(sc.pos_idx)), "params": int(g.n_params),
                        "l2": "flushed between timed steps (256 MB write)", "graph": "none (eager)"},
             "contributions_per_s": contributions * args.steps / t_total,
-            # per call: the three binning kernels and the deep estimator
-            "gpu_launches": 4 * args.steps,
+            # per call: the three binning kernels, the vertex pass, the texel sign planes and the
+            # deep estimator
+            "gpu_launches": 6 * args.steps,
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -939,9 +945,10 @@ def run_converge(args):
                        "graph": "one iteration captured in a CUDA graph and replayed (device-resident iteration "
                                 "index and Adam step); the error is measured between replays"},
             "initial_error": e0, "curve": curve, "reduction": curve[-1][1] / e0,
-            # per iteration: 4 binning and pruning kernels, the vertex pass, the two estimators, the
-            # background loss, the step, the advance (+ the two refine products of the control mesh)
-            "gpu_launches": (12 if control else 10) * n_iter}
+            # per iteration: 4 binning and pruning kernels, the vertex pass, the texel sign planes, the
+            # two estimators, the background loss, the step, the advance (+ the two refine products
+            # of the control mesh)
+            "gpu_launches": (13 if control else 11) * n_iter}
     print(json.dumps(line), flush=True)
 
 
