@@ -51,7 +51,9 @@ typedef enum {
     SGE_ERR_BIN_OVERFLOW = 3,  /* (device status) tile bins exceeded bin_capacity    */
     SGE_ERR_BAD_INDEX = 4,     /* (device status) an index buffer entry out of range */
     SGE_ERR_UNSUPPORTED = 5,   /* a valid request the library does not implement     */
-    SGE_ERR_WORKSPACE = 6      /* workspace missing, too small or misaligned         */
+    SGE_ERR_WORKSPACE = 6,     /* workspace missing, too small or misaligned         */
+    SGE_ERR_BOUNDS = 7         /* (device status, checked build) an index failed its
+                                  range check; that access was skipped               */
 } sge_result;
 
 /* Texture roles: what the shading model reads a texture as. */
@@ -371,6 +373,36 @@ int sge_render_idb_static(const sge_scene_desc *desc, int32_t view, uint64_t see
  * CUDA events on `stream`: n_threads * per_thread reductions.  n_addr = n_threads gives one
  * address per thread; small n_addr gives 1-of-n_addr hot addresses. */
 int sge_atomic_bench(float *buf, int64_t n_addr, int64_t n_threads, int32_t per_thread, sge_stream_t stream);
+
+/* ---- checked build (the library compiled with SGE_CHECKED=1, libsge_checked.so) ----
+ * Stand-in for a memory checker: every kernel range-checks the indices it takes from the
+ * caller's data or computes into the workspace before it uses them: vertex and UV indices read
+ * from pos_idx / uv_idx (against n_positions / n_uvs), bin entries (against bin_capacity),
+ * texel sign-plane words (against one estimate's plane size), parameter indices of the gradient
+ * sums and counts (against sge_num_params), and the direct slots of the fast estimator's
+ * shared-memory texel table.  A failing check does not make the access (a read yields element
+ * 0 or nothing, a write or credit is dropped) and records SGE_ERR_BOUNDS in the device status
+ * word (sge_status); nothing traps.  Results of a call that recorded it are meaningless. */
+
+/* 1 if this library is the checked build, else 0. */
+int sge_checked_build(void);
+
+/* Which range sge_check_limit lowers. */
+enum {
+    SGE_LIMIT_VERTICES = 0,     /* vertex indices read from pos_idx        */
+    SGE_LIMIT_UVS = 1,          /* UV indices read from uv_idx             */
+    SGE_LIMIT_BIN_ENTRIES = 2,  /* bin entries (bin_capacity)              */
+    SGE_LIMIT_SIGN_WORDS = 3,   /* words of one estimate's sign planes     */
+    SGE_LIMIT_PARAMS = 4        /* parameter indices of grad_sums / counts */
+};
+
+/* Checked build only (else SGE_ERR_UNSUPPORTED): set the bound that the checks of `which`
+ * compare against to `limit` (0 <= limit <= the true size), or back to the true size
+ * (limit < 0).  It changes no allocation and no logic of the library, only what the checks
+ * treat as the end of the range, so that a test can make the range too small from the host and
+ * see the checks fire without any access leaving its buffer.  SGE_ERR_INVALID_ARG for a bad
+ * `which` or a limit above the true size. */
+int sge_check_limit(sge_scene *scene, int32_t which, int64_t limit);
 
 /* Timing of the estimator kernels, for benchmarks (the paper has no counterpart).
  * While enabled, each sge_estimate_grad call records CUDA events on its stream right

@@ -15,17 +15,25 @@ import ctypes as C
 from typing import List, Optional, Sequence
 
 from . import _abi
-from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, FOOT_BILINEAR, FOOT_NEAREST, MAX_LAYERS, MAX_TEXTURES, MAX_VIEWS_PER_CALL, OK,
+from ._abi import (ERR_BIN_OVERFLOW, ERR_BAD_INDEX, ERR_BOUNDS, LIMIT_VERTICES, LIMIT_UVS, LIMIT_BIN_ENTRIES,
+                   LIMIT_SIGN_WORDS, LIMIT_PARAMS, FOOT_BILINEAR, FOOT_NEAREST, MAX_LAYERS, MAX_TEXTURES, MAX_VIEWS_PER_CALL, OK,
                    SHADE_GGX, SHADE_LAMBERT, SHADE_TRANSPARENT, SHADE_UNLIT, STEP_ADAM, STEP_SGD, STEP_SGD_MEAN,
                    SGEError)
 from ._build import build
 
-__all__ = ["Scene", "Batch", "ControlMesh", "IterState", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
-           "STEP_SGD_MEAN", "FOOT_BILINEAR", "FOOT_NEAREST", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "MAX_VIEWS_PER_CALL"]
+__all__ = ["Scene", "Batch", "ControlMesh", "IterState", "save_checkpoint", "load_checkpoint", "draw_views", "refine", "SGEError", "SGEFunction", "sge_loss", "build", "load", "STEP_SGD", "STEP_ADAM",
+           "STEP_SGD_MEAN", "FOOT_BILINEAR", "FOOT_NEAREST", "OK", "ERR_BIN_OVERFLOW", "ERR_BAD_INDEX", "ERR_BOUNDS",
+           "LIMIT_VERTICES", "LIMIT_UVS", "LIMIT_BIN_ENTRIES", "LIMIT_SIGN_WORDS", "LIMIT_PARAMS", "checked_build",
+           "MAX_VIEWS_PER_CALL"]
 
 
 def load(build_if_missing: bool = False):
     return _abi.load(build_if_missing)
+
+
+def checked_build() -> bool:
+    """Is the loaded library the range-checked build (SGE_CHECKED=1)?"""
+    return bool(_abi.load().sge_checked_build())
 
 
 def _torch():
@@ -178,6 +186,11 @@ class Scene:
         L = _abi.load()
         _abi.check(L.sge_validate(self._h, _stream_ptr(stream)))
         return self.status(stream)
+
+    def check_limit(self, which: int, limit: int = -1) -> None:
+        """Checked build only: lower the bound the range checks of `which` (LIMIT_*) compare
+        against (limit < 0: back to the true size); no allocation or logic changes."""
+        _abi.check(_abi.load().sge_check_limit(self._h, which, limit))
 
     def status(self, stream=None) -> int:
         v = C.c_int32()
@@ -337,6 +350,59 @@ class IterState:
         """(iteration, t) as they stand (synchronises)."""
         it, t = (int(x) for x in self.tensor.tolist())
         return it & 0xFFFFFFFF, t
+
+
+CHECKPOINT_FORMAT = "sge-checkpoint-1"
+
+
+def save_checkpoint(path, scene, seed: int, it, t=None, m=None, v=None) -> None:
+    """Save an optimisation's state with torch.save: theta (every parameter group of `scene`:
+    positions, then each texture), Adam's first and second moments m and v (or None for SGD), the
+    seed, the iteration index and Adam's step number t.  `it` may be an IterState (then it also
+    gives t).  Synchronises the device first.  The sign generator is counter-based (seed,
+    iteration, view, pair, parameter), so these determine every later estimate: a resumed run
+    draws the same signs and credits the same counts."""
+    torch = _torch()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+    if isinstance(it, IterState):
+        it, t = it.value()
+    if t is None:
+        raise ValueError("save_checkpoint: t (Adam's step number) is required")
+    state = {"format": CHECKPOINT_FORMAT, "seed": int(seed), "iter": int(it), "t": int(t),
+             "n_params": int(scene.n_params),
+             "groups": [g.detach().to("cpu", copy=True) for g in scene.param_groups()],
+             "m": None if m is None else m.detach().to("cpu", copy=True),
+             "v": None if v is None else v.detach().to("cpu", copy=True)}
+    torch.save(state, path)
+
+
+def load_checkpoint(path, scene, m=None, v=None, iter_state=None):
+    """Restore a save_checkpoint file into `scene`'s own parameter tensors (in place: the
+    library keeps their device addresses), into m and v (when the file has them), and, given one,
+    into an IterState.  Returns (seed, iteration, t).  Raises ValueError if the file is not a
+    checkpoint of a scene with the same parameter groups."""
+    torch = _torch()
+    state = torch.load(path, map_location="cpu", weights_only=True)
+    if not isinstance(state, dict) or state.get("format") != CHECKPOINT_FORMAT:
+        raise ValueError(f"{path}: not a {CHECKPOINT_FORMAT} file")
+    groups = scene.param_groups()
+    if state["n_params"] != scene.n_params or len(state["groups"]) != len(groups) or \
+            any(tuple(a.shape) != tuple(b.shape) for a, b in zip(state["groups"], groups)):
+        raise ValueError(f"{path}: parameter groups differ from the scene's")
+    for dst, src in zip(groups, state["groups"]):
+        dst.copy_(src)
+    for dst, key in ((m, "m"), (v, "v")):
+        if dst is not None and state[key] is not None:
+            if dst.numel() != state[key].numel():
+                raise ValueError(f"{path}: {key} has {state[key].numel()} entries, the buffer {dst.numel()}")
+            dst.copy_(state[key].reshape(dst.shape))
+    if iter_state is not None:
+        it = state["iter"] - (1 << 32) if state["iter"] >= (1 << 31) else state["iter"]  # uint32 in an int32 word
+        iter_state.tensor.copy_(torch.tensor([it, state["t"]], dtype=torch.int32))
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+    return state["seed"], state["iter"], state["t"]
 
 
 def draw_views(seed: int, it: int, n_views: int, count: int) -> List[int]:

@@ -16,7 +16,8 @@ MAX_BATCH = 64
 MAX_BATCH_VIEWS = 8
 MAX_LAYERS = 4  # fragments per pixel of a transparent scene's deep ID buffer
 
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_BIN_OVERFLOW, ERR_BAD_INDEX, ERR_UNSUPPORTED, ERR_WORKSPACE = range(7)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_BIN_OVERFLOW, ERR_BAD_INDEX, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_BOUNDS = range(8)
+LIMIT_VERTICES, LIMIT_UVS, LIMIT_BIN_ENTRIES, LIMIT_SIGN_WORDS, LIMIT_PARAMS = range(5)
 STEP_SGD, STEP_ADAM, STEP_SGD_MEAN = 0, 1, 2
 FOOT_BILINEAR, FOOT_NEAREST = 0, 1
 SHADE_UNLIT, SHADE_LAMBERT, SHADE_GGX, SHADE_TRANSPARENT = 0, 1, 2, 3
@@ -27,7 +28,7 @@ EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_
            "sge_estimate_grad_batch", "sge_autotune_batch", "sge_kernel_timing", "sge_kernel_time",
            "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image",
            "sge_refine", "sge_render_deep", "sge_estimate_grad_state", "sge_step_state", "sge_iter_advance",
-           "sge_estimate_grad_batch_state", "sge_atomic_bench")
+           "sge_estimate_grad_batch_state", "sge_atomic_bench", "sge_checked_build", "sge_check_limit")
 
 
 class Texture(C.Structure):
@@ -76,12 +77,18 @@ class SGEError(RuntimeError):
         self.code = code
 
 
+def checked_requested() -> bool:
+    """SGE_CHECKED=1 in the environment selects the checked build (libsge_checked.so)."""
+    return os.environ.get("SGE_CHECKED", "0") == "1"
+
+
 def lib_path() -> str:
-    return _build.OUT
+    return _build.OUT_CHECKED if checked_requested() else _build.OUT
 
 
 def load(build_if_missing: bool = False):
-    """Load libsge.so (never falls back to anything else: raises if it is missing)."""
+    """Load libsge.so, or libsge_checked.so under SGE_CHECKED=1 (never falls back to anything else:
+    raises if it is missing)."""
     global _lib
     with _lock:
         if _lib is not None:
@@ -90,7 +97,7 @@ def load(build_if_missing: bool = False):
         if not os.path.exists(path):
             if not build_if_missing:
                 raise RuntimeError(f"{path} is missing: build it with paper_2404_09758_gb300.build.build()")
-            _build.build()
+            _build.build(checked=checked_requested())
         L = C.CDLL(path)
         P, I32, U32, U64, I64, SZ = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64, C.c_int64, C.c_size_t
         L.sge_workspace_size.argtypes = [P, P, C.POINTER(SZ)]
@@ -108,6 +115,8 @@ def load(build_if_missing: bool = False):
         L.sge_iter_advance.argtypes = [P, I32, I32, P]
         L.sge_estimate_grad_batch_state.argtypes = [P, I32, U64, P, I32, P, P]
         L.sge_atomic_bench.argtypes = [P, I64, I64, I32, P]
+        L.sge_checked_build.argtypes = []
+        L.sge_check_limit.argtypes = [P, I32, I64]
         L.sge_status.argtypes = [P, P, C.POINTER(I32)]
         L.sge_render_idb_static.argtypes = [P, I32, U64, U32, U32, I32, P, P, P, P, P]
         L.sge_loss.argtypes = [P, P, I32, P, P]

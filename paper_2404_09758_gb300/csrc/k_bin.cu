@@ -34,12 +34,12 @@ __global__ void k_bin_rect_count(SceneDev S, Workspace ws, ViewList vl) {
   __syncthreads();
   int tri = blockIdx.x * blockDim.x + threadIdx.x;
   if (tri >= S.nt) return;
-  int vi[3] = {__ldg(S.pidx + 3 * tri), __ldg(S.pidx + 3 * tri + 1), __ldg(S.pidx + 3 * tri + 2)};
+  int vi[3] = {vert_of(S, tri, 0), vert_of(S, tri, 1), vert_of(S, tri, 2)};
   int4 rect = make_int4(1, 1, 0, 0);  // empty
   bool skip = vi[0] == vi[1] || vi[1] == vi[2] || vi[0] == vi[2];  // welded duplicates: zero area always
   // a triangle with an index out of range is never binned, so no render reads through it
   for (int k = 0; k < 3; ++k) {
-    const int ti = __ldg(S.uvidx + 3 * tri + k);
+    const int ti = uv_of(S, tri, k);
     if (ti < 0 || ti >= S.nuv) skip = true;
   }
   float sx0 = 3.4e38f, sx1 = -3.4e38f, sy0 = 3.4e38f, sy1 = -3.4e38f;
@@ -183,7 +183,7 @@ __global__ void k_bin_fill(SceneDev S, Workspace ws) {
   for (int ty = rect.y; ty <= rect.w; ++ty)
     for (int tx = rect.x; tx <= rect.z; ++tx) {
       uint32_t pos = atomicAdd(ws.tile_cur + (long long)slot * nt + ty * S.tiles_x + tx, 1u);
-      if ((long long)pos < ws.bin_capacity) ws.bins[pos] = (uint32_t)tri;
+      if ((long long)pos < ws.bin_capacity && chk(S, pos, S.chk.bins)) ws.bins[pos] = (uint32_t)tri;
     }
 }
 

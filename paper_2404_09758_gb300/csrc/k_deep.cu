@@ -68,7 +68,7 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
     const int cnt = min(DCHUNK, nb - c0);
     __syncthreads();
     if ((int)threadIdx.x < cnt) {
-      const int tri = (int)ws.bins[beg + c0 + threadIdx.x];
+      const int tri = (int)bin_at(S, ws, beg + c0 + threadIdx.x);
       sm.tri[threadIdx.x] = tri;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
@@ -76,7 +76,7 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
           PVert v[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            const int4 q = __ldg(pv + 2 * __ldg(S.pidx + 3 * tri + k) + s);
+            const int4 q = __ldg(pv + 2 * vert_of(S, tri, k) + s);
             v[k].X = q.x;
             v[k].Y = q.y;
             v[k].z = __int_as_float(q.z);
@@ -131,7 +131,7 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
         PVert v[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const int4 q = __ldg(pv + 2 * __ldg(S.pidx + 3 * tri + k) + (side < 0 ? 1 : 0));
+          const int4 q = __ldg(pv + 2 * vert_of(S, tri, k) + (side < 0 ? 1 : 0));
           v[k].X = q.x;
           v[k].Y = q.y;
           v[k].z = __int_as_float(q.z);
@@ -149,7 +149,7 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     float l[3];
     lambdas(e, t.inv_area, l);
     PerspW pw = persp(l, t.iw);
-    const int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
+    const int t0 = uv_of(S, tri, 0), t1 = uv_of(S, tri, 1), t2 = uv_of(S, tri, 2);
     const float u = persp_interp(pw, __ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t2));
     const float v = persp_interp(pw, __ldg(S.uvs + 2 * t0 + 1), __ldg(S.uvs + 2 * t1 + 1), __ldg(S.uvs + 2 * t2 + 1));
     Foot f = footprint(u, v, A.w, A.h);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
   // the estimate's projected vertices and signs, from the vertex pass and the texel sign planes
   const int pb = pair - a.pair_begin;
   const int4* pv = ws.pverts + 2 * (((long long)slot * ws.max_pairs + pb) * S.nv);
-  const PairSigns ps = pair_signs(ws, slot, pb, S.nv);
+  const PairSigns ps = pair_signs(S, ws, slot, pb);
   const bool resident = deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy, pv);
   float lv = 0.0f;
   if (px < S.W && py < S.H) {
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     };
     auto credit_keys = [&](int tri, const Foot& f) {
 #pragma unroll
-      for (int v = 0; v < 3; ++v) add(vkey(__ldg(S.pidx + 3 * tri + v)));
+      for (int v = 0; v < 3; ++v) add(vkey(vert_of(S, tri, v)));
       if (S.foot_nearest) {
         add(tkey(A.index, f.nearest));
         return;
@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
     for (int q = 0; q < nk; ++q)
       for_each_signed_channel<false>(S, ps, ks[q], [&](long long p, int, bool neg) {
+        if (!chk(S, p, S.chk.params)) return;
         atomicAdd(a.grad + p, neg ? -df : df);
         atomicAdd(a.counts + p, 1u);
       });

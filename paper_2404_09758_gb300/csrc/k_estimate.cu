@@ -142,6 +142,7 @@ __device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT, TSC>& tb
     slot = (slot + 1) & (HT - 1);
   }
   for_each_signed_channel<GR>(S, ps, key, [&](long long p, int, bool neg) {
+    if (!chk(S, p, S.chk.params)) return;
     atomicAdd(grad + p, neg ? -df : df);
     atomicAdd(counts + p, 1u);
   });
@@ -171,6 +172,7 @@ __device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem<HT,
     if (key != EMPTY) {
       const uint32_t cn = tb.cnt[slot];
       for_each_channel<GR>(S, key, [&](long long p, int c) {
+        if (!chk(S, p, S.chk.params)) return;
         atomicAdd(grad + p, tb.S[c][slot]);
         if (cn) atomicAdd(counts + p, cn);
       });
@@ -191,7 +193,7 @@ __device__ __forceinline__ void setup_from_pverts(const SceneDev& S, const Works
   PVert v[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int4 q = __ldg(ws.pverts + 2 * (vb + __ldg(S.pidx + 3 * tri + k)) + sd);
+    const int4 q = __ldg(ws.pverts + 2 * (vb + vert_of(S, tri, k)) + sd);
     v[k].X = q.x;
     v[k].Y = q.y;
     v[k].z = __int_as_float(q.z);
@@ -276,7 +278,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
 
     for (int pair = p0; pair < p1; ++pair) {
       // the estimate's signs, from the vertex pass and the texel sign planes
-      const PairSigns ps = pair_signs(ws, slot, pair - a.pair_begin, S.nv);
+      const PairSigns ps = pair_signs(S, ws, slot, pair - a.pair_begin);
       const long long vb = ((long long)slot * ws.max_pairs + (pair - a.pair_begin)) * S.nv;
       unsigned long long best[2] = {~0ull, ~0ull};
       int bestj[2] = {-1, -1}, bestc[2] = {-1, -1};
@@ -285,7 +287,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
         const int cnt = min(BIN_CHUNK, nb - c0);
         __syncthreads();
         if (tid < cnt) {
-          const int tri = (int)ws.bins[bin_beg + c0 + tid];
+          const int tri = (int)bin_at(S, ws, bin_beg + c0 + tid);
 #pragma unroll
           for (int sd = 0; sd < 2; ++sd) {
             Tri t;

@@ -208,8 +208,10 @@ __device__ __forceinline__ int texel_of(uint32_t pk, int q, int w) {
 }
 
 // Sign bits of texel t's channels (bit c: s = -1) in one texture's sign plane of an estimate.
-__device__ __forceinline__ uint32_t plane_nibble(const uint32_t* plane, int t) {
-  return (__ldg(plane + (t >> 3)) >> (4 * (t & 7))) & 0xFu;
+__device__ __forceinline__ uint32_t plane_nibble(const SceneDev& S, const uint32_t* planes, int off, int t) {
+  const long long w = (long long)off + (t >> 3);
+  if (!chk(S, w, S.chk.sign_words)) return 0u;
+  return (__ldg(planes + w) >> (4 * (t & 7))) & 0xFu;
 }
 
 // Every slot of the table empty (once per call of the estimator loop in a CTA).
@@ -493,7 +495,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
   __syncthreads();
   auto stage = [&](int c0, int cnt, bool from_live) {
     if (tid < cnt) {
-      const int tri = (int)ws.bins[beg + c0 + tid];
+      const int tri = (int)bin_at(S, ws, beg + c0 + tid);
       sm.id[tid] = (uint32_t)tri;
       stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid], sm.reach[tid]);
       if (!from_live) sm.live[tid] = 0;
@@ -540,7 +542,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     const int pos = block_prefix(f, sm.wsum, &total);
     // positions only move towards the front, past entries this CTA has already read
     if (f) {
-      ws.bins[beg + n_live + pos] = sm.id[tid];
+      if (chk(S, (long long)beg + n_live + pos, S.chk.bins)) ws.bins[beg + n_live + pos] = sm.id[tid];
       if (single) sm.remap[tid] = (uint16_t)pos;
     }
     n_live += total;
@@ -638,13 +640,13 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     // ---- per item: the bin's live triangles (pruned and compacted by k_bin_prune), their
     //      smallest depths, and this pixel's candidates among them (in order of that depth)
     if (tid < nb) {
-      const int tri = (int)ws.bins[bin_beg + tid];
+      const int tri = (int)bin_at(S, ws, bin_beg + tid);
       sm.btri[tid] = tri;
       sm.zminb[tid] = ordered_bits(ws.tri_z[(long long)slot * S.nt + tri].x);
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        sm.vid[tid][k] = __ldg(S.pidx + 3 * tri + k);
-        const int ti = __ldg(S.uvidx + 3 * tri + k);
+        sm.vid[tid][k] = vert_of(S, tri, k);
+        const int ti = uv_of(S, tri, k);
         sm.uv[tid][2 * k] = __ldg(S.uvs + 2 * ti);
         sm.uv[tid][2 * k + 1] = __ldg(S.uvs + 2 * ti + 1);
         sm.A_cor[tid][k] = 0.0f;
@@ -832,6 +834,9 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
               const uint32_t s10 = (uint32_t)((y1 - sm.win[2]) * ww + ix - sm.win[0]);
               tslot[sd][r][0] = s00 | ((s00 + 1) << 16);
               tslot[sd][r][1] = s10 | ((s10 + 1) << 16);
+              // (checked build) both rows' slots inside the window: else credit globally
+              if (!chk(S, (long long)s00 + 1, sm.n_win) || !chk(S, (long long)s10 + 1, sm.n_win))
+                tslot[sd][r][0] = tslot[sd][r][1] = NOSLOT | (NOSLOT << 16);
             } else if (!Model<SH, GR>::HASH_OUTSIDE) {
               tslot[sd][r][0] = tslot[sd][r][1] = NOSLOT | (NOSLOT << 16);  // global credits
             } else {
@@ -859,7 +864,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
           for (int r = 0; r < NREAD; ++r) {
             const TexDev& T = S.rtex[r];
-            const uint32_t* plane = planes + ws.sgn_off[T.index];
+            const int poff = ws.sgn_off[T.index];
             const int fi = GR ? 0 : r;  // the footprint this texture uses
             const float fx = ffx[sd][fi], fy = ffy[sd][fi];
             const float wq[4] = {(1.0f - fx) * (1.0f - fy), fx * (1.0f - fy), (1.0f - fx) * fy, fx * fy};
@@ -868,7 +873,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int texel = texel_of(tpk[sd][fi], q, T.w);
-              const uint32_t sb_s = plane_nibble(plane, texel);
+              const uint32_t sb_s = plane_nibble(S, planes, poff, texel);
               if (GR) {
                 gsb[q] |= sb_s << (4 * r);
               } else if (!S.foot_nearest) {
@@ -969,9 +974,10 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
           for (int g = 0; g < (GR ? NREAD : 1); ++g) {
             const TexDev& U = S.rtex[GR ? g : r];
-            const uint32_t sb = plane_nibble(planes + ws.sgn_off[U.index], id);
+            const uint32_t sb = plane_nibble(S, planes, ws.sgn_off[U.index], id);
             const long long base = U.offset + (long long)id * U.c;
             for (int c = 0; c < U.c; ++c) {
+              if (!chk(S, base + c, S.chk.params)) continue;
               atomicAdd(a.grad + base + c, ((sb >> c) & 1) ? -df : df);
               atomicAdd(a.counts + base + c, 1u);
             }
@@ -1030,6 +1036,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
         const TexDev& T = S.tex[(key >> 28) - 1];
         const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
         for (int c = 0; c < T.c; ++c) {
+          if (!chk(S, base + c, S.chk.params)) continue;
           atomicAdd(a.grad + base + c, sm.tS[c][s]);
           atomicAdd(a.counts + base + c, sm.tcnt[s]);
         }
@@ -1040,6 +1047,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           const TexDev& T = S.rtex[r];
           const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
           for (int c = 0; c < T.c; ++c) {
+            if (!chk(S, base + c, S.chk.params)) continue;
             atomicAdd(a.grad + base + c, sm.tS[(4 * r + c) % TSC][s]);
             atomicAdd(a.counts + base + c, sm.tcnt[s]);
           }
@@ -1054,6 +1062,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
         const long long base = 3ll * sm.vid[tid][k];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
+          if (!chk(S, base + c, S.chk.params)) continue;
           atomicAdd(a.grad + base + c, sm.S_cor[tid][k][c]);
           atomicAdd(a.counts + base + c, cn);
         }

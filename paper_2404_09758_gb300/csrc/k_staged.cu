@@ -36,7 +36,7 @@ __device__ __forceinline__ void raster_tile(const SceneDev& S, const Workspace& 
     const int cnt = min(RCHUNK, nb - c0);
     __syncthreads();
     if ((int)threadIdx.x < cnt) {
-      const int tri = (int)ws.bins[beg + c0 + threadIdx.x];
+      const int tri = (int)bin_at(S, ws, beg + c0 + threadIdx.x);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         setup_from_scene(S, sm[0].m, tri, key, sides[s], rx, ry, sm[s].t[threadIdx.x]);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(TILE_PX) k_raster_pair(SceneDev S, Workspace w
       float l[3];
       lambdas(e, t.inv_area, l);
       PerspW pw = persp(l, t.iw);
-      int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
+      int t0 = uv_of(S, tri, 0), t1 = uv_of(S, tri, 1), t2 = uv_of(S, tri, 2);
       uvv.x = persp_interp(pw, __ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t2));
       uvv.y = persp_interp(pw, __ldg(S.uvs + 2 * t0 + 1), __ldg(S.uvs + 2 * t1 + 1), __ldg(S.uvs + 2 * t2 + 1));
     }
@@ -236,6 +236,7 @@ __global__ void k_scatter(SceneDev S, Workspace ws, uint64_t key, float* grad, u
     int nch;
     key_params(S, ck, base, nch);
     for (int c = 0; c < nch; ++c) {
+      if (!chk(S, base + c, S.chk.params)) continue;
       atomicAdd(grad + base + c, sign_neg(key, (uint64_t)(base + c)) ? -df : df);
       atomicAdd(counts + base + c, 1u);
     }

@@ -95,7 +95,7 @@ __global__ void k_texel_signs(SceneDev S, Workspace ws, ViewList vl, EstimateArg
       case 3: bits = sign_word<3>(pkey, first, n); break;
       default: bits = sign_word<4>(pkey, first, n); break;
     }
-    out[w] = bits;
+    if (chk(S, w, S.chk.sign_words)) out[w] = bits;
   }
 }
 

@@ -29,6 +29,7 @@ struct sge_scene {
   // back to the caller's stream with events (graph capture follows the fork)
   cudaStream_t side;
   cudaEvent_t fork, join;
+  CheckDev chk_true;  // the checked build's true bounds (sge_check_limit lowers dev.chk)
   int n_timed;                // pairs recorded since the last sge_kernel_time
 };
 
@@ -237,6 +238,10 @@ void make_dev(const sge_scene_desc* d, SceneDev& S) {
   S.ambient = d->ambient;
   S.tiles_x = tiles_of(d->width);
   S.tiles_y = tiles_of(d->height);
+  // the checked build's bounds: the true sizes (the workspace's own are set where it is carved)
+  S.chk.nv = d->n_vertices;
+  S.chk.nuv = d->n_uvs;
+  S.chk.params = S.n_params;
 }
 
 }  // namespace sge
@@ -328,6 +333,10 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   w.bin_capacity = L.bin_capacity;
   w.max_views = L.max_views;
   w.light_bin = kLightBin;
+  s->dev.chk.status = w.counters + 3;
+  s->dev.chk.bins = w.bin_capacity;
+  s->dev.chk.sign_words = w.sgn_words;
+  s->chk_true = s->dev.chk;
   s->desc_dev = reinterpret_cast<AssetDesc*>(base + L.desc);
   s->desc_dirty = true;
   s->n_tev = 0;
@@ -924,6 +933,35 @@ int sge_atomic_bench(float* buf, int64_t n_addr, int64_t n_threads, int32_t per_
     return fail(SGE_ERR_INVALID_ARG, "sge_atomic_bench: need buf, n_addr >= 1, 1 <= n_threads, per_thread >= 1");
   cudaError_t e = launch_red_bench(buf, n_addr, n_threads, per_thread, (cudaStream_t)stream);
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_atomic_bench");
+}
+
+int sge_checked_build(void) { return SGE_CHECKED ? 1 : 0; }
+
+int sge_check_limit(sge_scene* s, int32_t which, int64_t limit) {
+  if (!SGE_CHECKED) return fail(SGE_ERR_UNSUPPORTED, "sge_check_limit: not the checked build");
+  if (!s) return fail(SGE_ERR_INVALID_ARG, "scene is NULL");
+  CheckDev& c = s->dev.chk;
+  const CheckDev& t = s->chk_true;
+  long long top;
+  switch (which) {
+    case SGE_LIMIT_VERTICES: top = t.nv; break;
+    case SGE_LIMIT_UVS: top = t.nuv; break;
+    case SGE_LIMIT_BIN_ENTRIES: top = t.bins; break;
+    case SGE_LIMIT_SIGN_WORDS: top = t.sign_words; break;
+    case SGE_LIMIT_PARAMS: top = t.params; break;
+    default: return fail(SGE_ERR_INVALID_ARG, "sge_check_limit: bad range %d", which);
+  }
+  if (limit > top) return fail(SGE_ERR_INVALID_ARG, "sge_check_limit: %lld above the true size %lld", (long long)limit, top);
+  const long long v = limit < 0 ? top : limit;
+  switch (which) {
+    case SGE_LIMIT_VERTICES: c.nv = (int)v; break;
+    case SGE_LIMIT_UVS: c.nuv = (int)v; break;
+    case SGE_LIMIT_BIN_ENTRIES: c.bins = v; break;
+    case SGE_LIMIT_SIGN_WORDS: c.sign_words = v; break;
+    default: c.params = v; break;
+  }
+  s->desc_dirty = true;  // batched launches read the scene's device copy
+  return SGE_OK;
 }
 
 void sge_destroy_scene(sge_scene* s) {

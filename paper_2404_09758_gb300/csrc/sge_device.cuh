@@ -14,6 +14,39 @@
 
 namespace sge {
 
+// ---------------------------------------------------------------- range checks (checked build)
+// Is 0 <= i < n?  The unchecked build assumes so (the host validates what it can); the checked
+// build tests it and, when it fails, records SGE_ERR_BOUNDS in the status word so that the caller
+// skips the access.
+__device__ __forceinline__ bool chk(const SceneDev& S, long long i, long long n) {
+#if SGE_CHECKED
+  if (i >= 0 && i < n) return true;
+  atomicCAS(S.chk.status, 0u, (uint32_t)SGE_ERR_BOUNDS);
+  return false;
+#else
+  (void)S;
+  (void)i;
+  (void)n;
+  return true;
+#endif
+}
+
+// Vertex / UV index k of triangle tri (a failing check reads as index 0).
+__device__ __forceinline__ int vert_of(const SceneDev& S, int tri, int k) {
+  const int v = __ldg(S.pidx + 3 * tri + k);
+  return chk(S, v, S.chk.nv) ? v : 0;
+}
+__device__ __forceinline__ int uv_of(const SceneDev& S, int tri, int k) {
+  const int t = __ldg(S.uvidx + 3 * tri + k);
+  return chk(S, t, S.chk.nuv) ? t : 0;
+}
+
+// Bin entry i (a failing check reads as triangle 0).
+__device__ __forceinline__ uint32_t bin_at(const SceneDev& S, const Workspace& ws, long long i) {
+  return chk(S, i, S.chk.bins) ? ws.bins[i] : 0u;
+}
+
+
 // ---------------------------------------------------------------- sign hash (Algorithm 1)
 // The paper draws s_i with a hash function it does not name.  This uses
 // SplitMix64 (Steele, Lea & Flood 2014): mix64 is its output function; one
@@ -330,7 +363,7 @@ __device__ __forceinline__ void surface(const SceneDev& S, int view, int tri, co
   float l[3];
   lambdas(e, t.inv_area, l);
   PerspW pw = persp(l, t.iw);
-  int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
+  int t0 = uv_of(S, tri, 0), t1 = uv_of(S, tri, 1), t2 = uv_of(S, tri, 2);
   float2 uv[3] = {make_float2(__ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t0 + 1)),
                   make_float2(__ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t1 + 1)),
                   make_float2(__ldg(S.uvs + 2 * t2), __ldg(S.uvs + 2 * t2 + 1))};
@@ -351,7 +384,7 @@ __device__ __forceinline__ void surface(const SceneDev& S, int view, int tri, co
     out.rgb = f3(alb[0], alb[1], alb[2]);
     return;
   }
-  int v0 = __ldg(S.pidx + 3 * tri), v1 = __ldg(S.pidx + 3 * tri + 1), v2 = __ldg(S.pidx + 3 * tri + 2);
+  int v0 = vert_of(S, tri, 0), v1 = vert_of(S, tri, 1), v2 = vert_of(S, tri, 2);
   float3 p[3] = {perturbed_pos(S, v0, key, side), perturbed_pos(S, v1, key, side),
                  perturbed_pos(S, v2, key, side)};
   float b[3] = {pw.q[0] / pw.qs, pw.q[1] / pw.qs, pw.q[2] / pw.qs};
@@ -365,16 +398,27 @@ struct PairSigns {
   const uint32_t* planes;  // this estimate's texel sign planes
   const uint8_t* vbits;    // this estimate's vertex sign bits (bits 0-2: x, y, z have s = -1)
   const int* sgn_off;      // word offset of texture k's plane (Workspace::sgn_off)
+#if SGE_CHECKED
+  const SceneDev* S;       // range checks of the plane words
+#endif
 };
 
-__device__ __forceinline__ PairSigns pair_signs(const Workspace& ws, int slot, int pb, int nv) {
+__device__ __forceinline__ PairSigns pair_signs(const SceneDev& S, const Workspace& ws, int slot, int pb) {
   const long long e = (long long)slot * ws.max_pairs + pb;
-  return PairSigns{ws.tsign + e * ws.sgn_words, ws.vbits + e * nv, ws.sgn_off};
+#if SGE_CHECKED
+  return PairSigns{ws.tsign + e * ws.sgn_words, ws.vbits + e * S.nv, ws.sgn_off, &S};
+#else
+  return PairSigns{ws.tsign + e * ws.sgn_words, ws.vbits + e * S.nv, ws.sgn_off};
+#endif
 }
 
 // Sign bits of texel t of texture k (bit c: channel c has s = -1).
 __device__ __forceinline__ uint32_t texel_signs(const PairSigns& ps, int k, long long t) {
-  return (__ldg(ps.planes + ps.sgn_off[k] + (t >> 3)) >> (4 * (t & 7))) & 0xFu;
+  const long long w = ps.sgn_off[k] + (t >> 3);
+#if SGE_CHECKED
+  if (ps.S && !chk(*ps.S, w, ps.S->chk.sign_words)) return 0u;
+#endif
+  return (__ldg(ps.planes + w) >> (4 * (t & 7))) & 0xFu;
 }
 
 // Sign bits of welded vertex v (bit c: coordinate c has s = -1).
@@ -407,7 +451,7 @@ __device__ __forceinline__ void surface_ps(const SceneDev& S, int view, int tri,
   float l[3];
   lambdas(e, t.inv_area, l);
   PerspW pw = persp(l, t.iw);
-  int t0 = __ldg(S.uvidx + 3 * tri), t1 = __ldg(S.uvidx + 3 * tri + 1), t2 = __ldg(S.uvidx + 3 * tri + 2);
+  int t0 = uv_of(S, tri, 0), t1 = uv_of(S, tri, 1), t2 = uv_of(S, tri, 2);
   float2 uv[3] = {make_float2(__ldg(S.uvs + 2 * t0), __ldg(S.uvs + 2 * t0 + 1)),
                   make_float2(__ldg(S.uvs + 2 * t1), __ldg(S.uvs + 2 * t1 + 1)),
                   make_float2(__ldg(S.uvs + 2 * t2), __ldg(S.uvs + 2 * t2 + 1))};
@@ -431,7 +475,7 @@ __device__ __forceinline__ void surface_ps(const SceneDev& S, int view, int tri,
   float3 p[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int vi = __ldg(S.pidx + 3 * tri + k);
+    const int vi = vert_of(S, tri, k);
     uint32_t sb = vertex_signs(ps, vi);
     if (side < 0) sb = ~sb;
     const float* src = S.pos + 3ll * vi;
@@ -449,7 +493,7 @@ __device__ __forceinline__ void setup_from_scene(const SceneDev& S, const float*
   PVert v[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    int vi = __ldg(S.pidx + 3 * tri + k);
+    int vi = vert_of(S, tri, k);
     float3 q = perturbed_pos(S, vi, key, side);
     v[k] = project(m, q.x, q.y, q.z, S.W, S.H, S.near_w);
   }
@@ -550,7 +594,7 @@ __device__ __forceinline__ void for_each_contrib(const SceneDev& S, const int tr
   for (int sd = 0; sd < 2; ++sd) {
     if (tris[sd] < 0) continue;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) vid[sd][k] = __ldg(S.pidx + 3 * tris[sd] + k);
+    for (int k = 0; k < 3; ++k) vid[sd][k] = vert_of(S, tris[sd], k);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       bool dup = false;

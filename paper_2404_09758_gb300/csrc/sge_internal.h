@@ -32,6 +32,20 @@ struct TexDev {
   int index;         // position of this texture in the scene's list
 };
 
+#ifndef SGE_CHECKED
+#define SGE_CHECKED 0
+#endif
+
+// Bounds of the checked build's range checks (SGE_CHECKED=1): the true sizes unless
+// sge_check_limit lowered them.  Unused by the unchecked build.
+struct CheckDev {
+  uint32_t* status;    // the device status word a failing check writes
+  int nv, nuv;         // vertex and UV indices
+  long long bins;      // bin entries
+  long long sign_words;  // words of one estimate's sign planes
+  long long params;    // parameter indices
+};
+
 // Device view of a scene, passed to kernels by value.
 struct SceneDev {
   const float* pos;
@@ -60,6 +74,7 @@ struct SceneDev {
   long long n_params;
   int tiles_x, tiles_y;
   int foot_nearest;  // credit the nearest texel instead of the bilinear 2x2 footprint (SGE_FOOT_NEAREST)
+  CheckDev chk;
 };
 
 // Views of one estimate call, by value (graph capture bakes them in).
