@@ -102,8 +102,7 @@ struct FastSmem {
   float S_cor[NB][3][3];
   uint32_t c_cor[NB][3];
   uint32_t tkey[TABLE];
-  float tA[TABLE];
-  uint32_t tn[TABLE];
+  float tA[TABLE];       // the current pair's sum of f+ - f- over the pixels crediting the entry
   float tS[TSC][TABLE];
   uint32_t tcnt[TABLE];
   uint32_t tsb[TABLE];   // the current pair's sign bits of the entry's channels (4 r + c), stored by
@@ -220,7 +219,6 @@ __device__ __forceinline__ void clear_table(FastSmem<TABLE, TSC>& sm) {
   for (int s = threadIdx.x; s < TABLE; s += blockDim.x) {
     sm.tkey[s] = EMPTY;
     sm.tA[s] = 0.0f;
-    sm.tn[s] = 0u;
     sm.tcnt[s] = 0u;
     sm.tsb[s] = 0u;
 #pragma unroll
@@ -236,7 +234,6 @@ __device__ __forceinline__ void clear_used(FastSmem<TABLE, TSC>& sm, uint32_t n_
     const uint32_t s = sm.used[i];
     sm.tkey[s] = EMPTY;
     sm.tA[s] = 0.0f;
-    sm.tn[s] = 0u;
     sm.tcnt[s] = 0u;
 #pragma unroll
     for (int c = 0; c < TSC; ++c) sm.tS[c][s] = 0.0f;
@@ -245,6 +242,8 @@ __device__ __forceinline__ void clear_used(FastSmem<TABLE, TSC>& sm, uint32_t n_
 
 // Fold a pair's credits (table entries and triangle corners) into the per-channel sums with
 // that pair's signs: texel signs in tsb (stored while sampling), vertex signs in sgn9[parity].
+// A table entry's counts go straight to tcnt when it is credited; an entry whose pair sum is
+// exactly zero is skipped (adding +-0 leaves every sum as it is).
 template <int TABLE, int TSC, bool GR, int NREAD>
 __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE, TSC>& sm, int nb, int parity) {
   // the item's keys only (the used list, whose first n_win entries are the window's slots 0, 1, ...
@@ -252,9 +251,8 @@ __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE, TSC>& sm
   const uint32_t n_used = sm.n_used, n_win = sm.n_win;
   for (uint32_t i = threadIdx.x; i < n_used; i += blockDim.x) {
     const uint32_t s = i < n_win ? i : sm.used[i];
-    const uint32_t nn = sm.tn[s];
-    if (!nn) continue;
     const float A = sm.tA[s];
+    if (A == 0.0f) continue;
     const uint32_t sbits = sm.tsb[s];
     if (!GR) {
       const int cn = NREAD == 1 ? S.rtex[0].c : S.tex[(sm.tkey[s] >> 28) - 1].c;
@@ -271,9 +269,7 @@ __device__ __forceinline__ void fold(const SceneDev& S, FastSmem<TABLE, TSC>& sm
           if (c < cn) sm.tS[4 * r + c][s] += ((sbits >> (4 * r + c)) & 1) ? -A : A;
       }
     }
-    sm.tcnt[s] += nn;
     sm.tA[s] = 0.0f;
-    sm.tn[s] = 0u;
   }
   const int j = threadIdx.x;
   if (j < nb) {
@@ -316,6 +312,29 @@ __device__ __forceinline__ bool run_sum(int k, float& v, int& n) {
 }
 
 // ---------------------------------------------------------------- bin pruning
+// The tile's columns (bits 0-15) and rows (bits 16-31) whose pixel centres lie in the bounding
+// box of the projected vertices v grown by `grow` fixed-point units per axis (rx, ry: the tile's
+// first pixel centre).  Every perturbed version of a triangle lies in its box grown by the margin
+// (each snapped vertex moves at most that far per axis), and a pixel inside the triangle in its
+// box: a pre-filter for maybe_visible and surely_covers, which decide inside it.
+__device__ __forceinline__ uint32_t box_span(const PVert (&v)[3], long long rx, long long ry, long long grow) {
+  const long long xl = (long long)min(v[0].X, min(v[1].X, v[2].X)) - rx - grow;
+  const long long xh = (long long)max(v[0].X, max(v[1].X, v[2].X)) - rx + grow;
+  const long long yl = (long long)min(v[0].Y, min(v[1].Y, v[2].Y)) - ry - grow;
+  const long long yh = (long long)max(v[0].Y, max(v[1].Y, v[2].Y)) - ry + grow;
+  // pixel (dx, dy) sits at (256 dx, 256 dy): columns ceil(xl / 256) .. floor(xh / 256)
+  const long long x0 = -((-xl) >> 8), x1 = xh >> 8, y0 = -((-yl) >> 8), y1 = yh >> 8;
+  if (x0 > 15 || x1 < 0 || y0 > 15 || y1 < 0 || x0 > x1 || y0 > y1) return 0u;
+  const int xa = (int)max(x0, 0ll), xb = (int)min(x1, 15ll), ya = (int)max(y0, 0ll), yb = (int)min(y1, 15ll);
+  const uint32_t xm = ((2u << xb) - 1u) & ~((1u << xa) - 1u);
+  const uint32_t ym = ((2u << yb) - 1u) & ~((1u << ya) - 1u);
+  return xm | (ym << 16);
+}
+
+__device__ __forceinline__ bool in_span(uint32_t span, int dx, int dy) {
+  return ((span >> dx) & (span >> (16 + dy)) & 1u) != 0;
+}
+
 // Unperturbed set-up of a bin triangle with its perturbation margin and depth interval; a
 // triangle not drawable unperturbed (zero area, a vertex behind the near limit) gets tri = -2:
 // a perturbed version may still be drawable, so it is a candidate everywhere.  reach[k]: how far
@@ -323,9 +342,15 @@ __device__ __forceinline__ bool run_sum(int k, float& v, int& n) {
 // each vertex moves at most margin per axis, so at most sqrt(2) margin (+ slack); -1: never sure.
 __device__ __forceinline__ void stage_unperturbed(const SceneDev& S, const Workspace& ws, const float* m, int slot,
                                                   int tri, long long rx, long long ry, TriS& d, float2& zr,
-                                                  long long (&reach)[3]) {
+                                                  long long (&reach)[3], uint32_t (&span)[2]) {
+  PVert v[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float3 q = perturbed_pos(S, vert_of(S, tri, k), 0, 0);
+    v[k] = project(m, q.x, q.y, q.z, S.W, S.H, S.near_w);
+  }
   Tri t;
-  setup_from_scene(S, m, tri, 0, 0, rx, ry, t);
+  setup_tri(v[0], v[1], v[2], rx, ry, t);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     d.e0[k] = t.e0[k];
@@ -344,6 +369,15 @@ __device__ __forceinline__ void stage_unperturbed(const SceneDev& S, const Works
       r = (long long)ceilf(1.41422f * (float)d.margin * sqrtf(fa * fa + fb * fb) * 1.0001f + 2.0f);
     }
     reach[k] = r;
+  }
+  // pixels that may pass surely_covers (inside the triangle) and maybe_visible (inside its edges
+  // pushed out by the margin terms); a triangle those tests always fail / pass: none / all
+  if (can) {
+    span[0] = box_span(v, rx, ry, 0);
+    span[1] = box_span(v, rx, ry, d.margin);
+  } else {
+    span[0] = 0u;
+    span[1] = 0xFFFFFFFFu;
   }
   // over the tile (offsets 0..15 * 256) |e| < 2^30 and the margin terms stay below 2^28
   bool small = can && d.margin < (1 << 10);
@@ -406,6 +440,7 @@ struct PruneSmem {
   uint8_t live[NB];
   uint16_t remap[NB];  // compacted position of each live entry of a single-chunk bin
   uint16_t cl[kHeavyCand][TILE_PX];  // each pixel's first kHeavyCand candidates (column per pixel)
+  uint32_t span[NB][2];  // tile_span of the sure-cover and the maybe-visible regions
   float m[16];
   int wsum[TILE_PX / 32];
 };
@@ -497,7 +532,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     if (tid < cnt) {
       const int tri = (int)bin_at(S, ws, beg + c0 + tid);
       sm.id[tid] = (uint32_t)tri;
-      stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid], sm.reach[tid]);
+      stage_unperturbed(S, ws, sm.m, slot, tri, rx, ry, sm.t[tid], sm.zr[tid], sm.reach[tid], sm.span[tid]);
       if (!from_live) sm.live[tid] = 0;
     }
   };
@@ -509,7 +544,8 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     stage(c0, cnt, false);
     __syncthreads();
     for (int j = 0; j < cnt; ++j)
-      if (surely_covers(sm.t[j], sm.reach[j], dx, dy)) zsure = fminf(zsure, sm.zr[j].y);
+      if (in_span(sm.span[j][0], dx, dy) && surely_covers(sm.t[j], sm.reach[j], dx, dy))
+        zsure = fminf(zsure, sm.zr[j].y);
   }
   // pass 2: mark and compact the triangles some pixel may see (a single chunk is still staged;
   // its pixels' candidate lists are found on the way, by bin position, and renumbered below)
@@ -526,14 +562,15 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     if (valid) {
       if (single) {
         for (int j = 0; j < cnt; ++j)
-          if (maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
+          if (in_span(sm.span[j][1], dx, dy) && maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
             sm.live[j] = 1;
             if (n_cl < kHeavyCand) sm.cl[n_cl][tid] = (uint16_t)j;
             ++n_cl;
           }
       } else {
         for (int j = 0; j < cnt; ++j)
-          if (!sm.live[j] && maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) sm.live[j] = 1;
+          if (!sm.live[j] && in_span(sm.span[j][1], dx, dy) && maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy))
+            sm.live[j] = 1;
       }
     }
     __syncthreads();
@@ -574,7 +611,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     __syncthreads();
     if (valid)
       for (int j = 0; j < cnt; ++j)
-        if (maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
+        if (in_span(sm.span[j][1], dx, dy) && maybe_visible(sm.t[j], sm.zr[j], zsure, dx, dy)) {
           if (n_cl < kHeavyCand) sm.cl[n_cl][tid] = (uint16_t)(c0 + j);
           ++n_cl;
         }
@@ -968,7 +1005,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
         auto credit_texel = [&](int r, int id, uint32_t sl) {
           if (sl != NOSLOT) {
             atomicAdd(&sm.tA[sl], df);
-            atomicAdd(&sm.tn[sl], 1u);
+            atomicAdd(&sm.tcnt[sl], 1u);
             return;
           }
 #pragma unroll
@@ -1008,10 +1045,10 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int id = sd == 0 ? id0[q] : texel_of(tpk[1][r], q, T.w);
-              bool dup = false;
-              // the footprint's own repeats (clamped rows, a one-texel-wide texture)
-#pragma unroll
-              for (int o = 0; o < q; ++o) dup = dup || (sd == 0 ? id0[o] : texel_of(tpk[1][r], o, T.w)) == id;
+              // the footprint's own repeats: its second row when the rows are clamped to one, its
+              // second column in a one-texel-wide texture (texel_of gives every other corner a
+              // different texel)
+              bool dup = ((q & 2) && (tpk[sd][r] >> 31)) || ((q & 1) && T.w == 1);
               if (sd == 1) {
 #pragma unroll
                 for (int o = 0; o < 4; ++o) dup = dup || id0[o] == id;
