@@ -924,7 +924,8 @@ def run_converge(args):
     n_iter = 0
     next_sample = 1.0
     while True:
-        graph.replay()
+        with torch.cuda.stream(st):  # the loss below runs on st too: one stream orders both
+            graph.replay()
         st.synchronize()  # no backlog: the clock reads finished work
         n_iter += 1
         el = time.perf_counter() - t0

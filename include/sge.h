@@ -27,7 +27,10 @@
  *    thread-local message for the last failing call of the calling thread.
  *  - Parameter vector theta (Table 1): all vertex coordinates first (vertex-major
  *    x,y,z), then each texture in order, row-major (y, x, channel).
- *  - A scene is not thread-safe: calls on one scene must be serialised by the caller.
+ *  - A scene is not thread-safe: calls on one scene must be serialised by the caller,
+ *    across streams too.  Every call on a scene uses its one workspace (bins, work lists,
+ *    counters), so work enqueued on two streams (or a replayed CUDA graph and an eager call on
+ *    another stream) must be ordered by the caller with events or a synchronisation.
  */
 #ifndef SGE_H
 #define SGE_H
@@ -403,6 +406,13 @@ enum {
  * see the checks fire without any access leaving its buffer.  SGE_ERR_INVALID_ARG for a bad
  * `which` or a limit above the true size. */
 int sge_check_limit(sge_scene *scene, int32_t which, int64_t limit);
+
+/* Checked build only (else SGE_ERR_UNSUPPORTED): synchronise `stream`, then give the site of the
+ * first range check that failed since the last call (0: none; otherwise the source file's id
+ * times 100000 plus the line: 1 k_bin.cu, 2 k_deep.cu, 3 k_estimate.cu, 4 k_fast.cu,
+ * 5 k_staged.cu, 6 k_vertex.cu, 9 sge_device.cuh) and the low 32 bits of its index, and clear
+ * both.  site, index: host. */
+int sge_check_report(sge_scene *scene, sge_stream_t stream, int32_t *site, int64_t *index);
 
 /* Timing of the estimator kernels, for benchmarks (the paper has no counterpart).
  * While enabled, each sge_estimate_grad call records CUDA events on its stream right

@@ -192,6 +192,13 @@ class Scene:
         against (limit < 0: back to the true size); no allocation or logic changes."""
         _abi.check(_abi.load().sge_check_limit(self._h, which, limit))
 
+    def check_report(self, stream=None):
+        """Checked build only: (site, index) of the first range check that failed since the last
+        report (site 0: none), cleared by reading."""
+        site, index = C.c_int32(), C.c_int64()
+        _abi.check(_abi.load().sge_check_report(self._h, _stream_ptr(stream), C.byref(site), C.byref(index)))
+        return int(site.value), int(index.value)
+
     def status(self, stream=None) -> int:
         v = C.c_int32()
         _abi.check(_abi.load().sge_status(self._h, _stream_ptr(stream), C.byref(v)))

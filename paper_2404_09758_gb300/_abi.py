@@ -28,7 +28,8 @@ EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_
            "sge_estimate_grad_batch", "sge_autotune_batch", "sge_kernel_timing", "sge_kernel_time",
            "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image",
            "sge_refine", "sge_render_deep", "sge_estimate_grad_state", "sge_step_state", "sge_iter_advance",
-           "sge_estimate_grad_batch_state", "sge_atomic_bench", "sge_checked_build", "sge_check_limit")
+           "sge_estimate_grad_batch_state", "sge_atomic_bench", "sge_checked_build", "sge_check_limit",
+           "sge_check_report")
 
 
 class Texture(C.Structure):
@@ -117,6 +118,7 @@ def load(build_if_missing: bool = False):
         L.sge_atomic_bench.argtypes = [P, I64, I64, I32, P]
         L.sge_checked_build.argtypes = []
         L.sge_check_limit.argtypes = [P, I32, I64]
+        L.sge_check_report.argtypes = [P, P, C.POINTER(I32), C.POINTER(I64)]
         L.sge_status.argtypes = [P, P, C.POINTER(I32)]
         L.sge_render_idb_static.argtypes = [P, I32, U64, U32, U32, I32, P, P, P, P, P]
         L.sge_loss.argtypes = [P, P, I32, P, P]

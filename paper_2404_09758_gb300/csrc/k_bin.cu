@@ -9,6 +9,7 @@
 // tile's bin, with the exact perturbed vertices.
 #include <cuda_runtime.h>
 
+#define SGE_FILE_ID 1  // range-check sites of this file (checked build)
 #include "sge_device.cuh"
 
 namespace sge {
@@ -183,7 +184,7 @@ __global__ void k_bin_fill(SceneDev S, Workspace ws) {
   for (int ty = rect.y; ty <= rect.w; ++ty)
     for (int tx = rect.x; tx <= rect.z; ++tx) {
       uint32_t pos = atomicAdd(ws.tile_cur + (long long)slot * nt + ty * S.tiles_x + tx, 1u);
-      if ((long long)pos < ws.bin_capacity && chk(S, pos, S.chk.bins)) ws.bins[pos] = (uint32_t)tri;
+      if ((long long)pos < ws.bin_capacity && CHK(S, pos, S.chk.bins)) ws.bins[pos] = (uint32_t)tri;
     }
 }
 

@@ -11,6 +11,7 @@
 // come from the conservative binning without pruning: a fragment behind another is still listed.
 #include <cuda_runtime.h>
 
+#define SGE_FILE_ID 2  // range-check sites of this file (checked build)
 #include "sge_device.cuh"
 
 namespace sge {
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
     for (int q = 0; q < nk; ++q)
       for_each_signed_channel<false>(S, ps, ks[q], [&](long long p, int, bool neg) {
-        if (!chk(S, p, S.chk.params)) return;
+        if (!CHK(S, p, S.chk.params)) return;
         atomicAdd(a.grad + p, neg ? -df : df);
         atomicAdd(a.counts + p, 1u);
       });

@@ -21,6 +21,7 @@
 // falls back to direct global atomics for the keys that do not fit.
 #include <cuda_runtime.h>
 
+#define SGE_FILE_ID 3  // range-check sites of this file (checked build)
 #include "sge_device.cuh"
 
 namespace sge {
@@ -142,7 +143,7 @@ __device__ __forceinline__ void credit(const SceneDev& S, TableSmem<HT, TSC>& tb
     slot = (slot + 1) & (HT - 1);
   }
   for_each_signed_channel<GR>(S, ps, key, [&](long long p, int, bool neg) {
-    if (!chk(S, p, S.chk.params)) return;
+    if (!CHK(S, p, S.chk.params)) return;
     atomicAdd(grad + p, neg ? -df : df);
     atomicAdd(counts + p, 1u);
   });
@@ -172,7 +173,7 @@ __device__ __forceinline__ void flush_and_clear(const SceneDev& S, TableSmem<HT,
     if (key != EMPTY) {
       const uint32_t cn = tb.cnt[slot];
       for_each_channel<GR>(S, key, [&](long long p, int c) {
-        if (!chk(S, p, S.chk.params)) return;
+        if (!CHK(S, p, S.chk.params)) return;
         atomicAdd(grad + p, tb.S[c][slot]);
         if (cn) atomicAdd(counts + p, cn);
       });
@@ -244,6 +245,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
     const uint32_t it = ws.items[n_all - 1 - (int)(w / n_chunks)];
     const int chunk = (int)(w % n_chunks);
     const int slot = it >> 24, tile = it & 0xFFFFFF;
+    if (!CHK(S, slot, vl.n) || !CHK(S, tile, ntl)) continue;  // (checked build; uniform over the CTA)
     const int view = vl.id[slot];
     const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
     const int px = tx * TILE + dx, py = ty * TILE + dy;
@@ -314,6 +316,7 @@ __device__ __forceinline__ void heavy_items(const SceneDev& S, const Workspace& 
             for (; q < ncand; ++q) {
               const int j = (int)((cand[q >> 1] >> (16 * (q & 1))) & 0xFFFFu) - c0;
               if (j >= cnt) break;
+              if (!CHK(S, j, cnt)) continue;
               test(j);
             }
           }

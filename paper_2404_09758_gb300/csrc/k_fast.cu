@@ -30,6 +30,7 @@
 // atomic per channel for its sum and its count.
 #include <cuda_runtime.h>
 
+#define SGE_FILE_ID 4  // range-check sites of this file (checked build)
 #include "sge_device.cuh"
 
 namespace sge {
@@ -209,7 +210,7 @@ __device__ __forceinline__ int texel_of(uint32_t pk, int q, int w) {
 // Sign bits of texel t's channels (bit c: s = -1) in one texture's sign plane of an estimate.
 __device__ __forceinline__ uint32_t plane_nibble(const SceneDev& S, const uint32_t* planes, int off, int t) {
   const long long w = (long long)off + (t >> 3);
-  if (!chk(S, w, S.chk.sign_words)) return 0u;
+  if (!CHK(S, w, S.chk.sign_words)) return 0u;
   return (__ldg(planes + w) >> (4 * (t & 7))) & 0xFu;
 }
 
@@ -486,15 +487,17 @@ __device__ __forceinline__ void store_cands(const Workspace& ws, long long tile_
     }
   } else {
     // each entry goes to its rank in depth order: the estimator stops at the first candidate
-    // that lies wholly behind the nearest covering triangle found so far
+    // that lies wholly behind the nearest covering triangle found so far.  The order compares
+    // the depths' ordered bits (a total order, NaN included: a float compare would give two
+    // entries one rank) with ties broken by list position, so the ranks are a permutation.
     const int k = min(n, CMAX);
     uint32_t b[CMAX / 4] = {};
     for (int q = 0; q < k; ++q) {
       const uint32_t j = cl[q][tid];
-      const float zj = zr(j);
+      const uint32_t zj = ordered_bits(zr(j));
       int rank = 0;
       for (int r = 0; r < k; ++r) {
-        const float zo = zr((uint32_t)cl[r][tid]);
+        const uint32_t zo = ordered_bits(zr((uint32_t)cl[r][tid]));
         rank += (zo < zj || (zo == zj && r < q)) ? 1 : 0;
       }
       const uint32_t bits = j << (8 * (rank & 3));
@@ -579,7 +582,7 @@ __device__ __forceinline__ void prune_tile(const SceneDev& S, const Workspace& w
     const int pos = block_prefix(f, sm.wsum, &total);
     // positions only move towards the front, past entries this CTA has already read
     if (f) {
-      if (chk(S, (long long)beg + n_live + pos, S.chk.bins)) ws.bins[beg + n_live + pos] = sm.id[tid];
+      if (CHK(S, (long long)beg + n_live + pos, S.chk.bins)) ws.bins[beg + n_live + pos] = sm.id[tid];
       if (single) sm.remap[tid] = (uint16_t)pos;
     }
     n_live += total;
@@ -663,6 +666,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
     const uint32_t it = ws.items[w / n_chunks];
     const int chunk = (int)(w % n_chunks);
     const int slot = it >> 24, tile = it & 0xFFFFFF;
+    if (!CHK(S, slot, vl.n) || !CHK(S, tile, ntl)) continue;  // (checked build; uniform over the CTA)
     const int view = vl.id[slot];
     const int tx = tile % S.tiles_x, ty = tile / S.tiles_x;
     const int px = tx * TILE + dx, py = ty * TILE + dy;
@@ -773,6 +777,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
             for (int q = 0; q < ncand; ++q) {
               const uint32_t word = q < 4 ? cand[0] : (q < 8 ? cand[1] : (q < 12 ? cand[2] : cand[3]));
               const int j = (int)((word >> (8 * (q & 3))) & 0xFFu);
+              if (!CHK(S, j, nb)) continue;
               const uint32_t zb = sm.zminb[j];
               if (zb > (uint32_t)(best[0] >> 32) && zb > (uint32_t)(best[1] >> 32)) break;
               test(j);
@@ -872,7 +877,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
               tslot[sd][r][0] = s00 | ((s00 + 1) << 16);
               tslot[sd][r][1] = s10 | ((s10 + 1) << 16);
               // (checked build) both rows' slots inside the window: else credit globally
-              if (!chk(S, (long long)s00 + 1, sm.n_win) || !chk(S, (long long)s10 + 1, sm.n_win))
+              if (!CHK(S, (long long)s00 + 1, sm.n_win) || !CHK(S, (long long)s10 + 1, sm.n_win))
                 tslot[sd][r][0] = tslot[sd][r][1] = NOSLOT | (NOSLOT << 16);
             } else if (!Model<SH, GR>::HASH_OUTSIDE) {
               tslot[sd][r][0] = tslot[sd][r][1] = NOSLOT | (NOSLOT << 16);  // global credits
@@ -910,12 +915,13 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int texel = texel_of(tpk[sd][fi], q, T.w);
+              if (!CHK(S, texel, (long long)T.w * T.h)) continue;
               const uint32_t sb_s = plane_nibble(S, planes, poff, texel);
               if (GR) {
                 gsb[q] |= sb_s << (4 * r);
               } else if (!S.foot_nearest) {
                 const uint32_t sl = (tslot[sd][r][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-                if (sl != NOSLOT) sm.tsb[sl] = sb_s;
+                if (sl != NOSLOT && CHK(S, sl, TABLE)) sm.tsb[sl] = sb_s;
               } else if (texel == (int)tslot[sd][r][1] && (tslot[sd][r][0] & 0xFFFFu) != NOSLOT) {
                 sm.tsb[tslot[sd][r][0] & 0xFFFFu] = sb_s;
               }
@@ -935,7 +941,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
               if (!S.foot_nearest) sl = (tslot[sd][0][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
               else sl = texel_of(tpk[sd][0], q, S.rtex[0].w) == (int)tslot[sd][0][1] ? (tslot[sd][0][0] & 0xFFFFu)
                                                                                      : NOSLOT;
-              if (sl != NOSLOT) sm.tsb[sl] = gsb[q];
+              if (sl != NOSLOT && CHK(S, sl, TABLE)) sm.tsb[sl] = gsb[q];
             }
           }
           if (SH == SHADE_UNLIT) {
@@ -1004,6 +1010,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
         // credit texel id (table slot sl, or NOSLOT: straight to the global sums)
         auto credit_texel = [&](int r, int id, uint32_t sl) {
           if (sl != NOSLOT) {
+            if (!CHK(S, sl, TABLE)) return;
             atomicAdd(&sm.tA[sl], df);
             atomicAdd(&sm.tcnt[sl], 1u);
             return;
@@ -1014,7 +1021,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
             const uint32_t sb = plane_nibble(S, planes, ws.sgn_off[U.index], id);
             const long long base = U.offset + (long long)id * U.c;
             for (int c = 0; c < U.c; ++c) {
-              if (!chk(S, base + c, S.chk.params)) continue;
+              if (!CHK(S, base + c, S.chk.params)) continue;
               atomicAdd(a.grad + base + c, ((sb >> c) & 1) ? -df : df);
               atomicAdd(a.counts + base + c, 1u);
             }
@@ -1073,7 +1080,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
         const TexDev& T = S.tex[(key >> 28) - 1];
         const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
         for (int c = 0; c < T.c; ++c) {
-          if (!chk(S, base + c, S.chk.params)) continue;
+          if (!CHK(S, base + c, S.chk.params)) continue;
           atomicAdd(a.grad + base + c, sm.tS[c][s]);
           atomicAdd(a.counts + base + c, sm.tcnt[s]);
         }
@@ -1084,7 +1091,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
           const TexDev& T = S.rtex[r];
           const long long base = T.offset + (long long)(key & 0x0FFFFFFFu) * T.c;
           for (int c = 0; c < T.c; ++c) {
-            if (!chk(S, base + c, S.chk.params)) continue;
+            if (!CHK(S, base + c, S.chk.params)) continue;
             atomicAdd(a.grad + base + c, sm.tS[(4 * r + c) % TSC][s]);
             atomicAdd(a.counts + base + c, sm.tcnt[s]);
           }
@@ -1099,7 +1106,7 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
         const long long base = 3ll * sm.vid[tid][k];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          if (!chk(S, base + c, S.chk.params)) continue;
+          if (!CHK(S, base + c, S.chk.params)) continue;
           atomicAdd(a.grad + base + c, sm.S_cor[tid][k][c]);
           atomicAdd(a.counts + base + c, cn);
         }

@@ -4,6 +4,7 @@
 // contributing parameter).
 #include <cuda_runtime.h>
 
+#define SGE_FILE_ID 5  // range-check sites of this file (checked build)
 #include "sge_device.cuh"
 
 namespace sge {
@@ -236,7 +237,7 @@ __global__ void k_scatter(SceneDev S, Workspace ws, uint64_t key, float* grad, u
     int nch;
     key_params(S, ck, base, nch);
     for (int c = 0; c < nch; ++c) {
-      if (!chk(S, base + c, S.chk.params)) continue;
+      if (!CHK(S, base + c, S.chk.params)) continue;
       atomicAdd(grad + base + c, sign_neg(key, (uint64_t)(base + c)) ? -df : df);
       atomicAdd(counts + base + c, 1u);
     }

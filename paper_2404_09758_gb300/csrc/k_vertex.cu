@@ -6,6 +6,7 @@
 // for every tile a vertex's triangles touch.
 #include <cuda_runtime.h>
 
+#define SGE_FILE_ID 6  // range-check sites of this file (checked build)
 #include "sge_device.cuh"
 
 namespace sge {
@@ -95,7 +96,7 @@ __global__ void k_texel_signs(SceneDev S, Workspace ws, ViewList vl, EstimateArg
       case 3: bits = sign_word<3>(pkey, first, n); break;
       default: bits = sign_word<4>(pkey, first, n); break;
     }
-    if (chk(S, w, S.chk.sign_words)) out[w] = bits;
+    if (CHK(S, w, S.chk.sign_words)) out[w] = bits;
   }
 }
 

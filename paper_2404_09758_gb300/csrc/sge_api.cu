@@ -334,6 +334,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   w.max_views = L.max_views;
   w.light_bin = kLightBin;
   s->dev.chk.status = w.counters + 3;
+  s->dev.chk.where = w.counters + 8;
   s->dev.chk.bins = w.bin_capacity;
   s->dev.chk.sign_words = w.sgn_words;
   s->chk_true = s->dev.chk;
@@ -936,6 +937,20 @@ int sge_atomic_bench(float* buf, int64_t n_addr, int64_t n_threads, int32_t per_
 }
 
 int sge_checked_build(void) { return SGE_CHECKED ? 1 : 0; }
+
+int sge_check_report(sge_scene* s, sge_stream_t stream, int32_t* site, int64_t* index) {
+  if (!SGE_CHECKED) return fail(SGE_ERR_UNSUPPORTED, "sge_check_report: not the checked build");
+  if (!s || !site || !index) return fail(SGE_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t w[2] = {0u, 0u};
+  cudaError_t e = cudaMemcpyAsync(w, s->ws.counters + 8, sizeof(w), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->ws.counters + 8, 0, sizeof(w), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "sge_check_report");
+  *site = (int32_t)w[0];
+  *index = (int64_t)w[1];
+  return SGE_OK;
+}
 
 int sge_check_limit(sge_scene* s, int32_t which, int64_t limit) {
   if (!SGE_CHECKED) return fail(SGE_ERR_UNSUPPORTED, "sge_check_limit: not the checked build");

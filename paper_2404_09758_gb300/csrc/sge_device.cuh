@@ -18,32 +18,40 @@ namespace sge {
 // Is 0 <= i < n?  The unchecked build assumes so (the host validates what it can); the checked
 // build tests it and, when it fails, records SGE_ERR_BOUNDS in the status word so that the caller
 // skips the access.
-__device__ __forceinline__ bool chk(const SceneDev& S, long long i, long long n) {
+// The first failing check also records its site (file id * 100000 + line) and the index.
+__device__ __forceinline__ bool chk(const SceneDev& S, long long i, long long n, int site) {
 #if SGE_CHECKED
   if (i >= 0 && i < n) return true;
   atomicCAS(S.chk.status, 0u, (uint32_t)SGE_ERR_BOUNDS);
+  if (S.chk.where && atomicCAS(S.chk.where, 0u, (uint32_t)site) == 0u) S.chk.where[1] = (uint32_t)i;
   return false;
 #else
   (void)S;
   (void)i;
   (void)n;
+  (void)site;
   return true;
 #endif
 }
+#ifndef SGE_FILE_ID
+#define SGE_FILE_ID 0
+#endif
+#define CHK(S_, i_, n_) chk(S_, i_, n_, SGE_FILE_ID * 100000 + __LINE__)
+#define CHK_H(S_, i_, n_) chk(S_, i_, n_, 900000 + __LINE__)
 
 // Vertex / UV index k of triangle tri (a failing check reads as index 0).
 __device__ __forceinline__ int vert_of(const SceneDev& S, int tri, int k) {
   const int v = __ldg(S.pidx + 3 * tri + k);
-  return chk(S, v, S.chk.nv) ? v : 0;
+  return CHK_H(S, v, S.chk.nv) ? v : 0;
 }
 __device__ __forceinline__ int uv_of(const SceneDev& S, int tri, int k) {
   const int t = __ldg(S.uvidx + 3 * tri + k);
-  return chk(S, t, S.chk.nuv) ? t : 0;
+  return CHK_H(S, t, S.chk.nuv) ? t : 0;
 }
 
 // Bin entry i (a failing check reads as triangle 0).
 __device__ __forceinline__ uint32_t bin_at(const SceneDev& S, const Workspace& ws, long long i) {
-  return chk(S, i, S.chk.bins) ? ws.bins[i] : 0u;
+  return CHK_H(S, i, S.chk.bins) ? ws.bins[i] : 0u;
 }
 
 
@@ -416,7 +424,7 @@ __device__ __forceinline__ PairSigns pair_signs(const SceneDev& S, const Workspa
 __device__ __forceinline__ uint32_t texel_signs(const PairSigns& ps, int k, long long t) {
   const long long w = ps.sgn_off[k] + (t >> 3);
 #if SGE_CHECKED
-  if (ps.S && !chk(*ps.S, w, ps.S->chk.sign_words)) return 0u;
+  if (ps.S && !CHK_H(*ps.S, w, ps.S->chk.sign_words)) return 0u;
 #endif
   return (__ldg(ps.planes + w) >> (4 * (t & 7))) & 0xFu;
 }

@@ -40,6 +40,7 @@ struct TexDev {
 // sge_check_limit lowered them.  Unused by the unchecked build.
 struct CheckDev {
   uint32_t* status;    // the device status word a failing check writes
+  uint32_t* where;     // [2]: the first failing check's site and (low 32 bits of) its index
   int nv, nuv;         // vertex and UV indices
   long long bins;      // bin entries
   long long sign_words;  // words of one estimate's sign planes

@@ -157,6 +157,7 @@ extern "C" int sge_render_idb_static(const sge_scene_desc* d, int32_t view, uint
   ws.max_views = 1;
   ws.light_bin = kLightBin;
   S.chk.status = ws.counters + 3;
+  S.chk.where = ws.counters + 8;
   S.chk.bins = kBinEntries;
 
   cudaStream_t st = (cudaStream_t)stream;

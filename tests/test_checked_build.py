@@ -40,9 +40,9 @@ def test_every_gradient_credit_and_bin_write_is_range_checked():
     for name, lines in _sources().items():
         for i, line in enumerate(lines):
             window = " ".join(lines[max(0, i - 2):i + 1])
-            if credit.search(line) and "chk(S, " not in window:
+            if credit.search(line) and "CHK(S, " not in window:
                 bad.append(f"{name}:{i + 1}: {line.strip()}")
-            if bins.search(line) and "chk(S, " not in line and "bin_at" not in window:
+            if bins.search(line) and "CHK(S, " not in line and "bin_at" not in window:
                 bad.append(f"{name}:{i + 1}: {line.strip()}")
     assert not bad, "\n".join(bad)
 
@@ -50,10 +50,10 @@ def test_every_gradient_credit_and_bin_write_is_range_checked():
 def test_sign_plane_reads_and_writes_are_range_checked():
     src = _sources()
     dev = "\n".join(src["sge_device.cuh"])
-    assert re.search(r"texel_signs\(.*?\{.*?chk\(\*ps\.S, w, ps\.S->chk\.sign_words\)", dev, re.S)
+    assert re.search(r"texel_signs\(.*?\{.*?CHK_H\(\*ps\.S, w, ps\.S->chk\.sign_words\)", dev, re.S)
     fast = "\n".join(src["k_fast.cu"])
-    assert re.search(r"plane_nibble\(.*?\{.*?chk\(S, w, S\.chk\.sign_words\)", fast, re.S)
-    assert "chk(S, w, S.chk.sign_words)) out[w] = bits;" in "\n".join(src["k_vertex.cu"])
+    assert re.search(r"plane_nibble\(.*?\{.*?CHK\(S, w, S\.chk\.sign_words\)", fast, re.S)
+    assert "CHK(S, w, S.chk.sign_words)) out[w] = bits;" in "\n".join(src["k_vertex.cu"])
 
 
 def test_both_libraries_answer_the_checked_entry_points():
