@@ -26,6 +26,7 @@ constexpr int kDeepEstimates = 16384;    // estimates (grid rows) of one launch
 template <int NS>
 struct DeepSmem {
   Tri t[NS][DCHUNK];
+  uint32_t span[NS][DCHUNK];  // box_span of each staged side-triangle: the pixels it may cover
   int tri[DCHUNK];
   float m[16];
   float red[TILE_PX / 32];
@@ -73,27 +74,33 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
       sm.tri[threadIdx.x] = tri;
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
-        if (pv) {
-          PVert v[3];
+        PVert v[3];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int4 q = __ldg(pv + 2 * vert_of(S, tri, k) + s);
+        for (int k = 0; k < 3; ++k) {
+          const int vi = vert_of(S, tri, k);
+          if (pv) {
+            const int4 q = __ldg(pv + 2 * vi + s);
             v[k].X = q.x;
             v[k].Y = q.y;
             v[k].z = __int_as_float(q.z);
             v[k].iw = __int_as_float(q.w);
             v[k].ok = q.x != kNotDrawn;
+          } else {
+            const float3 p = perturbed_pos(S, vi, key, sides[s]);
+            v[k] = project(sm.m, p.x, p.y, p.z, S.W, S.H, S.near_w);
           }
-          setup_tri(v[0], v[1], v[2], rx, ry, sm.t[s][threadIdx.x]);
-        } else {
-          setup_from_scene(S, sm.m, tri, key, sides[s], rx, ry, sm.t[s][threadIdx.x]);
         }
+        Tri& t = sm.t[s][threadIdx.x];
+        setup_tri(v[0], v[1], v[2], rx, ry, t);
+        // a covered pixel centre lies in the triangle's vertex box
+        sm.span[s][threadIdx.x] = t.ok ? box_span(v, rx, ry, 0) : 0u;
       }
     }
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
+        if (!in_span(sm.span[s][j], dx, dy)) continue;
         const Tri& t = sm.t[s][j];
         if (!t.ok) continue;
         long long e[3];
@@ -239,12 +246,17 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     const float df = loss_diff(cp, cm, f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2)), fp, fm);
     lv = 0.5f * (fp + fm);
     if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
-    for (int q = 0; q < nk; ++q)
+    // one count per key (k_expand_counts gives it to every channel after the call), a signed
+    // sum per channel
+    for (int q = 0; q < nk; ++q) {
+      const uint32_t kind = ks[q] >> 28, idx = ks[q] & 0x0FFFFFFFu;
+      const long long kc = kind == 0 ? (long long)idx : ws.kc_off[kind - 1] + idx;
+      if (CHK(S, kc, ws.n_kcount)) atomicAdd(ws.kcount + kc, 1u);
       for_each_signed_channel<false>(S, ps, ks[q], [&](long long p, int, bool neg) {
         if (!CHK(S, p, S.chk.params)) return;
         atomicAdd(a.grad + p, neg ? -df : df);
-        atomicAdd(a.counts + p, 1u);
       });
+    }
   }
   if (a.loss) cta_add(lv / (float)a.pairs, sm.red, a.loss + slot);
 }
@@ -298,6 +310,33 @@ cudaError_t launch_deep_estimate(const SceneDev& S, const Workspace& ws, const V
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Every key's contributions of the call into the counts of its channels (each parameter belongs to
+// one key: plain adds), and the key counts back to zero.
+__global__ void k_expand_counts(SceneDev S, Workspace ws, uint32_t* counts) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ws.n_kcount) return;
+  const uint32_t n = ws.kcount[j];
+  if (n == 0) return;
+  ws.kcount[j] = 0u;
+  long long base = 3 * j;
+  int nch = 3;
+  if (j >= S.nv) {
+    for (int k = 0; k < S.ntex; ++k)
+      if (ws.kc_off[k] >= 0 && j >= ws.kc_off[k] && j < ws.kc_off[k] + (long long)S.tex[k].w * S.tex[k].h) {
+        base = S.tex[k].offset + (j - ws.kc_off[k]) * S.tex[k].c;
+        nch = S.tex[k].c;
+      }
+  }
+  for (int c = 0; c < nch; ++c)
+    if (CHK(S, base + c, S.chk.params)) counts[base + c] += n;
+}
+
+cudaError_t launch_expand_counts(const SceneDev& S, const Workspace& ws, uint32_t* counts, cudaStream_t st) {
+  if (ws.n_kcount == 0) return cudaSuccess;
+  k_expand_counts<<<(unsigned)((ws.n_kcount + 255) / 256), 256, 0, st>>>(S, ws, counts);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_render_deep(const SceneDev& S, const Workspace& ws, int slot, int view, uint64_t key, int side,

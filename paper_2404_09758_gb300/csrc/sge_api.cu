@@ -61,11 +61,13 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
   size_t tri_rect, tri_margin, tri_z, pverts, vbits, tile_count, tile_off, tile_cur, bins, items, counters, keys, uvbuf, dfbuf,
-      desc, tile_live, cand, ncand, tsign, total;
+      desc, tile_live, cand, ncand, tsign, kcount, total;
   int max_views, max_pairs;
   long long bin_capacity;
   long long sgn_words;
   int sgn_off[SGE_MAX_TEXTURES];
+  long long n_kcount;
+  long long kc_off[SGE_MAX_TEXTURES];
 };
 
 int tiles_of(int n) { return (n + TILE - 1) / TILE; }
@@ -174,6 +176,17 @@ int make_layout(const sge_scene_desc* d, const sge_config* c, Layout& L) {
     L.sgn_words += ((long long)S.rtex[r].w * S.rtex[r].h + 7) / 8;
   }
   L.tsign = take(sizeof(uint32_t) * (size_t)L.max_views * L.max_pairs * (size_t)L.sgn_words);
+  // transparent scenes: one contribution count per key (welded vertex, texel of a read texture)
+  L.n_kcount = 0;
+  for (int k = 0; k < SGE_MAX_TEXTURES; ++k) L.kc_off[k] = -1;
+  if (d->shading == SGE_SHADE_TRANSPARENT) {
+    L.n_kcount = d->n_vertices;
+    for (int r = 0; r < S.nread; ++r) {
+      L.kc_off[S.read_k[r]] = L.n_kcount;
+      L.n_kcount += (long long)S.rtex[r].w * S.rtex[r].h;
+    }
+  }
+  L.kcount = take(sizeof(uint32_t) * (size_t)L.n_kcount);
   L.total = o;
   return SGE_OK;
 }
@@ -329,6 +342,9 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   w.dfbuf = reinterpret_cast<float*>(base + L.dfbuf);
   w.tsign = L.sgn_words > 0 ? reinterpret_cast<uint32_t*>(base + L.tsign) : nullptr;
   w.sgn_words = L.sgn_words;
+  w.kcount = L.n_kcount > 0 ? reinterpret_cast<uint32_t*>(base + L.kcount) : nullptr;
+  w.n_kcount = L.n_kcount;
+  for (int k = 0; k < SGE_MAX_TEXTURES; ++k) w.kc_off[k] = L.kc_off[k];
   for (int k = 0; k < SGE_MAX_TEXTURES; ++k) w.sgn_off[k] = L.sgn_off[k];
   w.bin_capacity = L.bin_capacity;
   w.max_views = L.max_views;
@@ -351,6 +367,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) e = cudaMemset(w.counters, 0, 64);
+  if (e == cudaSuccess && w.kcount) e = cudaMemset(w.kcount, 0, sizeof(uint32_t) * (size_t)w.n_kcount);
   if (e != cudaSuccess) {
     if (s->side) cudaStreamDestroy(s->side);
     if (s->fork) cudaEventDestroy(s->fork);
@@ -452,6 +469,7 @@ int estimate_grad(sge_scene* s, uint64_t seed, uint32_t iter, const uint32_t* it
       e = launch_vertex_pass(s->dev, s->ws, vl, b, st);
       if (e == cudaSuccess) e = launch_deep_estimate(s->dev, s->ws, vl, b, st);
     }
+    if (e == cudaSuccess) e = launch_expand_counts(s->dev, s->ws, counts, st);
     return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_estimate_grad");
   }
   // pairs run in blocks of at most max_pairs_per_call (the projected-vertex buffer holds one

@@ -508,6 +508,29 @@ __device__ __forceinline__ void setup_from_scene(const SceneDev& S, const float*
   setup_tri(v[0], v[1], v[2], rx, ry, t);
 }
 
+// The tile's columns (bits 0-15) and rows (bits 16-31) whose pixel centres lie in the bounding
+// box of the projected vertices v grown by `grow` fixed-point units per axis (rx, ry: the tile's
+// first pixel centre).  Every perturbed version of a triangle lies in its box grown by the margin
+// (each snapped vertex moves at most that far per axis), and a pixel inside the triangle in its
+// box: a pre-filter for maybe_visible and surely_covers, which decide inside it.
+__device__ __forceinline__ uint32_t box_span(const PVert (&v)[3], long long rx, long long ry, long long grow) {
+  const long long xl = (long long)min(v[0].X, min(v[1].X, v[2].X)) - rx - grow;
+  const long long xh = (long long)max(v[0].X, max(v[1].X, v[2].X)) - rx + grow;
+  const long long yl = (long long)min(v[0].Y, min(v[1].Y, v[2].Y)) - ry - grow;
+  const long long yh = (long long)max(v[0].Y, max(v[1].Y, v[2].Y)) - ry + grow;
+  // pixel (dx, dy) sits at (256 dx, 256 dy): columns ceil(xl / 256) .. floor(xh / 256)
+  const long long x0 = -((-xl) >> 8), x1 = xh >> 8, y0 = -((-yl) >> 8), y1 = yh >> 8;
+  if (x0 > 15 || x1 < 0 || y0 > 15 || y1 < 0 || x0 > x1 || y0 > y1) return 0u;
+  const int xa = (int)max(x0, 0ll), xb = (int)min(x1, 15ll), ya = (int)max(y0, 0ll), yb = (int)min(y1, 15ll);
+  const uint32_t xm = ((2u << xb) - 1u) & ~((1u << xa) - 1u);
+  const uint32_t ym = ((2u << yb) - 1u) & ~((1u << ya) - 1u);
+  return xm | (ym << 16);
+}
+
+__device__ __forceinline__ bool in_span(uint32_t span, int dx, int dy) {
+  return ((span >> dx) & (span >> (16 + dy)) & 1u) != 0;
+}
+
 // Evaluate the oriented edge functions of t at offset (dx, dy) pixels from its reference point.
 __device__ __forceinline__ bool cover(const Tri& t, int dx, int dy, long long e[3]) {
   bool in = true;

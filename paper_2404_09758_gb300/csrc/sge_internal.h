@@ -109,6 +109,11 @@ struct Workspace {
                          // per texel (bit c: channel c has s = -1) of every texture the shading reads
   long long sgn_words;   // 32-bit words of one estimate's planes
   int sgn_off[SGE_MAX_TEXTURES];  // word offset of texture k's plane in them (-1: not read)
+  uint32_t* kcount;      // [n_kcount] transparent scenes: contributions per key of the running call
+                         // (welded vertex v at v, texel t of read texture k at kc_off[k] + t), added
+                         // to every channel's count and cleared by k_expand_counts; zero between calls
+  long long n_kcount;
+  long long kc_off[SGE_MAX_TEXTURES];
   long long bin_capacity;
   int max_views;
   int max_pairs;
@@ -242,6 +247,7 @@ cudaError_t launch_step(const SceneDev& S, const sge_opt& o, float* grad, uint32
 // state[0] += d_iter, state[1] += d_t (one thread).
 cudaError_t launch_iter_advance(uint32_t* state, int d_iter, int d_t, cudaStream_t st);
 cudaError_t launch_validate(const SceneDev& S, uint32_t* status, cudaStream_t st);
+cudaError_t launch_expand_counts(const SceneDev& S, const Workspace& ws, uint32_t* counts, cudaStream_t st);
 
 __host__ __device__ inline int n_tiles(const SceneDev& S) { return S.tiles_x * S.tiles_y; }
 
