@@ -163,8 +163,29 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     Foot f = footprint(u, v, A.w, A.h);
     if (S.foot_nearest) f.nearest = nearest_texel(u, v, A.w, A.h);
     float a[4];
-    if (ps) sample_tex_ps(A, f, *ps, side, a);
-    else sample_tex(A, f, key, side, a);
+    // an RGBA albedo in a 16-byte aligned array: one vector load per texel
+    if (ps && A.c == 4 && ((reinterpret_cast<uintptr_t>(A.ptr) & 15) == 0)) {
+      const float w4[4] = {(1.0f - f.fx) * (1.0f - f.fy), f.fx * (1.0f - f.fy), (1.0f - f.fx) * f.fy, f.fx * f.fy};
+      const int tx[4] = {f.x0, f.x1, f.x0, f.x1};
+      const int ty[4] = {f.y0, f.y0, f.y1, f.y1};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a[c] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long tt = (long long)ty[q] * A.w + tx[q];
+        const float4 v4 = __ldg(reinterpret_cast<const float4*>(A.ptr + tt * 4));
+        uint32_t sb = texel_signs(*ps, A.index, tt);
+        if (side < 0) sb = ~sb;
+        a[0] += w4[q] * __fadd_rn(v4.x, (sb & 1) ? -A.eps : A.eps);
+        a[1] += w4[q] * __fadd_rn(v4.y, (sb & 2) ? -A.eps : A.eps);
+        a[2] += w4[q] * __fadd_rn(v4.z, (sb & 4) ? -A.eps : A.eps);
+        a[3] += w4[q] * __fadd_rn(v4.w, (sb & 8) ? -A.eps : A.eps);
+      }
+    } else if (ps) {
+      sample_tex_ps(A, f, *ps, side, a);
+    } else {
+      sample_tex(A, f, key, side, a);
+    }
     const float al = fminf(fmaxf(a[3], 0.0f), 1.0f);
     const float w = T * al;
     c0 += w * a[0];
