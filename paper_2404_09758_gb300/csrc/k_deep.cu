@@ -20,7 +20,6 @@ namespace {
 
 constexpr int K = SGE_MAX_LAYERS;
 constexpr int DCHUNK = 128;              // binned triangles staged per pass
-constexpr int MAX_KEYS = 2 * K * 7;      // contributor keys of a pixel: 3 vertices + 4 texels per fragment
 constexpr int kDeepEstimates = 16384;    // estimates (grid rows) of one launch
 
 template <int NS>
@@ -117,7 +116,7 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
 
 // Front-to-back composite of one side's list at one pixel: T = 1; per listed fragment
 // C += T a rgb, T *= 1 - a with a = clamp(alpha, 0, 1); C += T background.  on_fragment(tri,
-// foot) is called for each listed fragment with its triangle and albedo footprint.
+// foot, j) is called for each listed fragment with its triangle, albedo footprint and layer.
 // staged: the side's set-ups in shared memory (slots P) when the bin fit one chunk, else NULL
 // (each fragment is set up again; the same arithmetic gives the same set-up).
 // ps: the estimate's precomputed signs (vertex bits, texel planes), or NULL to hash with key.
@@ -192,7 +191,7 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     c1 += w * a[1];
     c2 += w * a[2];
     T *= 1.0f - al;
-    on_fragment(tri, f);
+    on_fragment(tri, f, j);
   }
   return f3(c0 + T * S.bg[0], c1 + T * S.bg[1], c2 + T * S.bg[2]);
 }
@@ -239,27 +238,56 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     // the contributor set, gathered while compositing: every listed fragment's welded vertices
     // and footprint texels, both sides, each key once
     const TexDev& A = S.rtex[0];
-    uint32_t ks[MAX_KEYS];
-    int nk = 0;
-    auto add = [&](uint32_t k) {
-      for (int q = 0; q < nk; ++q)
-        if (ks[q] == k) return;
-      ks[nk++] = k;
+    // vertex keys and texel keys in separate lists (a key of one kind never equals one of the other)
+    uint32_t vk[2 * K * 3], tk[2 * K * 4];
+    int nvk = 0, ntk = 0;
+    auto addv = [&](uint32_t k) {
+      for (int q = 0; q < nvk; ++q)
+        if (vk[q] == k) return;
+      vk[nvk++] = k;
     };
-    auto credit_keys = [&](int tri, const Foot& f) {
+    auto addt = [&](uint32_t k) {
+      for (int q = 0; q < ntk; ++q)
+        if (tk[q] == k) return;
+      tk[ntk++] = k;
+    };
+    // side +'s fragments (layer j: triangle and footprint); a side - fragment on a triangle listed
+    // there brings no new vertex, one with a footprint listed there no new texel
+    int g_tri[K], g_fp[K];
 #pragma unroll
-      for (int v = 0; v < 3; ++v) add(vkey(vert_of(S, tri, v)));
+    for (int j = 0; j < K; ++j) g_tri[j] = -1, g_fp[j] = -1;
+    bool minus = false;
+    auto credit_keys = [&](int tri, const Foot& f, int j) {
+      // a footprint: its first texel and whether its rows were clamped to one (x1 follows from x0)
+      const int fp = S.foot_nearest ? f.nearest : 2 * (f.y0 * A.w + f.x0) + (f.y1 != f.y0 ? 1 : 0);
+      bool tri_seen = false, fp_seen = false;
+      if (!minus) {
+        g_tri[j] = tri;
+        g_fp[j] = fp;
+      } else {
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          tri_seen = tri_seen || g_tri[i] == tri;
+          fp_seen = fp_seen || (g_tri[i] >= 0 && g_fp[i] == fp);
+        }
+      }
+      if (!tri_seen) {
+#pragma unroll
+        for (int v = 0; v < 3; ++v) addv(vkey(vert_of(S, tri, v)));
+      }
+      if (fp_seen) return;
       if (S.foot_nearest) {
-        add(tkey(A.index, f.nearest));
+        addt(tkey(A.index, f.nearest));
         return;
       }
-      add(tkey(A.index, f.y0 * A.w + f.x0));
-      add(tkey(A.index, f.y0 * A.w + f.x1));
-      add(tkey(A.index, f.y1 * A.w + f.x0));
-      add(tkey(A.index, f.y1 * A.w + f.x1));
+      addt(tkey(A.index, f.y0 * A.w + f.x0));
+      addt(tkey(A.index, f.y0 * A.w + f.x1));
+      addt(tkey(A.index, f.y1 * A.w + f.x0));
+      addt(tkey(A.index, f.y1 * A.w + f.x1));
     };
     const float3 cp = deep_composite(S, sm.m, key, 1, L[0], P[0], resident ? sm.t[0] : nullptr, rx, ry, dx, dy,
                                      credit_keys, &ps, pv);
+    minus = true;
     const float3 cm = deep_composite(S, sm.m, key, -1, L[1], P[1], resident ? sm.t[1] : nullptr, rx, ry, dx, dy,
                                      credit_keys, &ps, pv);
     const float* tp = S.targets + ((long long)view * npx + p) * 3;
@@ -269,11 +297,12 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
     // one count per key (k_expand_counts gives it to every channel after the call), a signed
     // sum per channel
-    for (int q = 0; q < nk; ++q) {
-      const uint32_t kind = ks[q] >> 28, idx = ks[q] & 0x0FFFFFFFu;
+    for (int q = 0; q < nvk + ntk; ++q) {
+      const uint32_t kq = q < nvk ? vk[q] : tk[q - nvk];
+      const uint32_t kind = kq >> 28, idx = kq & 0x0FFFFFFFu;
       const long long kc = kind == 0 ? (long long)idx : ws.kc_off[kind - 1] + idx;
       if (CHK(S, kc, ws.n_kcount)) atomicAdd(ws.kcount + kc, 1u);
-      for_each_signed_channel<false>(S, ps, ks[q], [&](long long p, int, bool neg) {
+      for_each_signed_channel<false>(S, ps, kq, [&](long long p, int, bool neg) {
         if (!CHK(S, p, S.chk.params)) return;
         atomicAdd(a.grad + p, neg ? -df : df);
       });
@@ -307,7 +336,7 @@ __global__ void __launch_bounds__(TILE_PX) k_render_deep(SceneDev S, Workspace w
     }
     if (rgb || loss) {
       const float3 c = deep_composite(S, sm.m, key, side, L[0], P[0], resident ? sm.t[0] : nullptr, rx, ry, dx, dy,
-                                      [](int, const Foot&) {});
+                                      [](int, const Foot&, int) {});
       if (rgb) rgb[3 * p] = c.x, rgb[3 * p + 1] = c.y, rgb[3 * p + 2] = c.z;
       if (loss) {
         const float* tp = S.targets + ((long long)view * npx + p) * 3;
