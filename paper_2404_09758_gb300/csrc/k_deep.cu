@@ -26,10 +26,41 @@ template <int NS>
 struct DeepSmem {
   Tri t[NS][DCHUNK];
   uint32_t span[NS][DCHUNK];  // box_span of each staged side-triangle: the pixels it may cover
+  uint8_t small[NS][DCHUNK];  // its edge functions over the tile fit 32 bits
   int tri[DCHUNK];
   float m[16];
   float red[TILE_PX / 32];
 };
+
+// Every edge function of t over the tile fits 32 bits: |a|, |b| < 2^16 and |e0| < 2^29, so
+// |e0 + a 256 dx + b 256 dy| < 2^30 for the pixel offsets 0..15.
+__device__ __forceinline__ bool small_tri(const Tri& t) {
+  bool small = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    small = small && abs(t.a[k]) < (1 << 16) && abs(t.b[k]) < (1 << 16) && t.e0[k] > -(1ll << 29) &&
+            t.e0[k] < (1ll << 29);
+  return small;
+}
+
+// cover() and lambdas() at pixel offset (dx, dy): the same integers and the same float
+// conversions, in 32-bit arithmetic for a small triangle.
+__device__ __forceinline__ bool cover_lambdas(const Tri& t, bool small, int dx, int dy, float l[3]) {
+  if (small) {
+    bool in = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = (int)t.e0[k] + t.a[k] * (dx * 256) + t.b[k] * (dy * 256);
+      in = in && (e + t.bias[k] >= 0);
+      l[k] = __fmul_rn(__int2float_rn(e), t.inv_area);
+    }
+    return in;
+  }
+  long long e[3];
+  const bool in = cover(t, dx, dy, e);
+  lambdas(e, t.inv_area, l);
+  return in;
+}
 
 // Insert key k (staged at shared-memory slot q) into the ascending list L (slots P); the
 // largest key falls off the end.
@@ -93,6 +124,7 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
         setup_tri(v[0], v[1], v[2], rx, ry, t);
         // a covered pixel centre lies in the triangle's vertex box
         sm.span[s][threadIdx.x] = t.ok ? box_span(v, rx, ry, 0) : 0u;
+        sm.small[s][threadIdx.x] = t.ok && small_tri(t);
       }
     }
     __syncthreads();
@@ -102,10 +134,8 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
         if (!in_span(sm.span[s][j], dx, dy)) continue;
         const Tri& t = sm.t[s][j];
         if (!t.ok) continue;
-        long long e[3];
-        if (!cover(t, dx, dy, e)) continue;
         float l[3];
-        lambdas(e, t.inv_area, l);
+        if (!cover_lambdas(t, sm.small[s][j] != 0, dx, dy, l)) continue;
         deep_insert(L[s], P[s], ((unsigned long long)ordered_bits(interp_depth(l, t.z)) << 32) | (uint32_t)sm.tri[j],
                     j);
       }

@@ -40,7 +40,8 @@ constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 struct SideSmem {
   long long e0[3][BIN_CHUNK];
   int a[3][BIN_CHUNK], b[3][BIN_CHUNK];
-  int bias[BIN_CHUNK];  // bit k set: edge k is not top/left
+  int bias[BIN_CHUNK];  // bit k set: edge k is not top/left; bit 3: every edge function over the tile
+                        // fits 32 bits (|a|, |b| < 2^16, |e0| < 2^29)
   float inv_area[BIN_CHUNK];
   float z[3][BIN_CHUNK], iw[3][BIN_CHUNK];
   int tri[BIN_CHUNK];  // -1 when not drawn on this side
@@ -70,6 +71,7 @@ __device__ __forceinline__ void store_tri(SideSmem& s, int j, const Tri& t, int 
     return;
   }
   int bias = 0;
+  bool small = true;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     s.e0[k][j] = t.e0[k];
@@ -78,8 +80,11 @@ __device__ __forceinline__ void store_tri(SideSmem& s, int j, const Tri& t, int 
     s.z[k][j] = t.z[k];
     s.iw[k][j] = t.iw[k];
     bias |= (t.bias[k] ? 1 : 0) << k;
+    // over the tile's pixel offsets (0..15) * 256: |a dx| + |b dy| < 2 * 2^28, so |e| < 2^30
+    small = small && abs(t.a[k]) < (1 << 16) && abs(t.b[k]) < (1 << 16) && t.e0[k] > -(1ll << 29) &&
+            t.e0[k] < (1ll << 29);
   }
-  s.bias[j] = bias;
+  s.bias[j] = bias | (small ? 8 : 0);
   s.inv_area[j] = t.inv_area;
   s.tri[j] = tri;
 }
@@ -104,16 +109,30 @@ __device__ __forceinline__ unsigned long long test_key(const SideSmem& s, int j,
   int tri = s.tri[j];
   if (tri < 0) return ~0ull;
   int bias = s.bias[j];
-  long long e[3];
+  float l[3];
   bool in = true;
+  if (bias & 8) {
+    // the same integers in 32-bit arithmetic, and the same float conversions
+    int e[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    e[k] = s.e0[k][j] + (long long)s.a[k][j] * (dx * 256) + (long long)s.b[k][j] * (dy * 256);
-    in = in && (e[k] - ((bias >> k) & 1) >= 0);
+    for (int k = 0; k < 3; ++k) {
+      e[k] = (int)s.e0[k][j] + s.a[k][j] * (dx * 256) + s.b[k][j] * (dy * 256);
+      in = in && (e[k] - ((bias >> k) & 1) >= 0);
+    }
+    if (!in) return ~0ull;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) l[k] = __fmul_rn(__int2float_rn(e[k]), s.inv_area[j]);
+  } else {
+    long long e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      e[k] = s.e0[k][j] + (long long)s.a[k][j] * (dx * 256) + (long long)s.b[k][j] * (dy * 256);
+      in = in && (e[k] - ((bias >> k) & 1) >= 0);
+    }
+    if (!in) return ~0ull;
+    lambdas(e, s.inv_area[j], l);
   }
-  if (!in) return ~0ull;
-  float l[3], z[3] = {s.z[0][j], s.z[1][j], s.z[2][j]};
-  lambdas(e, s.inv_area[j], l);
+  float z[3] = {s.z[0][j], s.z[1][j], s.z[2][j]};
   float d = interp_depth(l, z);
   return ((unsigned long long)ordered_bits(d) << 32) | (uint32_t)tri;
 }
