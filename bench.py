@@ -338,28 +338,28 @@ def run_ours(args):
     grad.zero_()
     counts.zero_()
 
-    # end to end through the public API from pinned host memory: parameters and targets in,
-    # updated parameters and the loss out, every step
-    host_params = [p.detach().cpu().pin_memory() for p in g.param_groups()]
-    host_targets = targets.cpu().pin_memory()
+    # end to end through the C ABI from pinned host memory (sge_iterate_host): parameters and
+    # targets copied in, the estimate, the Adam step and the advance, the updated parameters and
+    # the loss copied out, every step
+    host_theta = torch.cat([p.detach().reshape(-1) for p in g.param_groups()]).cpu().pin_memory()
+    host_targets = targets.reshape(-1).cpu().pin_memory()
+    host_theta_out = torch.empty_like(host_theta).pin_memory()
     host_loss = torch.empty(N_VIEWS, pin_memory=True)
-    h2d = sum(p.numel() * 4 for p in host_params) + host_targets.numel() * 4
-    d2h = sum(p.numel() * 4 for p in host_params) + host_loss.numel() * 4
+    h2d = host_theta.numel() * 4 + host_targets.numel() * 4
+    d2h = host_theta_out.numel() * 4 + host_loss.numel() * 4
     e2e_steps = max(1, min(args.steps, 5))
+    e2e_state = IterState(5000, 1, device=dev)
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     with torch.cuda.stream(st):
         for k in range(e2e_steps):
             flush.fill_(k & 0xFF)
             ee[k][0].record(st)
-            for hp, dp in zip(host_params, g.param_groups()):
-                dp.copy_(hp, non_blocking=True)
-            g.targets.copy_(host_targets, non_blocking=True)
-            graph.replay()
-            for hp, dp in zip(host_params, g.param_groups()):
-                hp.copy_(dp, non_blocking=True)
-            host_loss.copy_(loss, non_blocking=True)
+            g.iterate_host(1, e2e_state, views, PAIRS, grad, counts, m, v, sc.eps_pos, lr_tex, kind=STEP_ADAM,
+                           loss_dev=loss, theta_in=host_theta, targets_in=host_targets, theta_out=host_theta_out,
+                           loss_out=host_loss, stream=st)
             ee[k][1].record(st)
     torch.cuda.synchronize()
+    assert g.status(st) == 0
     e2e_s = sum(a.elapsed_time(b) for a, b in ee) / 1000.0
     e2e_value = world * px_per_step * e2e_steps / e2e_s
 
@@ -404,7 +404,8 @@ def run_ours(args):
                            "param_gradients_per_s": contributions / (plain_ms / 1000.0)},
             "batched_over_plain": plain_ms / (1000.0 * t_total / args.steps),
             "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "api": "sge_iterate_host with pinned host buffers (theta and targets in, theta and loss out)"},
             # per iteration: 3 binning kernels, the pruning pass, the vertex pass, the texel sign
             # planes, the fast and the heavy-bin estimator, the background-loss kernel, the step
             # kernel and the advance
@@ -767,9 +768,9 @@ def run_transparent(args):
                        "triangles": int(len(sc.pos_idx)), "params": int(g.n_params),
                        "l2": "flushed between timed steps (256 MB write)", "graph": "none (eager)"},
             "contributions_per_s": contributions * args.steps / t_total,
-            # per call: the three binning kernels, the vertex pass, the texel sign planes and the
-            # deep estimator
-            "gpu_launches": 6 * args.steps,
+            # per call: the three binning kernels, the vertex pass, the texel sign planes, the
+            # deep estimator and the count expansion
+            "gpu_launches": 7 * args.steps,
             "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -289,6 +289,38 @@ int sge_step_state(sge_scene *scene, const sge_opt *opt, const sge_iter_state *s
  * work enqueued before it (an iteration's last node in a captured loop). */
 int sge_iter_advance(sge_iter_state *state, int32_t d_iter, int32_t d_t, sge_stream_t stream);
 
+/* Host memory of one optimizer iteration run by sge_iterate_host; any member may be NULL
+ * (that copy is skipped).  Pinned (page-locked) host memory lets the copies run
+ * asynchronously; pageable memory works too, with the copies staged by the driver. */
+typedef struct {
+    const float *theta_in;   /* host [d]: theta in gradient order (positions vertex-major xyz,
+                                then each texture [height][width][channels]), copied into the
+                                scene's parameter arrays before the estimate                 */
+    const float *targets_in; /* host [n_views of the scene][height][width][3]: copied into the
+                                scene's target images before the estimate                   */
+    float *theta_out;        /* host [d]: the updated theta, copied out after the step       */
+    float *loss_out;         /* host [n_views of the call]: each listed view's image error
+                                (as loss_out of sge_estimate_grad), copied out after the step */
+} sge_host_io;
+
+/* One iteration of Section 5's loop (N = n_views x pairs_per_view estimates, Eq. 9, then one
+ * descent step) for a caller whose parameters and targets live in host memory: copies
+ * io->theta_in and io->targets_in into the device arrays the scene borrows (its positions,
+ * textures and targets: these are overwritten), zeroes loss_dev, then runs
+ * sge_estimate_grad_state, sge_step_state (n_pairs_total = N) and sge_iter_advance(state, 1, 1),
+ * and copies the updated theta to io->theta_out and loss_dev to io->loss_out.  Every copy and
+ * kernel is enqueued on `stream` in that order (one cudaMemcpyAsync per array); nothing
+ * synchronises, so the host buffers must stay valid until the stream has passed the call.
+ * grad_sums, counts (zeroed by the step), adam_m, adam_v, state: device memory, as in those
+ * calls; loss_dev: device [n_views] float32, required when io->loss_out is set (else may be
+ * NULL).  Errors: SGE_ERR_INVALID_ARG for a NULL scene, io, opt or state, a bad view list,
+ * pairs_per_view < 1, or loss_out without loss_dev (checked before anything is enqueued);
+ * the errors of the calls it runs; SGE_ERR_CUDA when a copy cannot be enqueued. */
+int sge_iterate_host(sge_scene *scene, uint64_t seed, sge_iter_state *state, const int32_t *view_ids,
+                     int32_t n_views, int32_t pairs_per_view, const sge_opt *opt, float *grad_sums,
+                     uint32_t *counts, float *adam_m, float *adam_v, float *loss_dev, const sge_host_io *io,
+                     sge_stream_t stream);
+
 /* One asset of a batched call: a scene with its views and its own outputs. */
 typedef struct {
     sge_scene *scene;          /* distinct within one call                                  */

@@ -298,6 +298,27 @@ class Scene:
                                                             _stream_ptr(stream)))
         return image_df
 
+    def iterate_host(self, seed: int, state: "IterState", view_ids: Sequence[int], pairs_per_view: int, grad,
+                     counts, m, v, lr_pos: float, lr_tex: Sequence[float], kind: int = _abi.STEP_ADAM,
+                     loss_dev=None, theta_in=None, targets_in=None, theta_out=None, loss_out=None,
+                     beta1: float = 0.9, beta2: float = 0.999, adam_eps: float = 1e-8, stream=None) -> None:
+        """One optimizer iteration from host memory (sge_iterate_host): theta_in [d] and
+        targets_in (CPU float32 tensors, pinned for asynchronous copies) into the scene's device
+        arrays, the estimate of the state's iteration, the step with the state's t, the
+        advance, then the updated theta into theta_out and the loss into loss_out.  Nothing
+        synchronises: keep the host tensors alive until the stream has passed the call."""
+        o = _abi.Opt()
+        o.kind = int(kind)
+        o.lr_pos = float(lr_pos)
+        for k, lr in enumerate(lr_tex):
+            o.lr_tex[k] = float(lr)
+        o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), 1
+        io = _abi.HostIO(_host_ptr(theta_in), _host_ptr(targets_in), _host_ptr(theta_out), _host_ptr(loss_out))
+        arr, n = self._views(view_ids)
+        _abi.check(_abi.load().sge_iterate_host(self._h, int(seed), state.ptr, arr, n, int(pairs_per_view),
+                                                C.byref(o), _ptr(grad), _ptr(counts), _ptr(m), _ptr(v),
+                                                _ptr(loss_dev), C.byref(io), _stream_ptr(stream)))
+
     def loss(self, view_ids: Sequence[int], out=None, stream=None):
         """Image error f(theta) of the unperturbed scene per listed view (Table 1), [n] float32."""
         torch = _torch()
@@ -333,6 +354,15 @@ class Scene:
         o.beta1, o.beta2, o.adam_eps, o.t = float(beta1), float(beta2), float(adam_eps), int(t)
         _abi.check(L.sge_step(self._h, C.byref(o), _ptr(grad), _ptr(counts), int(n_pairs_total),
                               _ptr(m), _ptr(v), _stream_ptr(stream)))
+
+
+def _host_ptr(t):
+    """Address of a host (CPU) tensor's data, or None."""
+    if t is None:
+        return None
+    if t.is_cuda or not t.is_contiguous() or t.dtype != _torch().float32:
+        raise ValueError("host buffers must be contiguous float32 CPU tensors")
+    return t.data_ptr()
 
 
 class IterState:

@@ -29,7 +29,7 @@ EXPORTS = ("sge_workspace_size", "sge_create_scene", "sge_num_params", "sge_set_
            "sge_bin_stats", "sge_draw_views", "sge_estimate_grad_full_image",
            "sge_refine", "sge_render_deep", "sge_estimate_grad_state", "sge_step_state", "sge_iter_advance",
            "sge_estimate_grad_batch_state", "sge_atomic_bench", "sge_checked_build", "sge_check_limit",
-           "sge_check_report")
+           "sge_check_report", "sge_iterate_host")
 
 
 class Texture(C.Structure):
@@ -52,6 +52,11 @@ class Config(C.Structure):
     _fields_ = [("max_views_per_call", C.c_int32), ("bin_capacity", C.c_int64),
                 ("pairs_per_item", C.c_int32), ("blocks_per_sm", C.c_int32),
                 ("max_pairs_per_call", C.c_int32), ("footprint", C.c_int32)]
+
+
+class HostIO(C.Structure):
+    _fields_ = [("theta_in", C.c_void_p), ("targets_in", C.c_void_p), ("theta_out", C.c_void_p),
+                ("loss_out", C.c_void_p)]
 
 
 class BatchEntry(C.Structure):
@@ -114,6 +119,7 @@ def load(build_if_missing: bool = False):
         L.sge_estimate_grad_state.argtypes = [P, U64, P, P, I32, I32, P, P, P, P, P]
         L.sge_step_state.argtypes = [P, P, P, P, P, I64, P, P, P]
         L.sge_iter_advance.argtypes = [P, I32, I32, P]
+        L.sge_iterate_host.argtypes = [P, U64, P, P, I32, I32, P, P, P, P, P, P, P, P]
         L.sge_estimate_grad_batch_state.argtypes = [P, I32, U64, P, I32, P, P]
         L.sge_atomic_bench.argtypes = [P, I64, I64, I32, P]
         L.sge_checked_build.argtypes = []

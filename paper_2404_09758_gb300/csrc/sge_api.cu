@@ -550,6 +550,55 @@ int sge_iter_advance(sge_iter_state* state, int32_t d_iter, int32_t d_t, sge_str
   return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_iter_advance");
 }
 
+int sge_iterate_host(sge_scene* s, uint64_t seed, sge_iter_state* state, const int32_t* view_ids, int32_t n_views,
+                     int32_t pairs_per_view, const sge_opt* opt, float* grad_sums, uint32_t* counts, float* adam_m,
+                     float* adam_v, float* loss_dev, const sge_host_io* io, sge_stream_t stream) {
+  if (!s || !io || !opt) return fail(SGE_ERR_INVALID_ARG, "scene, io and opt must be non-NULL");
+  if (!state || !aligned4(state)) return fail(SGE_ERR_INVALID_ARG, "state must be a 4-byte aligned device pointer");
+  if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
+  if (io->loss_out && !loss_dev) return fail(SGE_ERR_INVALID_ARG, "io->loss_out needs loss_dev");
+  ViewList vl;
+  int rc = views_of(s, view_ids, n_views, vl);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the parameter groups in gradient order: positions, then each texture
+  const sge_scene_desc& d = s->desc;
+  float* group[1 + SGE_MAX_TEXTURES];
+  size_t count[1 + SGE_MAX_TEXTURES];
+  int ng = 0;
+  group[ng] = d.positions, count[ng++] = 3 * (size_t)d.n_vertices;
+  for (int k = 0; k < d.n_textures; ++k)
+    group[ng] = d.textures[k].texels,
+    count[ng++] = (size_t)d.textures[k].width * d.textures[k].height * d.textures[k].channels;
+  auto copy_theta = [&](float* dst_host, const float* src_host) {
+    size_t off = 0;
+    for (int k = 0; k < ng; ++k) {
+      const size_t bytes = sizeof(float) * count[k];
+      cudaError_t e = src_host ? cudaMemcpyAsync(group[k], src_host + off, bytes, cudaMemcpyHostToDevice, st)
+                               : cudaMemcpyAsync(dst_host + off, group[k], bytes, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return e;
+      off += count[k];
+    }
+    return cudaSuccess;
+  };
+  cudaError_t e = io->theta_in ? copy_theta(nullptr, io->theta_in) : cudaSuccess;
+  if (e == cudaSuccess && io->targets_in)
+    e = cudaMemcpyAsync(const_cast<float*>(s->dev.targets), io->targets_in,
+                        sizeof(float) * 3 * (size_t)d.n_views * d.width * d.height, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && loss_dev) e = cudaMemsetAsync(loss_dev, 0, sizeof(float) * (size_t)n_views, st);
+  if (e != cudaSuccess) return cuda_fail(e, "sge_iterate_host (copies in)");
+  rc = estimate_grad(s, seed, 0, &state->iter, view_ids, n_views, pairs_per_view, grad_sums, counts, loss_dev, nullptr,
+                     stream);
+  if (rc) return rc;
+  rc = step(s, opt, &state->t, grad_sums, counts, (int64_t)n_views * pairs_per_view, adam_m, adam_v, stream);
+  if (rc) return rc;
+  e = launch_iter_advance(&state->iter, 1, 1, st);
+  if (e == cudaSuccess && io->theta_out) e = copy_theta(io->theta_out, nullptr);
+  if (e == cudaSuccess && io->loss_out)
+    e = cudaMemcpyAsync(io->loss_out, loss_dev, sizeof(float) * (size_t)n_views, cudaMemcpyDeviceToHost, st);
+  return e == cudaSuccess ? SGE_OK : cuda_fail(e, "sge_iterate_host (copies out)");
+}
+
 int sge_estimate_grad_plain(sge_scene* s, uint64_t seed, uint32_t iter, const int32_t* view_ids, int32_t n_views,
                             int32_t pairs_per_view, float* grad_sums, uint32_t* counts, float* loss_out,
                             sge_stream_t stream) {

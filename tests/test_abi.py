@@ -43,6 +43,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(sge_scene_desc, textures), offsetof(sge_scene_desc, mvp),
          offsetof(sge_scene_desc, targets), offsetof(sge_scene_desc, ambient));
   printf("%zu %zu %zu\n", offsetof(sge_opt, beta1), offsetof(sge_opt, t), offsetof(sge_config, max_pairs_per_call));
+  printf("%zu %zu %zu\n", sizeof(sge_host_io), offsetof(sge_host_io, targets_in), offsetof(sge_host_io, loss_out));
   return 0;
 }'''
     with tempfile.TemporaryDirectory() as d:
@@ -55,8 +56,26 @@ int main(void) {
     S = _abi.SceneDesc
     want = [ctypes.sizeof(_abi.Texture), ctypes.sizeof(S), ctypes.sizeof(_abi.Config), ctypes.sizeof(_abi.Opt),
             S.textures.offset, S.mvp.offset, S.targets.offset, S.ambient.offset,
-            _abi.Opt.beta1.offset, _abi.Opt.t.offset, _abi.Config.max_pairs_per_call.offset]
+            _abi.Opt.beta1.offset, _abi.Opt.t.offset, _abi.Config.max_pairs_per_call.offset,
+            ctypes.sizeof(_abi.HostIO), _abi.HostIO.targets_in.offset, _abi.HostIO.loss_out.offset]
     assert got == want
+
+
+def test_host_iteration_checks_its_arguments_before_enqueueing():
+    """sge_iterate_host refuses a NULL scene, io, opt or state with SGE_ERR_INVALID_ARG before it
+    copies or launches anything (no GPU is touched here)."""
+    from paper_2404_09758_gb300 import _abi
+    L = _abi.load()
+    io, opt = _abi.HostIO(), _abi.Opt()
+    state = ctypes.c_int32 * 2
+    st = state()
+    cases = ((None, ctypes.byref(st), ctypes.byref(opt), ctypes.byref(io)),
+             (ctypes.c_void_p(8), ctypes.byref(st), ctypes.byref(opt), None),
+             (ctypes.c_void_p(8), ctypes.byref(st), None, ctypes.byref(io)),
+             (ctypes.c_void_p(8), None, ctypes.byref(opt), ctypes.byref(io)))
+    for scene, stp, optp, iop in cases:
+        rc = L.sge_iterate_host(scene, 1, stp, None, 0, 1, optp, None, None, None, None, None, iop, None)
+        assert rc == _abi.ERR_INVALID_ARG, L.sge_last_error()
 
 
 def test_no_cpu_fallback_without_gpu():
