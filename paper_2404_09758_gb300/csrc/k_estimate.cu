@@ -466,15 +466,29 @@ int heavy_batch_blocks_t() {
   return n > 0 ? n : 1;
 }
 
-// Table shapes: unlit 2,048 slots; lit 4,096 slots with per-texture keys, or 2,048 slots of
-// texel-group keys (16 channel sums each) when the read textures share one size.
-constexpr int kHtUnlit = HeavyTable<0>::SLOTS, kHtLit = HeavyTable<1>::SLOTS, kHtGroup = 2048;
+// Table shapes: unlit 2,048 slots; lit 4,096 slots with per-texture keys, or texel-group keys
+// when the read textures share one size: 1,024 slots of 12 channel sums when their channels add
+// up to at most 12 (two CTAs fit an SM), else 2,048 slots of 16.
+constexpr int kHtUnlit = HeavyTable<0>::SLOTS, kHtLit = HeavyTable<1>::SLOTS, kHtGroup = 2048, kHtGroupSmall = 1024;
+constexpr int kGroupSmallChannels = 12;
 
 }  // namespace
 
-int estimate_blocks_per_sm(int shading, int grouped) {
+int group_channels(const SceneDev& S) {
+  int n = 0;
+  for (int r = 0; r < S.nread; ++r) n += S.rtex[r].c;
+  return n;
+}
+
+namespace {
+
+}  // namespace
+
+int estimate_blocks_per_sm(int shading, int grouped, int group_ch) {
   if (shading == SHADE_UNLIT) return heavy_blocks_t<kHtUnlit, 4, false>();
-  return grouped ? heavy_blocks_t<kHtGroup, 16, true>() : heavy_blocks_t<kHtLit, 4, false>();
+  if (!grouped) return heavy_blocks_t<kHtLit, 4, false>();
+  return group_ch <= kGroupSmallChannels ? heavy_blocks_t<kHtGroupSmall, kGroupSmallChannels, true>()
+                                         : heavy_blocks_t<kHtGroup, 16, true>();
 }
 
 int heavy_batch_blocks_per_sm(int shading) {
@@ -520,6 +534,8 @@ cudaError_t launch_estimate(const SceneDev& S, const Workspace& ws, const ViewLi
   if (e == cudaSuccess && ev_fast) e = cudaEventRecord(ev_fast[1], st);
   if (e != cudaSuccess) return e;
   if (S.shading == SHADE_UNLIT) e = launch_heavy_t<kHtUnlit, 4, false>(S, ws, vl, a, grid_heavy, st);
+  else if (S.grouped && group_channels(S) <= kGroupSmallChannels)
+    e = launch_heavy_t<kHtGroupSmall, kGroupSmallChannels, true>(S, ws, vl, a, grid_heavy, st);
   else if (S.grouped) e = launch_heavy_t<kHtGroup, 16, true>(S, ws, vl, a, grid_heavy, st);
   else e = launch_heavy_t<kHtLit, 4, false>(S, ws, vl, a, grid_heavy, st);
   if (e == cudaSuccess && ev_fast) e = cudaEventRecord(ev_fast[2], st);

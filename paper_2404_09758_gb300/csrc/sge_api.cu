@@ -377,7 +377,7 @@ int sge_create_scene(const sge_scene_desc* desc, const sge_config* cfg, void* wo
   }
   int bps = (s->cfg.blocks_per_sm > 0) ? s->cfg.blocks_per_sm : fast_blocks_per_sm(desc->shading, s->dev.grouped);
   s->grid_fast = sms * bps;
-  s->grid_heavy = sms * estimate_blocks_per_sm(desc->shading, s->dev.grouped);
+  s->grid_heavy = sms * estimate_blocks_per_sm(desc->shading, s->dev.grouped, group_channels(s->dev));
   if (s->cfg.pairs_per_item <= 0) s->cfg.pairs_per_item = 8;
   if (s->cfg.pairs_per_item > kMaxPairsPerItem) s->cfg.pairs_per_item = kMaxPairsPerItem;
   *out = s;

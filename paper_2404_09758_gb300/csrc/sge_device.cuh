@@ -550,7 +550,8 @@ __device__ __forceinline__ uint32_t tkey(int k, int texel) { return ((uint32_t)(
 
 // Every parameter channel of a contributor key: f(parameter index, its channel slot in a table
 // entry).  Vertex keys: x, y, z; texel keys: the texture's channels, or with GR (a group key of
-// for_each_contrib<true>) channel c of every read texture r, at slot 4 r + c.
+// for_each_contrib<true>) channel c of every read texture r, at slot (channels of the read
+// textures before r) + c.
 template <bool GR, typename F>
 __device__ __forceinline__ void for_each_channel(const SceneDev& S, uint32_t key, F&& f) {
   const uint32_t kind = key >> 28, idx = key & 0x0FFFFFFFu;
@@ -560,12 +561,14 @@ __device__ __forceinline__ void for_each_channel(const SceneDev& S, uint32_t key
     return;
   }
   if constexpr (GR) {
+    int co = 0;
 #pragma unroll
     for (int r = 0; r < MAX_READ; ++r) {
       if (r >= S.nread) break;
       const TexDev& T = S.rtex[r];
       const long long base = T.offset + (long long)idx * T.c;
-      for (int c = 0; c < T.c; ++c) f(base + c, 4 * r + c);
+      for (int c = 0; c < T.c; ++c) f(base + c, co + c);
+      co += T.c;
     }
   } else {
     const TexDev& T = S.tex[kind - 1];
@@ -585,13 +588,15 @@ __device__ __forceinline__ void for_each_signed_channel(const SceneDev& S, const
     return;
   }
   if constexpr (GR) {
+    int co = 0;
 #pragma unroll
     for (int r = 0; r < MAX_READ; ++r) {
       if (r >= S.nread) break;
       const TexDev& T = S.rtex[r];
       const long long base = T.offset + (long long)idx * T.c;
       const uint32_t sb = texel_signs(ps, T.index, idx);
-      for (int c = 0; c < T.c; ++c) f(base + c, 4 * r + c, ((sb >> c) & 1) != 0);
+      for (int c = 0; c < T.c; ++c) f(base + c, co + c, ((sb >> c) & 1) != 0);
+      co += T.c;
     }
   } else {
     const TexDev& T = S.tex[kind - 1];

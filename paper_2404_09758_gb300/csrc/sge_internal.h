@@ -192,7 +192,9 @@ cudaError_t launch_fast(const SceneDev& S, const Workspace& ws, const ViewList& 
 // Perturbed, projected vertices of both sides for every (view slot, pair) of a block of pairs.
 cudaError_t launch_vertex_pass(const SceneDev& S, const Workspace& ws, const ViewList& vl, const EstimateArgs& a,
                                cudaStream_t st);
-int estimate_blocks_per_sm(int shading, int grouped);
+int estimate_blocks_per_sm(int shading, int grouped, int group_channels);
+// channels of every read texture together (the channel sums of a texel-group table entry)
+int group_channels(const SceneDev& S);
 int fast_blocks_per_sm(int shading, int grouped);
 
 // Batched form of the two estimator kernels over BatchArgs' assets.
