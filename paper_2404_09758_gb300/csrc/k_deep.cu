@@ -7,8 +7,11 @@
 // One CTA per (16 x 16 tile, estimate).  The tile's binned triangles are set up for both sides
 // in shared memory a chunk at a time; each pixel keeps both sides' lists in registers (with each
 // entry's chunk slot, so that a bin of one chunk is not set up again to shade), then shades,
-// forms f+ - f- and credits the union of its fragments' parameters with global atomics.  Bins
-// come from the conservative binning without pruning: a fragment behind another is still listed.
+// forms f+ - f- and credits the union of its fragments' parameters.  When the bin fits one chunk
+// the vertex credits are summed per staged triangle corner in shared memory and reach the global
+// sums once per corner at the end of the CTA; texel credits (and every credit of a larger bin) go
+// to global atomics per pixel.  Bins come from the conservative binning without pruning: a
+// fragment behind another is still listed.
 #include <cuda_runtime.h>
 
 #define SGE_FILE_ID 2  // range-check sites of this file (checked build)
@@ -28,6 +31,12 @@ struct DeepSmem {
   uint32_t span[NS][DCHUNK];  // box_span of each staged side-triangle: the pixels it may cover
   uint8_t small[NS][DCHUNK];  // its edge functions over the tile fit 32 bits
   int tri[DCHUNK];
+  // estimator (two sides) with a bin of one chunk: each staged triangle's welded vertices, and
+  // per corner the sum of f+ - f- and the count of the pixels that credit it through this triangle
+  static constexpr int NV = NS == 2 ? DCHUNK : 1;
+  int vid[NV][3];
+  float vA[NV][3];
+  uint32_t vn[NV][3];
   float m[16];
   float red[TILE_PX / 32];
 };
@@ -78,12 +87,13 @@ __device__ __forceinline__ void deep_insert(unsigned long long (&L)[K], int (&P)
 }
 
 // Deep lists of one pixel of the tile for NS sides (sides[s] = +1, -1 or 0), with each entry's
-// slot in the staged chunk.  Returns whether the whole bin fit one chunk: then sm.t[s][P[s][j]]
-// still holds the set-up of entry j when the raster is done.
+// slot in the staged chunk.  Returns the number of binned triangles it rasterized; when that is at
+// most DCHUNK the whole bin fit one chunk, and sm.t[s][P[s][j]] (and sm.vid[P[s][j]]) still hold
+// entry j's set-up when the raster is done.
 // pv: the estimate's projected vertices from the vertex pass ([nv][2]: sides +, -), for the two
 // sides of an estimate; NULL: each triangle is projected from the scene with key and sides[].
 template <int NS>
-__device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& ws, DeepSmem<NS>& sm, int slot,
+__device__ __forceinline__ int deep_raster(const SceneDev& S, const Workspace& ws, DeepSmem<NS>& sm, int slot,
                                             int tile, uint64_t key, const int (&sides)[NS],
                                             unsigned long long (&L)[NS][K], int (&P)[NS][K], long long rx,
                                             long long ry, int dx, int dy, const int4* pv = nullptr) {
@@ -102,6 +112,14 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
     if ((int)threadIdx.x < cnt) {
       const int tri = (int)bin_at(S, ws, beg + c0 + threadIdx.x);
       sm.tri[threadIdx.x] = tri;
+      if constexpr (NS == 2) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          sm.vid[threadIdx.x][k] = vert_of(S, tri, k);
+          sm.vA[threadIdx.x][k] = 0.0f;
+          sm.vn[threadIdx.x][k] = 0u;
+        }
+      }
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         PVert v[3];
@@ -141,12 +159,13 @@ __device__ __forceinline__ bool deep_raster(const SceneDev& S, const Workspace& 
       }
     }
   }
-  return nb <= DCHUNK;
+  return nb;
 }
 
 // Front-to-back composite of one side's list at one pixel: T = 1; per listed fragment
 // C += T a rgb, T *= 1 - a with a = clamp(alpha, 0, 1); C += T background.  on_fragment(tri,
-// foot, j) is called for each listed fragment with its triangle, albedo footprint and layer.
+// foot, j, q) is called for each listed fragment with its triangle, albedo footprint, layer and
+// chunk slot.
 // staged: the side's set-ups in shared memory (slots P) when the bin fit one chunk, else NULL
 // (each fragment is set up again; the same arithmetic gives the same set-up).
 // ps: the estimate's precomputed signs (vertex bits, texel planes), or NULL to hash with key.
@@ -221,7 +240,7 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
     c1 += w * a[1];
     c2 += w * a[2];
     T *= 1.0f - al;
-    on_fragment(tri, f, j);
+    on_fragment(tri, f, j, P[j]);
   }
   return f3(c0 + T * S.bg[0], c1 + T * S.bg[1], c2 + T * S.bg[2]);
 }
@@ -261,7 +280,8 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
   const int pb = pair - a.pair_begin;
   const int4* pv = ws.pverts + 2 * (((long long)slot * ws.max_pairs + pb) * S.nv);
   const PairSigns ps = pair_signs(S, ws, slot, pb);
-  const bool resident = deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy, pv);
+  const int nb = deep_raster<2>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy, pv);
+  const bool resident = nb <= DCHUNK;
   float lv = 0.0f;
   if (px < S.W && py < S.H) {
     const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
@@ -287,7 +307,12 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
 #pragma unroll
     for (int j = 0; j < K; ++j) g_tri[j] = -1, g_fp[j] = -1;
     bool minus = false;
-    auto credit_keys = [&](int tri, const Foot& f, int j) {
+    // a bin of one chunk: the pixel's distinct triangles by chunk slot, each with the corners whose
+    // vertex no earlier one of them has; their credits go to the shared per-corner sums
+    int ds[2 * K];
+    uint32_t dm[2 * K];
+    int nds = 0;
+    auto credit_keys = [&](int tri, const Foot& f, int j, int q) {
       // a footprint: its first texel and whether its rows were clamped to one (x1 follows from x0)
       const int fp = S.foot_nearest ? f.nearest : 2 * (f.y0 * A.w + f.x0) + (f.y1 != f.y0 ? 1 : 0);
       bool tri_seen = false, fp_seen = false;
@@ -301,7 +326,19 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
           fp_seen = fp_seen || (g_tri[i] >= 0 && g_fp[i] == fp);
         }
       }
-      if (!tri_seen) {
+      if (!tri_seen && resident) {
+        uint32_t mask = 7u;
+        for (int i = 0; i < nds; ++i) {
+          const int o = ds[i];
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk)
+              if (sm.vid[q][k] == sm.vid[o][kk]) mask &= ~(1u << k);
+        }
+        ds[nds] = q;
+        dm[nds++] = mask;
+      } else if (!tri_seen) {
 #pragma unroll
         for (int v = 0; v < 3; ++v) addv(vkey(vert_of(S, tri, v)));
       }
@@ -325,6 +362,15 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
     const float df = loss_diff(cp, cm, f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2)), fp, fm);
     lv = 0.5f * (fp + fm);
     if (a.delta_f) a.delta_f[((long long)slot * a.pairs + pair) * npx + p] = df;
+    for (int i = 0; i < nds; ++i) {
+      const int q = ds[i];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (!((dm[i] >> k) & 1u)) continue;
+        atomicAdd(&sm.vA[q][k], df);
+        atomicAdd(&sm.vn[q][k], 1u);
+      }
+    }
     // one count per key (k_expand_counts gives it to every channel after the call), a signed
     // sum per channel
     for (int q = 0; q < nvk + ntk; ++q) {
@@ -336,6 +382,28 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
         if (!CHK(S, p, S.chk.params)) return;
         atomicAdd(a.grad + p, neg ? -df : df);
       });
+    }
+  }
+  if (resident) {
+    // every staged corner credited by some pixel: one count and one signed sum per channel
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < nb) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint32_t n = sm.vn[t][k];
+        if (!n) continue;
+        const int v = sm.vid[t][k];
+        if (CHK(S, v, ws.n_kcount)) atomicAdd(ws.kcount + v, n);
+        const float A = sm.vA[t][k];
+        if (A == 0.0f) continue;
+        const uint32_t sb = vertex_signs(ps, v);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long q = 3ll * v + c;
+          if (CHK(S, q, S.chk.params)) atomicAdd(a.grad + q, ((sb >> c) & 1) ? -A : A);
+        }
+      }
     }
   }
   if (a.loss) cta_add(lv / (float)a.pairs, sm.red, a.loss + slot);
@@ -356,7 +424,7 @@ __global__ void __launch_bounds__(TILE_PX) k_render_deep(SceneDev S, Workspace w
   unsigned long long L[1][K];
   int P[1][K];
   const int sides[1] = {side};
-  const bool resident = deep_raster<1>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy);
+  const bool resident = deep_raster<1>(S, ws, sm, slot, tile, key, sides, L, P, rx, ry, dx, dy) <= DCHUNK;
   float f = 0.0f;
   if (px < S.W && py < S.H) {
     const long long npx = (long long)S.W * S.H, p = (long long)py * S.W + px;
@@ -366,7 +434,7 @@ __global__ void __launch_bounds__(TILE_PX) k_render_deep(SceneDev S, Workspace w
     }
     if (rgb || loss) {
       const float3 c = deep_composite(S, sm.m, key, side, L[0], P[0], resident ? sm.t[0] : nullptr, rx, ry, dx, dy,
-                                      [](int, const Foot&, int) {});
+                                      [](int, const Foot&, int, int) {});
       if (rgb) rgb[3 * p] = c.x, rgb[3 * p + 1] = c.y, rgb[3 * p + 2] = c.z;
       if (loss) {
         const float* tp = S.targets + ((long long)view * npx + p) * 3;
