@@ -372,12 +372,25 @@ __global__ void __launch_bounds__(TILE_PX, 3) k_estimate_deep(SceneDev S, Worksp
       }
     }
     // one count per key (k_expand_counts gives it to every channel after the call), a signed
-    // sum per channel
+    // sum per channel (RGBA texels of an 8-byte aligned gradient: two vector reductions)
+    const bool pairs4 = A.c == 4 && ((reinterpret_cast<uintptr_t>(a.grad + A.offset) & 7) == 0);
     for (int q = 0; q < nvk + ntk; ++q) {
       const uint32_t kq = q < nvk ? vk[q] : tk[q - nvk];
       const uint32_t kind = kq >> 28, idx = kq & 0x0FFFFFFFu;
       const long long kc = kind == 0 ? (long long)idx : ws.kc_off[kind - 1] + idx;
       if (CHK(S, kc, ws.n_kcount)) atomicAdd(ws.kcount + kc, 1u);
+      if (kind != 0 && pairs4) {
+        // an RGBA texel: two 2-channel reductions
+        const long long base = A.offset + (long long)idx * 4;
+        const uint32_t sb = texel_signs(ps, A.index, idx);
+        if (CHK(S, base + 3, S.chk.params)) {
+          atomicAdd(reinterpret_cast<float2*>(a.grad + base),
+                    make_float2((sb & 1) ? -df : df, (sb & 2) ? -df : df));
+          atomicAdd(reinterpret_cast<float2*>(a.grad + base + 2),
+                    make_float2((sb & 4) ? -df : df, (sb & 8) ? -df : df));
+        }
+        continue;
+      }
       for_each_signed_channel<false>(S, ps, kq, [&](long long p, int, bool neg) {
         if (!CHK(S, p, S.chk.params)) return;
         atomicAdd(a.grad + p, neg ? -df : df);
