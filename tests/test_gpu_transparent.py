@@ -46,7 +46,10 @@ def synth_layers():
     return MAX_LAYERS
 
 
-@pytest.mark.parametrize("render,views,pairs", [(100, 2, 3), (48, 1, 5)])
+# 100 x 100: tiles whose bins fit one staged chunk of 128 triangles (credits pre-summed in shared
+# memory) beside larger ones; 32 x 32: the three spheres' 1,536 triangles over four tiles, every
+# bin larger than a chunk (credits straight to the global sums)
+@pytest.mark.parametrize("render,views,pairs", [(100, 2, 3), (48, 1, 5), (32, 1, 2)])
 def test_estimate_matches_oracle(render, views, pairs):
     import torch
     sc, tg = _scene(render, views, pairs)
