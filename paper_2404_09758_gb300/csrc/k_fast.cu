@@ -686,8 +686,23 @@ __device__ __forceinline__ void fast_items(const SceneDev& S, const Workspace& w
       sm.win[1] = sm.win[3] = -0x7FFFFFFF;
       sm.n_win = 0;
     }
+    // the tile's target pixels: a tile inside the image whose rows start 16-byte aligned is read
+    // as 16 rows of 12 float4 (each row's 16 RGB pixels) into the per-pair set-up array, which is
+    // free until the first pair's set-up; any other tile pixel by pixel
     float3 tgt = f3(0.f, 0.f, 0.f);
-    if (valid) {
+    const float* trow = S.targets + (((long long)view * S.H + ty * TILE) * S.W + tx * TILE) * 3;
+    const bool vec_tgt = (tx + 1) * TILE <= S.W && (ty + 1) * TILE <= S.H && (S.W & 3) == 0 &&
+                         (reinterpret_cast<uintptr_t>(S.targets) & 15) == 0;
+    if (vec_tgt) {
+      float4* stage = reinterpret_cast<float4*>(&sm.side[0][0]);
+      if (tid < TILE * 12) {
+        const int r = tid / 12, q = tid % 12;
+        stage[tid] = __ldg(reinterpret_cast<const float4*>(trow + (long long)r * S.W * 3) + q);
+      }
+      __syncthreads();
+      const float* st = reinterpret_cast<const float*>(stage) + (dy * TILE + dx) * 3;
+      tgt = f3(st[0], st[1], st[2]);
+    } else if (valid) {
       const float* tp = S.targets + (((long long)view * S.H + py) * S.W + px) * 3;
       tgt = f3(__ldg(tp), __ldg(tp + 1), __ldg(tp + 2));
     }
