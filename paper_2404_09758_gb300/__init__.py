@@ -564,14 +564,75 @@ class Batch:
         _abi.check(L.sge_estimate_grad_batch(self._arr, len(self.scenes), int(seed), int(it),
                                              int(pairs_per_view), C.byref(self.tuning), _stream_ptr(stream)))
 
-    def autotune(self, pairs_per_view: int, repeats: int = 2, stream=None) -> float:
-        """Pick the launch shape for these entries (zeroes their buffers); returns its ms."""
+    def autotune(self, pairs_per_view: int, repeats: int = 2, stream=None, cache: Optional[str] = None) -> float:
+        """Pick the launch shape for these entries (zeroes their buffers); returns its ms.
+        With `cache` (a JSON file path), a launch shape stored there for the same GPU, render
+        sizes, triangle-count buckets and pairs is reused without timing, and a new one is
+        stored."""
+        key = None
+        if cache is not None:
+            torch = _torch()
+            dev = self.scenes[0].device
+            key = tuning_key(torch.cuda.get_device_name(dev),
+                             [(sc.width, sc.height, int(sc.pos_idx.shape[0])) for sc in self.scenes],
+                             pairs_per_view)
+            hit = tuning_cache_load(cache, key)
+            if hit is not None:
+                self.tuning, ms = hit
+                return ms
         t = _abi.BatchTuning()
         ms = C.c_float(0.0)
         _abi.check(_abi.load().sge_autotune_batch(self._arr, len(self.scenes), int(pairs_per_view), int(repeats),
                                                   C.byref(t), C.byref(ms), _stream_ptr(stream)))
         self.tuning = t
+        if key is not None:
+            tuning_cache_store(cache, key, t, float(ms.value))
         return float(ms.value)
+
+
+def tuning_key(gpu: str, assets, pairs_per_view: int) -> str:
+    """Key of a batch's launch shape in the tuning cache: the GPU's name, each asset's render
+    size and triangle count rounded up to a power of two (in the batch's order), and the pairs per
+    view.  assets: [(width, height, n_triangles), ...]."""
+    parts = [f"{int(w)}x{int(h)}:T{1 << max(0, int(t) - 1).bit_length()}" for w, h, t in assets]
+    return f"{gpu}|{int(pairs_per_view)}|" + ",".join(parts)
+
+
+def tuning_cache_load(path: str, key: str):
+    """(BatchTuning, ms) stored under key, or None (no file, no entry, or an unreadable file)."""
+    import json
+    import os
+    if not os.path.exists(path):
+        return None
+    try:
+        with open(path) as f:
+            e = json.load(f).get(key)
+        if e is None:
+            return None
+        return _abi.BatchTuning(int(e["pairs_per_item"]), int(e["blocks_per_sm"]), int(e["light_bin"])), float(e["ms"])
+    except (OSError, ValueError, KeyError, TypeError, AttributeError):
+        return None
+
+
+def tuning_cache_store(path: str, key: str, t, ms: float) -> None:
+    """Store a launch shape under key (the file is rewritten whole, through a temporary file)."""
+    import json
+    import os
+    data = {}
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                data = json.load(f)
+            if not isinstance(data, dict):
+                data = {}
+        except (OSError, ValueError):
+            data = {}
+    data[key] = {"pairs_per_item": int(t.pairs_per_item), "blocks_per_sm": int(t.blocks_per_sm),
+                 "light_bin": int(t.light_bin), "ms": float(ms)}
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 def _make_function():
