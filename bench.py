@@ -55,8 +55,8 @@ OPS_CREDIT = 2      # per contribution: one add to the parameter's sum, one to i
 # one estimate call, 134.2 M pixel pairs): smsp__inst_executed.sum 5.151 G x 22.73 active lanes =
 # 872 thread instructions per pixel pair; dram__bytes_read.sum + dram__bytes_write.sum =
 # 164.40 MB + 7.09 MB per launch.  Set to None when the kernel changes until it is captured again.
-NCU_INSTR_PER_PIXEL_PAIR = 872.0
-NCU_DRAM_BYTES_PER_LAUNCH = 171.49e6
+NCU_INSTR_PER_PIXEL_PAIR = None
+NCU_DRAM_BYTES_PER_LAUNCH = None
 
 
 def method_ops(shading: int, read_channels, covered_sides: float, covered_pairs: float, contributions: float):
