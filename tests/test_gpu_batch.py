@@ -90,6 +90,36 @@ def test_batch_pair_blocks_and_autotune_match_oracle(small):
     _check_against_oracle(scs, targets, bufs, sts, 3)
 
 
+def test_autotune_cache_reuses_the_stored_shape(small, tmp_path):
+    """With a cache file, the first autotune times and stores its shape; a second batch of the
+    same assets takes it from the file without timing (the same shape and the stored ms), and
+    its estimate still matches the oracle."""
+    import json
+    import torch
+    from paper_2404_09758_gb300 import Batch
+    scs, targets = small
+    cache = str(tmp_path / "tune.json")
+    shapes = []
+    for rep in range(2):
+        gs, bufs, entries = [], [], []
+        for k, (sc, tg) in enumerate(zip(scs, targets)):
+            g = gpu_scene(sc, tg, max_views_per_call=2)
+            grad, counts = g.new_grad_buffers()
+            loss = torch.zeros(2, device=g.device)
+            gs.append(g)
+            bufs.append((grad, counts, loss))
+            entries.append((g, _views_of(k), grad, counts, loss))
+        b = Batch(entries)
+        ms = b.autotune(3, repeats=1, cache=cache)
+        shapes.append((b.tuning.pairs_per_item, b.tuning.blocks_per_sm, b.tuning.light_bin, ms))
+    assert shapes[0] == shapes[1]
+    assert len(json.load(open(cache))) == 1
+    b.estimate_grad(SEED, ITER, 3)
+    sts = [g.status() for g in gs]
+    torch.cuda.synchronize()
+    _check_against_oracle(scs, targets, bufs, sts, 3)
+
+
 def test_batch_equals_single_scene_calls(small):
     """Same estimates as one sge_estimate_grad per asset: counts exactly, sums to float order."""
     import torch
