@@ -52,11 +52,11 @@ OPS_SHADE = {0: 0, 1: 55, 2: 125}  # unlit; Lambert with a normal map; GGX + Lam
 OPS_LOSS_DIFF = 12  # per pixel pair: sum_c (I+ - I-)(I+ + I- - 2I)
 OPS_CREDIT = 2      # per contribution: one add to the parameter's sum, one to its count
 # One ncu --set full capture of this build's k_estimate_fast<unlit> on this workload (one launch =
-# one estimate call, 134.2 M pixel pairs): smsp__inst_executed.sum 5.151 G x 22.73 active lanes =
-# 872 thread instructions per pixel pair; dram__bytes_read.sum + dram__bytes_write.sum =
-# 164.40 MB + 7.09 MB per launch.  Set to None when the kernel changes until it is captured again.
-NCU_INSTR_PER_PIXEL_PAIR = None
-NCU_DRAM_BYTES_PER_LAUNCH = None
+# one estimate call, 134.2 M pixel pairs): smsp__inst_executed.sum 5.158 G x 22.74 active lanes =
+# 874 thread instructions per pixel pair; dram__bytes_read.sum + dram__bytes_write.sum =
+# 164.16 MB + 6.58 MB per launch.  Set to None when the kernel changes until it is captured again.
+NCU_INSTR_PER_PIXEL_PAIR = 874.0
+NCU_DRAM_BYTES_PER_LAUNCH = 170.74e6
 
 
 def method_ops(shading: int, read_channels, covered_sides: float, covered_pairs: float, contributions: float):
