@@ -177,7 +177,9 @@ __device__ __forceinline__ float3 deep_composite(const SceneDev& S, const float*
                                                  const int4* pv = nullptr) {
   const TexDev& A = S.rtex[0];  // the RGBA albedo, the one texture this model reads
   float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f, T = 1.0f;
-#pragma unroll
+  // not unrolled: one copy of the fragment's set-up, sampling and credit code per side keeps the
+  // kernel's code within the instruction cache (the lists are read from local memory instead)
+#pragma unroll 1
   for (int j = 0; j < K; ++j) {
     if (L[j] == ~0ull) continue;
     const int tri = (int)(L[j] & 0xFFFFFFFFu);
