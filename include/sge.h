@@ -313,9 +313,10 @@ typedef struct {
  * synchronises, so the host buffers must stay valid until the stream has passed the call.
  * grad_sums, counts (zeroed by the step), adam_m, adam_v, state: device memory, as in those
  * calls; loss_dev: device [n_views] float32, required when io->loss_out is set (else may be
- * NULL).  Errors: SGE_ERR_INVALID_ARG for a NULL scene, io, opt or state, a bad view list,
- * pairs_per_view < 1, or loss_out without loss_dev (checked before anything is enqueued);
- * the errors of the calls it runs; SGE_ERR_CUDA when a copy cannot be enqueued. */
+ * NULL).  Errors: SGE_ERR_INVALID_ARG for a NULL scene, io, opt, state, grad_sums or counts,
+ * a bad view list, pairs_per_view < 1, loss_out without loss_dev, a bad step kind, Adam without
+ * m and v, or an eps <= 0 (all checked before anything is enqueued); the errors of the calls it
+ * runs; SGE_ERR_CUDA when a copy cannot be enqueued. */
 int sge_iterate_host(sge_scene *scene, uint64_t seed, sge_iter_state *state, const int32_t *view_ids,
                      int32_t n_views, int32_t pairs_per_view, const sge_opt *opt, float *grad_sums,
                      uint32_t *counts, float *adam_m, float *adam_v, float *loss_dev, const sge_host_io *io,

@@ -557,9 +557,17 @@ int sge_iterate_host(sge_scene* s, uint64_t seed, sge_iter_state* state, const i
   if (!state || !aligned4(state)) return fail(SGE_ERR_INVALID_ARG, "state must be a 4-byte aligned device pointer");
   if (pairs_per_view < 1) return fail(SGE_ERR_INVALID_ARG, "pairs_per_view must be >= 1");
   if (io->loss_out && !loss_dev) return fail(SGE_ERR_INVALID_ARG, "io->loss_out needs loss_dev");
+  // the step's argument checks too, so that a call it would refuse enqueues nothing
+  if (!grad_sums || !counts) return fail(SGE_ERR_INVALID_ARG, "grad_sums and counts must be non-NULL");
+  if (opt->kind < SGE_STEP_SGD || opt->kind > SGE_STEP_SGD_MEAN)
+    return fail(SGE_ERR_INVALID_ARG, "bad step kind %d", opt->kind);
+  if (opt->kind == SGE_STEP_ADAM && (!adam_m || !adam_v)) return fail(SGE_ERR_INVALID_ARG, "Adam needs m and v");
   ViewList vl;
   int rc = views_of(s, view_ids, n_views, vl);
   if (rc) return rc;
+  if (s->desc.eps_pos <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "eps_pos must be > 0 to form Eq. 9's estimate");
+  for (int k = 0; k < s->dev.ntex; ++k)
+    if (s->dev.tex[k].eps <= 0.0f) return fail(SGE_ERR_INVALID_ARG, "texture %d eps must be > 0 to step", k);
   cudaStream_t st = (cudaStream_t)stream;
   // the parameter groups in gradient order: positions, then each texture
   const sge_scene_desc& d = s->desc;

@@ -76,6 +76,20 @@ def test_host_iteration_checks_its_arguments_before_enqueueing():
     for scene, stp, optp, iop in cases:
         rc = L.sge_iterate_host(scene, 1, stp, None, 0, 1, optp, None, None, None, None, None, iop, None)
         assert rc == _abi.ERR_INVALID_ARG, L.sge_last_error()
+    # the step's own argument checks, also before the scene is looked at
+    buf = (ctypes.c_float * 4)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    scene, stp, iop = ctypes.c_void_p(8), ctypes.byref(st), ctypes.byref(io)
+    rc = L.sge_iterate_host(scene, 1, stp, None, 1, 1, ctypes.byref(opt), None, p, p, p, None, iop, None)
+    assert rc == _abi.ERR_INVALID_ARG and b"grad_sums" in L.sge_last_error()
+    bad = _abi.Opt()
+    bad.kind = 7
+    rc = L.sge_iterate_host(scene, 1, stp, None, 1, 1, ctypes.byref(bad), p, p, p, p, None, iop, None)
+    assert rc == _abi.ERR_INVALID_ARG and b"kind" in L.sge_last_error()
+    adam = _abi.Opt()
+    adam.kind = _abi.STEP_ADAM
+    rc = L.sge_iterate_host(scene, 1, stp, None, 1, 1, ctypes.byref(adam), p, p, None, p, None, iop, None)
+    assert rc == _abi.ERR_INVALID_ARG and b"Adam" in L.sge_last_error()
 
 
 def test_no_cpu_fallback_without_gpu():
